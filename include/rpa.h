@@ -1,0 +1,151 @@
+/*
+ * rpa.h - C ABI of the GB300 static-subspace RPA correlation-energy path.
+ *
+ * Method: Weinberg et al., "Static subspace approximation for random phase
+ * approximation correlation energies" (arXiv:2405.20258).  One q-point's work:
+ *
+ *   chi0(0)  = -(1/Omega) A^H diag(f(0)) A             Eq. (chi0_partial_occs)
+ *   chi~(0)  = v^1/2 chi0(0) v^1/2,  v(G) = 4 pi/|q+G|^2 Eq. (rpaE), symmetrised
+ *   C        = N_eig eigenvectors of chi~(0) with the most negative eigenvalues (Method, C_s)
+ *   M~       = (A v^1/2 C)^H                            Method, M_s = M C_s
+ *   chi_s(k) = -(1/Omega) M~ diag(f(w_k)) M~^H           Method, chi0_s = M_s^+ Delta M_s
+ *   E_c      = (1/2pi) sum_k w_k sum_i [ln(1 - l_ki) + l_ki]   Eq. (rpaE), trace in the subspace
+ *
+ * with A[vc][g] = M_vc(G_g) (Eq. pwMat), row vc = v*n_c + c, and the transition
+ * weight f_vc(w) = 4 D_vc / (D_vc^2 + w^2), D_vc = e_c[c] - e_v[v]: the
+ * resonant and anti-resonant terms of Delta_vck(q, iw) for integer
+ * occupations with the spin factor 2.  The frequencies w_k, weights are
+ * Gauss-Legendre points on [0,1] mapped by w = s t/(1-t) (Computational Details).
+ *
+ * Conventions shared by every entry point
+ *  - Complex arrays are interleaved (re, im) pairs, row-major, in DEVICE memory
+ *    unless the argument says "host".  The caller owns every array it passes;
+ *    the plan owns its workspace and frees it in rpa_plan_destroy.
+ *  - All work is enqueued on the plan's CUDA stream.  Only rpa_ecorr (which
+ *    returns energies to the host) and rpa_plan_create synchronise.
+ *  - Errors are returned, never aborted on.  After RPA_EINVAL or RPA_ESTATE the
+ *    plan is unchanged and stays usable.  rpa_last_error() gives a message.
+ *  - Stages of one q-point must run in order chi0 -> basis -> freq -> ecorr;
+ *    calling a stage early returns RPA_ESTATE.
+ *  - Output pointers marked "may be NULL" are optional copies of intermediates.
+ *  - Not thread-safe per plan: one host thread drives one plan at a time.
+ */
+#ifndef RPA_H
+#define RPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RPA_OK = 0,
+  RPA_EINVAL = 1,    /* bad argument: sizes, NULL pointer, unknown option   */
+  RPA_ENOMEM = 2,    /* device or host allocation failed                    */
+  RPA_ECUDA = 3,     /* a CUDA runtime call failed                          */
+  RPA_EEIG = 4,      /* an eigensolver reported failure (info != 0)         */
+  RPA_ENUMERIC = 5,  /* non-finite value or 1 - lambda <= 0 in the energy   */
+  RPA_ETIMEOUT = 6,  /* a bounded device wait gave up                       */
+  RPA_ESTATE = 7     /* stage called out of order                           */
+} rpa_status;
+
+typedef enum {
+  RPA_FP64 = 0,      /* every contraction in FP64 (SIMT DFMA)                              */
+  RPA_MIXED = 1      /* contractions on BF16 tensor cores with exact slicing, FP64 solves  */
+} rpa_precision;
+
+typedef enum {
+  RPA_ROUTE_EIG = 0,      /* eigenvalues of each chi_s(k): sum ln(1 - l) + l              */
+  RPA_ROUTE_CHOLESKY = 1  /* ln det(1 - chi_s) from a Cholesky factor + FP64 trace term     */
+} rpa_energy_route;
+
+typedef enum { RPA_C128 = 0, RPA_C64 = 1 } rpa_dtype;
+
+/* One q-point.  Arrays are device memory owned by the caller and must stay
+ * valid and unchanged until the plan is destroyed. */
+typedef struct {
+  int n_g;                 /* plane waves N_G >= 1                                  */
+  int n_v, n_c;            /* valence / conduction bands, N_vc = n_v*n_c >= 1       */
+  int n_eig;               /* subspace size, 1 <= n_eig <= n_g                      */
+  int n_freq;              /* Gauss-Legendre points, 1 <= n_freq <= 256             */
+  double omega_cell;       /* cell volume Omega (bohr^3) > 0                        */
+  const double* qg2;       /* [n_g] |q+G|^2 (bohr^-2) > 0                           */
+  const double* e_v;       /* [n_v] valence energies (Ha)                           */
+  const double* e_c;       /* [n_c] conduction energies (Ha), e_c[c] > e_v[v]       */
+  const void* m;           /* [n_v*n_c][n_g] A = M_vc(G), complex of m_dtype;
+                              NULL: drawn on the device by the counter generator    */
+  int m_dtype;             /* rpa_dtype of m                                        */
+  int iq;                  /* q index fed to the generator (m == NULL)              */
+  unsigned long long seed; /* generator seed (m == NULL)                            */
+  const int* miller;       /* [n_g][3] Miller indices of G (m == NULL)              */
+} rpa_qpoint;
+
+typedef struct {
+  int precision;           /* rpa_precision                                          */
+  int energy_route;        /* rpa_energy_route                                       */
+  double omega_scale;      /* s of the frequency map w = s t/(1-t); <= 0 means 0.5 Ha */
+  int reserved[8];         /* zero                                                   */
+} rpa_options;
+
+typedef struct rpa_plan_s* rpa_plan_t;
+
+/* Create a plan for n_q q-points: validate, record the descriptors, allocate
+ * workspace for the largest q-point, build the frequency grid on the device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  opt may be NULL
+ * (FP64, eigenvalue route, s = 0.5).  On failure *out is NULL. */
+rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q,
+                           const rpa_options* opt, void* stream);
+rpa_status rpa_plan_destroy(rpa_plan_t plan);
+const char* rpa_last_error(rpa_plan_t plan);   /* plan may be NULL: last create error */
+const char* rpa_status_string(int status);
+
+/* Static polarizability chi~(0) = -(1/Omega) v^1/2 A^H diag(f(0)) A v^1/2,
+ * Eq. (chi0_partial_occs) at w = 0 and the symmetrisation of Eq. (rpaE).
+ * chi_tilde_out: [n_g][n_g] complex128, full Hermitian matrix, may be NULL. */
+rpa_status rpa_chi0_static(rpa_plan_t plan, int iq, void* chi_tilde_out);
+
+/* Subspace basis (Method, C_s): the n_eig eigenpairs of chi~(0) with the most
+ * negative eigenvalues, FP64 Hermitian eigensolve, ascending order; each
+ * eigenvector's entry of largest modulus (lowest g on ties) is made real > 0.
+ * lambda_out: [n_eig] float64, may be NULL.  c_out: [n_g][n_eig] complex128,
+ * may be NULL.  Returns RPA_EEIG if the solver fails. */
+rpa_status rpa_subspace_basis(rpa_plan_t plan, int iq, double* lambda_out, void* c_out);
+
+/* Projection and frequency-dependent subspace polarizabilities (Method):
+ * M~ = (A v^1/2 C)^H, chi_s(k) = -(1/Omega) M~ diag(f(w_k)) M~^H for every
+ * quadrature node, and the FP64 trace T_k = -(1/Omega) sum_vc f_vc(w_k) |M~[:,vc]|^2.
+ * mtilde_out: [n_eig][n_v*n_c] complex128, may be NULL.
+ * chi_s_out:  [n_freq][n_eig][n_eig] complex128 (full Hermitian), may be NULL.
+ * trace_out:  [n_freq] float64, may be NULL. */
+rpa_status rpa_chi_freq(rpa_plan_t plan, int iq, void* mtilde_out, void* chi_s_out,
+                        double* trace_out);
+
+/* Correlation energy of Eq. (rpaE) in the subspace: eigenvalues of every
+ * chi_s(k) (FP64), or ln det(1 - chi_s) by Cholesky on the Cholesky route, then
+ * E_c = (1/2pi) sum_k w_k [sum_i log1p(-l_ki) + T_k].  Synchronises the stream.
+ * ec_host: host float64 [1] (iq >= 0) or [n_q] (iq == -1: every q-point, each
+ * run through all stages).  lam_out: [n_freq][n_eig] float64 device, may be
+ * NULL (eigenvalue route only).  RPA_ENUMERIC if any 1 - l <= 0 or a value is
+ * not finite. */
+rpa_status rpa_ecorr(rpa_plan_t plan, int iq, double* ec_host, double* lam_out);
+
+/* The quadrature the plan uses: omega_host, weight_host host float64 [n_freq]
+ * of q-point iq (weights include the Jacobian of the map). */
+rpa_status rpa_plan_frequencies(rpa_plan_t plan, int iq, double* omega_host, double* weight_host);
+
+/* Device generator of synthetic matrix elements (the counter-based splitmix64
+ * and Box-Muller recipe of the input generator): writes A[v][c][g] for
+ * v in [v0, v0+nv), c in [c0, c0+nc) to out ([nv*nc][q->n_g] complex of dtype).
+ * Uses q->seed, q->iq, q->miller, q->qg2 (device).  Asynchronous on stream. */
+rpa_status rpa_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc,
+                          void* out, int dtype, void* stream);
+
+/* Library version string. */
+const char* rpa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPA_H */

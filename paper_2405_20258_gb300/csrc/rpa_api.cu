@@ -1,0 +1,517 @@
+// C ABI of the static-subspace RPA path: plan life cycle, argument checks,
+// stage ordering, workspace, and the FP64 eigensolves (cuSOLVER).
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rpa_internal.h"
+#include "rpa_tc.h"
+
+using rpa::cplx;
+
+namespace {
+
+enum Stage { ST_NONE = 0, ST_CHI0 = 1, ST_BASIS = 2, ST_FREQ = 3 };
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct rpa_plan_s {
+  int n_q = 0;
+  std::vector<rpa_qpoint> q;
+  rpa_options opt{};
+  cudaStream_t st = nullptr;
+  cusolverDnHandle_t sol = nullptr;
+  cusolverDnParams_t params = nullptr;
+  std::vector<int> stage;
+  std::string err;
+  int max_g = 0, max_eig = 0, max_freq = 0;
+  long max_vc = 0;
+  // device workspace
+  double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr;
+  double *omega = nullptr, *weight = nullptr;  // [n_q][max_freq]
+  double *lam_all = nullptr, *lam = nullptr, *trace = nullptr, *ec = nullptr, *logdet = nullptr;
+  int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
+  cplx *chi = nullptr, *chi_work = nullptr, *C = nullptr, *B = nullptr, *mt = nullptr;
+  cplx *chis = nullptr, *chis_work = nullptr;
+  void* gen_a = nullptr;      // device-drawn A for q-points with m == NULL
+  int gen_iq = -1;            // which q-point gen_a currently holds
+  void* sol_dev = nullptr;
+  size_t sol_dev_bytes = 0;
+  void* sol_host = nullptr;
+  size_t sol_host_bytes = 0;
+  rpa::tc::Workspace tcw;     // tensor-core path workspace
+};
+
+namespace {
+
+rpa_status fail(rpa_plan_t p, rpa_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (p)
+    p->err = buf;
+  else
+    g_create_error = buf;
+  return s;
+}
+
+#define CU(p, call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(p, RPA_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                  \
+  } while (0)
+
+#define CS(p, call)                                                                     \
+  do {                                                                                  \
+    cusolverStatus_t s_ = (call);                                                       \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                  \
+      return fail(p, RPA_EEIG, "%s failed: cusolver status %d", #call, (int)s_);        \
+  } while (0)
+
+template <typename T>
+rpa_status dalloc(rpa_plan_t p, T** ptr, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    (void)cudaGetLastError();
+    return fail(p, RPA_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  return RPA_OK;
+}
+
+void free_plan(rpa_plan_t p) {
+  if (!p) return;
+  void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->omega, p->weight, p->lam_all,
+                  p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
+                  p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  rpa::tc::free_workspace(p->tcw);
+  if (p->sol_host) free(p->sol_host);
+  if (p->params) cusolverDnDestroyParams(p->params);
+  if (p->sol) cusolverDnDestroy(p->sol);
+  delete p;
+}
+
+rpa_status check_qpoint(const rpa_qpoint& q, int i) {
+  auto bad = [&](const char* what) {
+    return fail(nullptr, RPA_EINVAL, "q-point %d: %s", i, what);
+  };
+  if (q.n_g < 1) return bad("n_g must be >= 1");
+  if (q.n_v < 1 || q.n_c < 1) return bad("n_v and n_c must be >= 1");
+  if ((long)q.n_v * q.n_c > (1L << 31) - 1) return bad("n_v*n_c too large");
+  if (q.n_eig < 1 || q.n_eig > q.n_g) return bad("n_eig must be in [1, n_g]");
+  if (q.n_freq < 1 || q.n_freq > 256) return bad("n_freq must be in [1, 256]");
+  if (!(q.omega_cell > 0.0) || !std::isfinite(q.omega_cell)) return bad("omega_cell must be > 0");
+  if (!q.qg2 || !q.e_v || !q.e_c) return bad("qg2, e_v and e_c must be device pointers");
+  if (q.m_dtype != RPA_C128 && q.m_dtype != RPA_C64) return bad("unknown m_dtype");
+  if (!q.m && !q.miller) return bad("m == NULL needs miller indices for the generator");
+  return RPA_OK;
+}
+
+const rpa_qpoint* qp(rpa_plan_t p, int iq) { return &p->q[iq]; }
+
+rpa_status check_iq(rpa_plan_t p, int iq) {
+  if (!p) return RPA_EINVAL;
+  if (iq < 0 || iq >= p->n_q) return fail(p, RPA_EINVAL, "iq %d out of range [0, %d)", iq, p->n_q);
+  return RPA_OK;
+}
+
+// A of q-point iq, drawing it on the device when the caller passed none.
+rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
+  const rpa_qpoint& q = p->q[iq];
+  if (q.m) {
+    *a = q.m;
+    *dtype = q.m_dtype;
+    return RPA_OK;
+  }
+  if (p->gen_iq != iq) {
+    CU(p, rpa::launch_generate_m(&q, 0, q.n_v, 0, q.n_c, p->gen_a, q.m_dtype, p->st));
+    p->gen_iq = iq;
+  }
+  *a = p->gen_a;
+  *dtype = q.m_dtype;
+  return RPA_OK;
+}
+
+rpa_status prepare(rpa_plan_t p, int iq) {
+  const rpa_qpoint& q = p->q[iq];
+  CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
+  CU(p, rpa::launch_prepare_scalars(q.qg2, q.n_g, q.e_v, q.n_v, q.e_c, q.n_c, p->sv, p->delta,
+                                    p->sf0, p->flags, p->st));
+  int h = 0;
+  CU(p, cudaMemcpyAsync(&h, p->flags, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaStreamSynchronize(p->st));
+  if (h & 1) return fail(p, RPA_EINVAL, "q-point %d: |q+G|^2 must be finite and > 0", iq);
+  if (h & 2) return fail(p, RPA_EINVAL, "q-point %d: e_c[c] - e_v[v] must be finite and > 0", iq);
+  return RPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rpa_version(void) { return "gb300-rpa 0.1 (sm_103a)"; }
+
+const char* rpa_status_string(int s) {
+  switch (s) {
+    case RPA_OK: return "ok";
+    case RPA_EINVAL: return "invalid argument";
+    case RPA_ENOMEM: return "out of memory";
+    case RPA_ECUDA: return "CUDA error";
+    case RPA_EEIG: return "eigensolver failure";
+    case RPA_ENUMERIC: return "numerical failure";
+    case RPA_ETIMEOUT: return "device wait timed out";
+    case RPA_ESTATE: return "stage called out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* rpa_last_error(rpa_plan_t p) { return p ? p->err.c_str() : g_create_error.c_str(); }
+
+rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const rpa_options* opt,
+                           void* stream) {
+  if (!out) return fail(nullptr, RPA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!q || n_q < 1) return fail(nullptr, RPA_EINVAL, "need n_q >= 1 q-point descriptors");
+  rpa_options o{};
+  o.precision = RPA_FP64;
+  o.energy_route = RPA_ROUTE_EIG;
+  o.omega_scale = 0.5;
+  if (opt) o = *opt;
+  if (!(o.omega_scale > 0.0)) o.omega_scale = 0.5;
+  if (o.precision != RPA_FP64 && o.precision != RPA_MIXED)
+    return fail(nullptr, RPA_EINVAL, "unknown precision %d", o.precision);
+  if (o.energy_route != RPA_ROUTE_EIG && o.energy_route != RPA_ROUTE_CHOLESKY)
+    return fail(nullptr, RPA_EINVAL, "unknown energy route %d", o.energy_route);
+  for (int i = 0; i < n_q; ++i) {
+    rpa_status s = check_qpoint(q[i], i);
+    if (s != RPA_OK) return s;
+  }
+  rpa_plan_t p = new rpa_plan_s();
+  p->n_q = n_q;
+  p->q.assign(q, q + n_q);
+  p->opt = o;
+  p->st = (cudaStream_t)stream;
+  p->stage.assign(n_q, ST_NONE);
+  bool need_gen = false;
+  size_t gen_bytes = 0;
+  for (int i = 0; i < n_q; ++i) {
+    p->max_g = std::max(p->max_g, q[i].n_g);
+    p->max_eig = std::max(p->max_eig, q[i].n_eig);
+    p->max_freq = std::max(p->max_freq, q[i].n_freq);
+    long nvc = (long)q[i].n_v * q[i].n_c;
+    p->max_vc = std::max(p->max_vc, nvc);
+    if (!q[i].m) {
+      need_gen = true;
+      gen_bytes = std::max(gen_bytes, (size_t)nvc * q[i].n_g * (q[i].m_dtype == RPA_C64 ? 8 : 16));
+    }
+  }
+  rpa_status s;
+#define ALLOC(ptr, n)                                                  \
+  do {                                                                 \
+    s = dalloc(nullptr, &p->ptr, (size_t)(n));                         \
+    if (s != RPA_OK) {                                                 \
+      free_plan(p);                                                    \
+      return s;                                                        \
+    }                                                                  \
+  } while (0)
+  const size_t G = p->max_g, E = p->max_eig, F = p->max_freq, V = p->max_vc;
+  ALLOC(sv, G);
+  ALLOC(delta, V);
+  ALLOC(sf0, V);
+  ALLOC(w, V);
+  ALLOC(omega, (size_t)n_q * F);
+  ALLOC(weight, (size_t)n_q * F);
+  ALLOC(lam_all, G);
+  ALLOC(lam, F * E);
+  ALLOC(trace, F);
+  ALLOC(ec, 1);
+  ALLOC(logdet, F);
+  ALLOC(flags, 4);
+  ALLOC(chi, G * G);
+  ALLOC(chi_work, G * G);
+  ALLOC(C, G * E);
+  ALLOC(B, G * E);
+  ALLOC(mt, E * V);
+  ALLOC(chis, F * E * E);
+  ALLOC(chis_work, F * E * E);
+#undef ALLOC
+  if (need_gen) {
+    cudaError_t e = cudaMalloc(&p->gen_a, gen_bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      free_plan(p);
+      return fail(nullptr, RPA_ENOMEM, "generator buffer of %zu bytes: %s", gen_bytes,
+                  cudaGetErrorString(e));
+    }
+  }
+  if (o.precision == RPA_MIXED) {
+    s = rpa::tc::alloc_workspace(p->tcw, G, E, V, F);
+    if (s != RPA_OK) {
+      free_plan(p);
+      return fail(nullptr, s, "tensor-core workspace allocation failed");
+    }
+  }
+  if (cusolverDnCreate(&p->sol) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnCreateParams(&p->params) != CUSOLVER_STATUS_SUCCESS) {
+    free_plan(p);
+    return fail(nullptr, RPA_ECUDA, "cusolverDnCreate failed");
+  }
+  cusolverDnSetStream(p->sol, p->st);
+  // solver workspace: range eigensolve of chi~ and eigenvalue-only solves of chi_s
+  size_t dmax = 0, hmax = 0;
+  for (int i = 0; i < n_q; ++i) {
+    size_t db = 0, hb = 0;
+    double vl = 0, vu = 0;
+    int64_t meig = 0;
+    if (cusolverDnXsyevdx_bufferSize(p->sol, p->params, CUSOLVER_EIG_MODE_VECTOR,
+                                     CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, q[i].n_g,
+                                     CUDA_C_64F, p->chi_work, q[i].n_g, &vl, &vu, 1, q[i].n_eig,
+                                     &meig, CUDA_R_64F, p->lam_all, CUDA_C_64F, &db,
+                                     &hb) != CUSOLVER_STATUS_SUCCESS) {
+      free_plan(p);
+      return fail(nullptr, RPA_EEIG, "cusolverDnXsyevdx_bufferSize failed");
+    }
+    dmax = std::max(dmax, db);
+    hmax = std::max(hmax, hb);
+    if (cusolverDnXsyevd_bufferSize(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR,
+                                    CUBLAS_FILL_MODE_LOWER, q[i].n_eig, CUDA_C_64F, p->chis_work,
+                                    q[i].n_eig, CUDA_R_64F, p->lam, CUDA_C_64F, &db,
+                                    &hb) != CUSOLVER_STATUS_SUCCESS) {
+      free_plan(p);
+      return fail(nullptr, RPA_EEIG, "cusolverDnXsyevd_bufferSize failed");
+    }
+    dmax = std::max(dmax, db);
+    hmax = std::max(hmax, hb);
+  }
+  p->sol_dev_bytes = std::max<size_t>(dmax, 16);
+  p->sol_host_bytes = std::max<size_t>(hmax, 16);
+  if (cudaMalloc(&p->sol_dev, p->sol_dev_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_plan(p);
+    return fail(nullptr, RPA_ENOMEM, "solver workspace of %zu bytes", dmax);
+  }
+  p->sol_host = malloc(p->sol_host_bytes);
+  // quadrature of every q-point
+  for (int i = 0; i < n_q; ++i) {
+    if (rpa::launch_freq_grid(q[i].n_freq, o.omega_scale, p->omega + (size_t)i * F,
+                              p->weight + (size_t)i * F, p->st) != cudaSuccess) {
+      free_plan(p);
+      return fail(nullptr, RPA_ECUDA, "frequency grid launch failed");
+    }
+  }
+  if (cudaStreamSynchronize(p->st) != cudaSuccess) {
+    free_plan(p);
+    return fail(nullptr, RPA_ECUDA, "stream synchronize failed during plan creation");
+  }
+  *out = p;
+  return RPA_OK;
+}
+
+rpa_status rpa_plan_destroy(rpa_plan_t p) {
+  if (!p) return RPA_EINVAL;
+  if (p->st) cudaStreamSynchronize(p->st);
+  free_plan(p);
+  return RPA_OK;
+}
+
+rpa_status rpa_plan_frequencies(rpa_plan_t p, int iq, double* omega_host, double* weight_host) {
+  rpa_status s = check_iq(p, iq);
+  if (s != RPA_OK) return s;
+  if (!omega_host || !weight_host) return fail(p, RPA_EINVAL, "NULL output");
+  size_t F = p->max_freq, n = p->q[iq].n_freq;
+  CU(p, cudaMemcpyAsync(omega_host, p->omega + iq * F, n * sizeof(double), cudaMemcpyDeviceToHost,
+                        p->st));
+  CU(p, cudaMemcpyAsync(weight_host, p->weight + iq * F, n * sizeof(double),
+                        cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaStreamSynchronize(p->st));
+  return RPA_OK;
+}
+
+rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
+  rpa_status s = check_iq(p, iq);
+  if (s != RPA_OK) return s;
+  const rpa_qpoint& q = *qp(p, iq);
+  s = prepare(p, iq);
+  if (s != RPA_OK) return s;
+  const void* A;
+  int dt;
+  s = matrix_a(p, iq, &A, &dt);
+  if (s != RPA_OK) return s;
+  const long n_vc = (long)q.n_v * q.n_c;
+  const double scale = -1.0 / q.omega_cell;
+  if (p->opt.precision == RPA_MIXED) {
+    s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
+                      p->err);
+    if (s != RPA_OK) return s;
+  } else {
+    CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
+  }
+  CU(p, rpa::launch_mirror_hermitian(p->chi, q.n_g, 1, p->st));
+  if (chi_out)
+    CU(p, cudaMemcpyAsync(chi_out, p->chi, sizeof(cplx) * (size_t)q.n_g * q.n_g,
+                          cudaMemcpyDeviceToDevice, p->st));
+  p->stage[iq] = ST_CHI0;
+  return RPA_OK;
+}
+
+rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_out) {
+  rpa_status s = check_iq(p, iq);
+  if (s != RPA_OK) return s;
+  if (p->stage[iq] < ST_CHI0) return fail(p, RPA_ESTATE, "rpa_chi0_static(%d) must come first", iq);
+  const rpa_qpoint& q = *qp(p, iq);
+  const int n = q.n_g;
+  CU(p, cudaMemcpyAsync(p->chi_work, p->chi, sizeof(cplx) * (size_t)n * n,
+                        cudaMemcpyDeviceToDevice, p->st));
+  double vl = 0.0, vu = 0.0;
+  int64_t meig = 0;
+  CU(p, cudaMemsetAsync(p->flags + 2, 0, sizeof(int), p->st));
+  // The row-major Hermitian chi~ read column-major is conj(chi~): same eigenvalues,
+  // conjugated eigenvectors, undone by the gauge kernel.
+  CS(p, cusolverDnXsyevdx(p->sol, p->params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                          CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, p->chi_work, n, &vl, &vu, 1,
+                          q.n_eig, &meig, CUDA_R_64F, p->lam_all, CUDA_C_64F, p->sol_dev,
+                          p->sol_dev_bytes, p->sol_host, p->sol_host_bytes, p->flags + 2));
+  int info = 0;
+  CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaStreamSynchronize(p->st));
+  if (info != 0) return fail(p, RPA_EEIG, "Xsyevdx info = %d", info);
+  if (meig != q.n_eig) return fail(p, RPA_EEIG, "Xsyevdx returned %lld of %d eigenpairs",
+                                   (long long)meig, q.n_eig);
+  CU(p, rpa::launch_gauge(p->chi_work, n, n, q.n_eig, p->sv, p->C, p->B, p->st));
+  if (lambda_out)
+    CU(p, cudaMemcpyAsync(lambda_out, p->lam_all, sizeof(double) * q.n_eig,
+                          cudaMemcpyDeviceToDevice, p->st));
+  if (c_out)
+    CU(p, cudaMemcpyAsync(c_out, p->C, sizeof(cplx) * (size_t)n * q.n_eig,
+                          cudaMemcpyDeviceToDevice, p->st));
+  p->stage[iq] = ST_BASIS;
+  return RPA_OK;
+}
+
+rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, double* trace_out) {
+  rpa_status s = check_iq(p, iq);
+  if (s != RPA_OK) return s;
+  if (p->stage[iq] < ST_BASIS)
+    return fail(p, RPA_ESTATE, "rpa_subspace_basis(%d) must come first", iq);
+  const rpa_qpoint& q = *qp(p, iq);
+  const void* A;
+  int dt;
+  s = matrix_a(p, iq, &A, &dt);
+  if (s != RPA_OK) return s;
+  const int n_vc = q.n_v * q.n_c, E = q.n_eig, F = q.n_freq;
+  const double scale = -1.0 / q.omega_cell;
+  const double* om = p->omega + (size_t)iq * p->max_freq;
+  if (p->opt.precision == RPA_MIXED) {
+    s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err);
+    if (s != RPA_OK) return s;
+    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err);
+    if (s != RPA_OK) return s;
+  } else {
+    CU(p, rpa::launch_project_fp64(A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st));
+    CU(p, rpa::launch_chis_fp64(p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st));
+  }
+  CU(p, rpa::launch_mirror_hermitian(p->chis, E, F, p->st));
+  CU(p, rpa::launch_trace(p->mt, E, n_vc, p->delta, om, F, scale, p->w, p->trace, p->st));
+  if (mt_out)
+    CU(p, cudaMemcpyAsync(mt_out, p->mt, sizeof(cplx) * (size_t)E * n_vc, cudaMemcpyDeviceToDevice,
+                          p->st));
+  if (chis_out)
+    CU(p, cudaMemcpyAsync(chis_out, p->chis, sizeof(cplx) * (size_t)F * E * E,
+                          cudaMemcpyDeviceToDevice, p->st));
+  if (trace_out)
+    CU(p, cudaMemcpyAsync(trace_out, p->trace, sizeof(double) * F, cudaMemcpyDeviceToDevice,
+                          p->st));
+  p->stage[iq] = ST_FREQ;
+  return RPA_OK;
+}
+
+static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_out) {
+  const rpa_qpoint& q = *qp(p, iq);
+  const int E = q.n_eig, F = q.n_freq;
+  const double* wt = p->weight + (size_t)iq * p->max_freq;
+  CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
+  if (p->opt.energy_route == RPA_ROUTE_CHOLESKY) {
+    CU(p, rpa::launch_cholesky_logdet(p->chis_work, p->chis, E, F, p->logdet, p->flags + 1,
+                                      p->st));
+    CU(p, rpa::launch_logdet_sum(p->logdet, F, p->trace, wt, p->ec, p->flags + 1, p->st));
+  } else {
+    CU(p, cudaMemcpyAsync(p->chis_work, p->chis, sizeof(cplx) * (size_t)F * E * E,
+                          cudaMemcpyDeviceToDevice, p->st));
+    for (int k = 0; k < F; ++k) {
+      CS(p, cusolverDnXsyevd(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER,
+                             E, CUDA_C_64F, p->chis_work + (size_t)k * E * E, E, CUDA_R_64F,
+                             p->lam + (size_t)k * E, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
+                             p->sol_host, p->sol_host_bytes, p->flags + 2));
+    }
+    CU(p, rpa::launch_logsum(p->lam, E, E, F, p->trace, wt, p->ec, p->flags + 1, p->st));
+    if (lam_out)
+      CU(p, cudaMemcpyAsync(lam_out, p->lam, sizeof(double) * (size_t)F * E,
+                            cudaMemcpyDeviceToDevice, p->st));
+  }
+  int fl[4];
+  CU(p, cudaMemcpyAsync(fl, p->flags, sizeof fl, cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaMemcpyAsync(ec_host, p->ec, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaStreamSynchronize(p->st));
+  if (fl[2] != 0) return fail(p, RPA_EEIG, "Xsyevd info = %d", fl[2]);
+  if (fl[1] != 0)
+    return fail(p, RPA_ENUMERIC, "energy of q-point %d: 1 - lambda <= 0 or non-finite (bits %d)",
+                iq, fl[1]);
+  return RPA_OK;
+}
+
+rpa_status rpa_ecorr(rpa_plan_t p, int iq, double* ec_host, double* lam_out) {
+  if (!p) return RPA_EINVAL;
+  if (!ec_host) return fail(p, RPA_EINVAL, "ec_host is NULL");
+  if (iq == -1) {
+    for (int i = 0; i < p->n_q; ++i) {
+      rpa_status s;
+      if ((s = rpa_chi0_static(p, i, nullptr)) != RPA_OK) return s;
+      if ((s = rpa_subspace_basis(p, i, nullptr, nullptr)) != RPA_OK) return s;
+      if ((s = rpa_chi_freq(p, i, nullptr, nullptr, nullptr)) != RPA_OK) return s;
+      if ((s = energy_one(p, i, ec_host + i, nullptr)) != RPA_OK) return s;
+    }
+    return RPA_OK;
+  }
+  rpa_status s = check_iq(p, iq);
+  if (s != RPA_OK) return s;
+  if (p->stage[iq] < ST_FREQ) return fail(p, RPA_ESTATE, "rpa_chi_freq(%d) must come first", iq);
+  return energy_one(p, iq, ec_host, lam_out);
+}
+
+rpa_status rpa_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,
+                          int dtype, void* stream) {
+  if (!q || !out || !q->miller || !q->qg2) return fail(nullptr, RPA_EINVAL, "NULL argument");
+  if (q->n_g < 1 || nv < 0 || nc < 0 || v0 < 0 || c0 < 0)
+    return fail(nullptr, RPA_EINVAL, "bad generator range");
+  if (dtype != RPA_C128 && dtype != RPA_C64) return fail(nullptr, RPA_EINVAL, "unknown dtype");
+  if ((long)nv * nc == 0) return RPA_OK;
+  cudaError_t e = rpa::launch_generate_m(q, v0, nv, c0, nc, out, dtype, (cudaStream_t)stream);
+  if (e != cudaSuccess)
+    return fail(nullptr, RPA_ECUDA, "generator launch failed: %s", cudaGetErrorString(e));
+  return RPA_OK;
+}
+
+}  // extern "C"

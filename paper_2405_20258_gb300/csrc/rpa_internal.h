@@ -1,0 +1,62 @@
+// Internal declarations shared by the CUDA translation units of librpa.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rpa.h"
+
+namespace rpa {
+
+struct cplx {
+  double re, im;
+};
+
+// ---- FP64 SIMT contractions (rpa_fp64.cu) ---------------------------------
+
+// chi[g][h] (+)= -(1/Omega) sum_vc conj(X[vc,g]) X[vc,h],  X = sf[vc] sv[g] A[vc,g].
+// Upper block-triangle only; zero `chi` first when split_k > 1.
+cudaError_t launch_herk_fp64(const void* A, int a_dtype, int n_vc, int n_g, const double* sf,
+                             const double* sv, double scale, cplx* chi, cudaStream_t st);
+
+// mt[i][vc] = conj(sum_g A[vc][g] B[g][i]), B = [n_g][n_eig].
+cudaError_t launch_project_fp64(const void* A, int a_dtype, int n_vc, int n_g, const cplx* B,
+                                int n_eig, cplx* mt, cudaStream_t st);
+
+// chis[k][i][j] (+)= scale sum_vc f_k(vc) mt[i][vc] conj(mt[j][vc]) for all k; upper triangle.
+cudaError_t launch_chis_fp64(const cplx* mt, int n_eig, int n_vc, const double* delta,
+                             const double* omega, int n_freq, double scale, cplx* chis,
+                             cudaStream_t st);
+
+// Fill the strictly lower triangle of `batch` n x n Hermitian matrices from the upper one,
+// and zero the imaginary part of the diagonal.
+cudaError_t launch_mirror_hermitian(cplx* m, int n, int batch, cudaStream_t st);
+
+// ---- small kernels (rpa_small.cu) -------------------------------------------
+
+cudaError_t launch_prepare_scalars(const double* qg2, int n_g, const double* e_v, int n_v,
+                                   const double* e_c, int n_c, double* sv, double* delta,
+                                   double* sf0, int* bad, cudaStream_t st);
+cudaError_t launch_freq_grid(int n_freq, double s, double* omega, double* weight,
+                             cudaStream_t st);
+// C = conj(U) in canonical gauge; B = sv * C.  U column-major [n_g x n_eig] (ld = ldu).
+cudaError_t launch_gauge(const cplx* U, int ldu, int n_g, int n_eig, const double* sv, cplx* C,
+                         cplx* B, cudaStream_t st);
+// w[vc] = sum_i |mt[i][vc]|^2 ; trace[k] = scale sum_vc f_k(vc) w[vc]
+cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delta,
+                         const double* omega, int n_freq, double scale, double* w,
+                         double* trace, cudaStream_t st);
+// ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam[k][i]) + trace_k]; bad |= 1 if 1 - lam <= 0.
+cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
+                          const double* trace, const double* weight, double* ec, int* bad,
+                          cudaStream_t st);
+// ec = (1/2pi) sum_k weight_k [logdet_k + trace_k]
+cudaError_t launch_logdet_sum(const double* logdet, int n_freq, const double* trace,
+                              const double* weight, double* ec, int* bad, cudaStream_t st);
+// Batched in-place Cholesky of I - chis[k] and logdet[k] = 2 sum ln L_ii.
+cudaError_t launch_cholesky_logdet(cplx* work, const cplx* chis, int n, int batch,
+                                   double* logdet, int* bad, cudaStream_t st);
+cudaError_t launch_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,
+                              int dtype, cudaStream_t st);
+
+}  // namespace rpa

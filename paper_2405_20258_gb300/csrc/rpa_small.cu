@@ -1,0 +1,367 @@
+// Small FP64 kernels of the RPA path: per-q scalars, the imaginary-frequency
+// quadrature, eigenvector gauge, the FP64 trace term, the energy reductions,
+// batched Cholesky log-determinants and the counter-based input generator.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "rpa_internal.h"
+
+namespace rpa {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed order for a fixed blockDim); result in every thread.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// sv[g] = sqrt(4 pi / |q+G|^2); delta[vc] = e_c[c] - e_v[v]; sf0[vc] = sqrt(f_vc(0)) = sqrt(4/delta)
+__global__ void prepare_kernel(const double* qg2, int n_g, const double* e_v, int n_v,
+                               const double* e_c, int n_c, double* sv, double* delta,
+                               double* sf0, int* bad) {
+  long n_vc = (long)n_v * n_c;
+  long stride = (long)gridDim.x * blockDim.x;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_g + n_vc; i += stride) {
+    if (i < n_g) {
+      double q = qg2[i];
+      if (!(q > 0.0) || !isfinite(q)) atomicOr(bad, 1);
+      sv[i] = sqrt(4.0 * kPi / q);
+    } else {
+      long vc = i - n_g;
+      int v = (int)(vc / n_c), c = (int)(vc % n_c);
+      double d = e_c[c] - e_v[v];
+      if (!(d > 0.0) || !isfinite(d)) atomicOr(bad, 2);
+      delta[vc] = d;
+      sf0[vc] = sqrt(4.0 / d);
+    }
+  }
+}
+
+// Gauss-Legendre nodes and weights on [-1,1] by Newton's method on P_n, then
+// the map t = (x+1)/2, w = s t/(1-t), weight = (w_GL/2) s/(1-t)^2.
+__global__ void freq_grid_kernel(int n, double s, double* omega, double* weight) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int i = n - k;  // root index, descending in x, so k runs ascending
+  double x = cos(kPi * (i - 0.25) / (n + 0.5));
+  double p0 = 1.0, p1 = x, dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    p0 = 1.0;
+    p1 = x;
+    for (int j = 1; j < n; ++j) {
+      double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (x * p1 - p0) / (x * x - 1.0);
+    double dx = p1 / dp;
+    x -= dx;
+    if (fabs(dx) <= 1e-16) break;
+  }
+  // derivative at the converged node
+  p0 = 1.0;
+  p1 = x;
+  for (int j = 1; j < n; ++j) {
+    double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  dp = n * (x * p1 - p0) / (x * x - 1.0);
+  double wgl = 2.0 / ((1.0 - x * x) * dp * dp);
+  double t = 0.5 * (x + 1.0);
+  double omt = 1.0 - t;
+  omega[k] = s * t / omt;
+  weight[k] = 0.5 * wgl * s / (omt * omt);
+}
+
+// One block per eigenvector column: C = conj(U) with its largest-modulus entry
+// (lowest row on ties) made real positive; B = sv * C.
+__global__ void gauge_kernel(const cplx* U, int ldu, int n_g, int n_eig, const double* sv,
+                             cplx* C, cplx* B) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  const int col = blockIdx.x;
+  const cplx* u = U + (size_t)col * ldu;
+  double best = -1.0;
+  int idx = 0x7fffffff;
+  for (int g = threadIdx.x; g < n_g; g += blockDim.x) {
+    double m = u[g].re * u[g].re + u[g].im * u[g].im;
+    if (m > best) {
+      best = m;
+      idx = g;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ob > best || (ob == best && oi < idx)) {
+      best = ob;
+      idx = oi;
+    }
+  }
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    bv[w] = best;
+    bi[w] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nw = blockDim.x >> 5;
+    for (int j = 1; j < nw; ++j)
+      if (bv[j] > bv[0] || (bv[j] == bv[0] && bi[j] < bi[0])) {
+        bv[0] = bv[j];
+        bi[0] = bi[j];
+      }
+  }
+  __syncthreads();
+  // pivot of C = conj(U[piv]); factor = |p| / p = conj(p)/|p| = U[piv]/|U[piv]|
+  cplx up = u[bi[0]];
+  double r = hypot(up.re, up.im);
+  double fr = r > 0.0 ? up.re / r : 1.0, fi = r > 0.0 ? up.im / r : 0.0;
+  for (int g = threadIdx.x; g < n_g; g += blockDim.x) {
+    double cr = u[g].re, ci = -u[g].im;  // conj(U)
+    double xr = cr * fr - ci * fi, xi = cr * fi + ci * fr;
+    if (g == bi[0]) xi = 0.0;
+    size_t o = (size_t)g * n_eig + col;
+    if (C) C[o] = {xr, xi};
+    B[o] = {sv[g] * xr, sv[g] * xi};
+  }
+}
+
+// w[vc] = sum_i |mt[i][vc]|^2
+__global__ void colnorm_kernel(const cplx* mt, int n_eig, int n_vc, double* w) {
+  int vc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vc >= n_vc) return;
+  double s = 0.0;
+  for (int i = 0; i < n_eig; ++i) {
+    cplx m = mt[(size_t)i * n_vc + vc];
+    s = fma(m.re, m.re, s);
+    s = fma(m.im, m.im, s);
+  }
+  w[vc] = s;
+}
+
+// trace[k] = scale sum_vc f_k(vc) w[vc]; one block per frequency, fixed order.
+__global__ void trace_kernel(const double* w, const double* delta, int n_vc,
+                             const double* omega, double scale, double* trace) {
+  __shared__ double sh[33];
+  const int k = blockIdx.x;
+  const double w2 = omega[k] * omega[k];
+  double s = 0.0;
+  for (int vc = threadIdx.x; vc < n_vc; vc += blockDim.x) {
+    double d = delta[vc];
+    s += 4.0 * d / (d * d + w2) * w[vc];
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) trace[k] = scale * s;
+}
+
+// ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam_ki) + trace_k]
+__global__ void logsum_kernel(const double* lam, int n_eig, int ld, int n_freq,
+                              const double* trace, const double* weight, double* ec, int* bad) {
+  __shared__ double sh[33];
+  double tot = 0.0;
+  for (int k = 0; k < n_freq; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n_eig; i += blockDim.x) {
+      double l = lam[(size_t)k * ld + i];
+      if (!(1.0 - l > 0.0) || !isfinite(l)) atomicOr(bad, 4);
+      s += log1p(-l);
+    }
+    s = block_sum(s, sh);
+    tot += weight[k] * (s + trace[k]);
+  }
+  if (threadIdx.x == 0) {
+    if (!isfinite(tot)) atomicOr(bad, 8);
+    *ec = tot / (2.0 * kPi);
+  }
+}
+
+__global__ void logdet_sum_kernel(const double* logdet, int n_freq, const double* trace,
+                                  const double* weight, double* ec, int* bad) {
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int k = 0; k < n_freq; ++k) tot += weight[k] * (logdet[k] + trace[k]);
+  if (!isfinite(tot)) atomicOr(bad, 8);
+  *ec = tot / (2.0 * kPi);
+}
+
+// One block per matrix: work = I - chis (Hermitian, row-major), right-looking
+// Cholesky of the lower triangle, logdet = 2 sum ln L_jj.
+__global__ void cholesky_logdet_kernel(cplx* work, const cplx* chis, int n, double* logdet,
+                                       int* bad) {
+  __shared__ double piv;
+  cplx* a = work + (size_t)blockIdx.x * n * n;
+  const cplx* x = chis + (size_t)blockIdx.x * n * n;
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    cplx v = x[e];
+    a[e] = {(i == j ? 1.0 : 0.0) - v.re, -v.im};
+  }
+  __syncthreads();
+  double ld = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = a[(size_t)j * n + j].re;
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicOr(bad, 16);
+        d = 1.0;
+      }
+      piv = sqrt(d);
+      a[(size_t)j * n + j] = {piv, 0.0};
+    }
+    __syncthreads();
+    const double p = piv;
+    if (threadIdx.x == 0) ld += 2.0 * log(p);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      cplx& l = a[(size_t)i * n + j];
+      l.re /= p;
+      l.im /= p;
+    }
+    __syncthreads();
+    const int rem = n - j - 1;
+    for (long e = threadIdx.x; e < (long)rem * rem; e += blockDim.x) {
+      int i = j + 1 + (int)(e / rem), m = j + 1 + (int)(e % rem);
+      if (m > i) continue;
+      cplx li = a[(size_t)i * n + j], lm = a[(size_t)m * n + j];
+      cplx& t = a[(size_t)i * n + m];
+      // t -= li * conj(lm)
+      t.re -= li.re * lm.re + li.im * lm.im;
+      t.im -= li.im * lm.re - li.re * lm.im;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) logdet[blockIdx.x] = ld;
+}
+
+// ---- counter-based generator (splitmix64 of Steele, Lea and Flood 2014) ----
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double unit_uniform(uint64_t b) {
+  return ((double)(b >> 11) + 0.5) * 0x1.0p-53;
+}
+
+template <typename T>
+__global__ void generate_m_kernel(int n_g, int iq, unsigned long long seed, const int* miller,
+                                  const double* qg2, int v0, int nv, int c0, int nc, T* out) {
+  long total = (long)nv * nc * n_g;
+  long stride = (long)gridDim.x * blockDim.x;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += stride) {
+    int g = (int)(e % n_g);
+    long vc = e / n_g;
+    uint64_t v = (uint64_t)(v0 + vc / nc), c = (uint64_t)(c0 + vc % nc);
+    const uint64_t bias = 1ull << 20;
+    uint64_t pk = ((uint64_t)(miller[3 * g] + (long)bias) << 42) |
+                  ((uint64_t)(miller[3 * g + 1] + (long)bias) << 21) |
+                  (uint64_t)(miller[3 * g + 2] + (long)bias);
+    uint64_t key = (((uint64_t)iq << 16) + v) << 32 | c;
+    key = splitmix64((uint64_t)seed ^ splitmix64(splitmix64(key) ^ pk));
+    double u0 = unit_uniform(splitmix64(key));
+    double u1 = unit_uniform(splitmix64(key ^ 2ull));
+    double rad = sqrt(-2.0 * log(u0)) / sqrt(2.0);
+    double ang = 2.0 * kPi * u1;
+    double env = exp(-qg2[g] / 8.0);
+    double re = rad * cos(ang) * env, im = rad * sin(ang) * env;
+    if constexpr (sizeof(T) == 8) {
+      out[e] = make_float2((float)re, (float)im);
+    } else {
+      out[e] = make_double2(re, im);
+    }
+  }
+}
+
+inline int grid_for(long n, int bs) {
+  long b = (n + bs - 1) / bs;
+  return (int)(b < 152L * 32 ? (b > 0 ? b : 1) : 152L * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_prepare_scalars(const double* qg2, int n_g, const double* e_v, int n_v,
+                                   const double* e_c, int n_c, double* sv, double* delta,
+                                   double* sf0, int* bad, cudaStream_t st) {
+  long n = n_g + (long)n_v * n_c;
+  prepare_kernel<<<grid_for(n, 256), 256, 0, st>>>(qg2, n_g, e_v, n_v, e_c, n_c, sv, delta, sf0,
+                                                    bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_freq_grid(int n_freq, double s, double* omega, double* weight,
+                             cudaStream_t st) {
+  freq_grid_kernel<<<(n_freq + 63) / 64, 64, 0, st>>>(n_freq, s, omega, weight);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauge(const cplx* U, int ldu, int n_g, int n_eig, const double* sv, cplx* C,
+                         cplx* B, cudaStream_t st) {
+  gauge_kernel<<<n_eig, 256, 0, st>>>(U, ldu, n_g, n_eig, sv, C, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delta,
+                         const double* omega, int n_freq, double scale, double* w,
+                         double* trace, cudaStream_t st) {
+  colnorm_kernel<<<(n_vc + 255) / 256, 256, 0, st>>>(mt, n_eig, n_vc, w);
+  trace_kernel<<<n_freq, 1024, 0, st>>>(w, delta, n_vc, omega, scale, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
+                          const double* trace, const double* weight, double* ec, int* bad,
+                          cudaStream_t st) {
+  logsum_kernel<<<1, 256, 0, st>>>(lam, n_eig, ld_lam, n_freq, trace, weight, ec, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logdet_sum(const double* logdet, int n_freq, const double* trace,
+                              const double* weight, double* ec, int* bad, cudaStream_t st) {
+  logdet_sum_kernel<<<1, 32, 0, st>>>(logdet, n_freq, trace, weight, ec, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_logdet(cplx* work, const cplx* chis, int n, int batch,
+                                   double* logdet, int* bad, cudaStream_t st) {
+  cholesky_logdet_kernel<<<batch, 512, 0, st>>>(work, chis, n, logdet, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,
+                              int dtype, cudaStream_t st) {
+  long n = (long)nv * nc * q->n_g;
+  if (dtype == RPA_C64)
+    generate_m_kernel<float2><<<grid_for(n, 256), 256, 0, st>>>(
+        q->n_g, q->iq, q->seed, q->miller, q->qg2, v0, nv, c0, nc, (float2*)out);
+  else
+    generate_m_kernel<double2><<<grid_for(n, 256), 256, 0, st>>>(
+        q->n_g, q->iq, q->seed, q->miller, q->qg2, v0, nv, c0, nc, (double2*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace rpa

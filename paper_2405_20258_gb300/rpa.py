@@ -1,0 +1,245 @@
+"""Thin ctypes binding of ``librpa.so`` (the C ABI declared in include/rpa.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream.  If the library is
+missing this module raises on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librpa.so")
+
+RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_EEIG, RPA_ENUMERIC, RPA_ETIMEOUT, RPA_ESTATE = range(8)
+RPA_FP64, RPA_MIXED = 0, 1
+RPA_ROUTE_EIG, RPA_ROUTE_CHOLESKY = 0, 1
+RPA_C128, RPA_C64 = 0, 1
+
+EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
+            "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
+            "rpa_plan_frequencies", "rpa_generate_m", "rpa_version")
+
+
+class rpa_qpoint(ctypes.Structure):
+    _fields_ = [("n_g", ctypes.c_int), ("n_v", ctypes.c_int), ("n_c", ctypes.c_int),
+                ("n_eig", ctypes.c_int), ("n_freq", ctypes.c_int),
+                ("omega_cell", ctypes.c_double),
+                ("qg2", ctypes.c_void_p), ("e_v", ctypes.c_void_p), ("e_c", ctypes.c_void_p),
+                ("m", ctypes.c_void_p), ("m_dtype", ctypes.c_int), ("iq", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("miller", ctypes.c_void_p)]
+
+
+class rpa_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("energy_route", ctypes.c_int),
+                ("omega_scale", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+
+
+class RPAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+_STATUS = {0: "RPA_OK", 1: "RPA_EINVAL", 2: "RPA_ENOMEM", 3: "RPA_ECUDA", 4: "RPA_EEIG",
+           5: "RPA_ENUMERIC", 6: "RPA_ETIMEOUT", 7: "RPA_ESTATE"}
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librpa.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librpa.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "rpa_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(rpa_qpoint), i,
+                             ctypes.POINTER(rpa_options), vp], i),
+        "rpa_plan_destroy": ([vp], i),
+        "rpa_last_error": ([vp], ctypes.c_char_p),
+        "rpa_status_string": ([i], ctypes.c_char_p),
+        "rpa_chi0_static": ([vp, i, vp], i),
+        "rpa_subspace_basis": ([vp, i, vp, vp], i),
+        "rpa_chi_freq": ([vp, i, vp, vp, vp], i),
+        "rpa_ecorr": ([vp, i, vp, vp], i),
+        "rpa_plan_frequencies": ([vp, i, vp, vp], i),
+        "rpa_generate_m": ([ctypes.POINTER(rpa_qpoint), i, i, i, i, vp, i, vp], i),
+        "rpa_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(status, plan=None):
+    if status != RPA_OK:
+        msg = load().rpa_last_error(plan).decode()
+        raise RPAError(status, msg)
+
+
+@dataclass
+class DeviceQPoint:
+    """Device arrays of one q-point (torch tensors kept alive by the plan)."""
+    qg2: object
+    e_v: object
+    e_c: object
+    m: object            # complex128/complex64 [n_v*n_c, n_g] or None
+    n_eig: int
+    n_freq: int
+    omega_cell: float = 1000.0
+    miller: object = None
+    seed: int = 0
+    iq: int = 0
+    m_dtype: int = RPA_C128
+
+    def struct(self):
+        import torch
+        n_g, n_v, n_c = self.qg2.shape[0], self.e_v.shape[0], self.e_c.shape[0]
+        dt = self.m_dtype
+        if self.m is not None:
+            dt = RPA_C64 if self.m.dtype == torch.complex64 else RPA_C128
+        return rpa_qpoint(n_g, n_v, n_c, self.n_eig, self.n_freq, float(self.omega_cell),
+                          _ptr(self.qg2), _ptr(self.e_v), _ptr(self.e_c), _ptr(self.m), dt,
+                          int(self.iq), int(self.seed), _ptr(self.miller))
+
+
+def device_qpoint(qp, n_eig, n_freq, A=None, device="cuda", m_dtype=None, generate=False):
+    """Upload a host ``inputs.QPoint`` (and optionally A) to the device."""
+    import torch
+    dq = DeviceQPoint(
+        qg2=torch.as_tensor(qp.qg2, dtype=torch.float64, device=device),
+        e_v=torch.as_tensor(qp.e_v, dtype=torch.float64, device=device),
+        e_c=torch.as_tensor(qp.e_c, dtype=torch.float64, device=device),
+        m=None if A is None else torch.as_tensor(A, device=device),
+        n_eig=n_eig, n_freq=n_freq, omega_cell=qp.omega_cell,
+        miller=torch.as_tensor(np.ascontiguousarray(qp.miller, dtype=np.int32), device=device),
+        seed=qp.seed, iq=qp.iq)
+    if m_dtype is not None:
+        dq.m_dtype = m_dtype
+    return dq
+
+
+class Plan:
+    """Owner of an ``rpa_plan_t``; methods mirror the C entry points."""
+
+    def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
+                 stream=None):
+        lib = load()
+        self.qpoints = list(qpoints)
+        self._structs = (rpa_qpoint * len(self.qpoints))(*[q.struct() for q in self.qpoints])
+        opt = rpa_options(precision, energy_route, omega_scale)
+        self._stream = _stream(stream)
+        h = ctypes.c_void_p()
+        st = lib.rpa_plan_create(ctypes.byref(h), self._structs, len(self.qpoints), ctypes.byref(opt),
+                                 self._stream)
+        if st != RPA_OK:
+            raise RPAError(st, lib.rpa_last_error(None).decode())
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rpa_plan_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def chi0_static(self, iq, chi_out=None):
+        _check(load().rpa_chi0_static(self.handle, iq, _ptr(chi_out)), self.handle)
+
+    def subspace_basis(self, iq, lam_out=None, c_out=None):
+        _check(load().rpa_subspace_basis(self.handle, iq, _ptr(lam_out), _ptr(c_out)), self.handle)
+
+    def chi_freq(self, iq, mt_out=None, chis_out=None, trace_out=None):
+        _check(load().rpa_chi_freq(self.handle, iq, _ptr(mt_out), _ptr(chis_out), _ptr(trace_out)),
+               self.handle)
+
+    def ecorr(self, iq, lam_out=None):
+        n = len(self.qpoints) if iq == -1 else 1
+        out = (ctypes.c_double * n)()
+        _check(load().rpa_ecorr(self.handle, iq, ctypes.cast(out, ctypes.c_void_p), _ptr(lam_out)),
+               self.handle)
+        return list(out) if iq == -1 else out[0]
+
+    def frequencies(self, iq):
+        n = self.qpoints[iq].n_freq
+        om = np.zeros(n)
+        wt = np.zeros(n)
+        _check(load().rpa_plan_frequencies(self.handle, iq, om.ctypes.data_as(ctypes.c_void_p),
+                                           wt.ctypes.data_as(ctypes.c_void_p)), self.handle)
+        return om, wt
+
+    def run(self, iq=0):
+        """All stages of one q-point; returns E_c (Ha)."""
+        self.chi0_static(iq)
+        self.subspace_basis(iq)
+        self.chi_freq(iq)
+        return self.ecorr(iq)
+
+
+# names of the C ABI, for callers that prefer the flat form
+def rpa_plan_create(qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
+                    stream=None):
+    return Plan(qpoints, precision, energy_route, omega_scale, stream)
+
+
+def rpa_chi0_static(plan, iq, chi_out=None):
+    plan.chi0_static(iq, chi_out)
+
+
+def rpa_subspace_basis(plan, iq, lam_out=None, c_out=None):
+    plan.subspace_basis(iq, lam_out, c_out)
+
+
+def rpa_chi_freq(plan, iq, mt_out=None, chis_out=None, trace_out=None):
+    plan.chi_freq(iq, mt_out, chis_out, trace_out)
+
+
+def rpa_ecorr(plan, iq, lam_out=None):
+    return plan.ecorr(iq, lam_out)
+
+
+def rpa_plan_destroy(plan):
+    plan.close()
+
+
+def rpa_generate_m(dq: DeviceQPoint, v0, nv, c0, nc, out, stream=None):
+    """Draw A[v0:v0+nv, c0:c0+nc, :] on the device into ``out`` (complex128 or complex64)."""
+    import torch
+    dt = RPA_C64 if out.dtype == torch.complex64 else RPA_C128
+    s = dq.struct()
+    _check(load().rpa_generate_m(ctypes.byref(s), v0, nv, c0, nc, _ptr(out), dt, _stream(stream)))
+
+
+def rpa_version():
+    return load().rpa_version().decode()
