@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the static-subspace RPA hot path on GB300.
+
+One step = every stage of one q-point through the C ABI: chi~(0), FP64
+eigensolve and subspace basis, projection M~, chi_s(iw_k) for all k, the FP64
+trace term, eigenvalues of every chi_s(iw_k) and E_c.  Workload: one q-point
+with N_G=4000, N_v=128, N_c=2000 (N_vc=256000), N_eig=400, 32 frequencies,
+synthetic splitmix64 matrix elements (16.4 GB complex128, larger than L2).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample, scaled to the workload).
+Multi-GPU (torchrun): every rank runs its own q-point; no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "q-points/sec and contraction TFLOP/s, mixed vs FP64 path at |dE_c|<=1e-6 Ha"
+WORKLOADS = {
+    "qpoint-4000": dict(n_g=4000, n_v=128, n_c=2000, n_eig=400, n_freq=32),
+    "qpoint-400": dict(n_g=400, n_v=16, n_c=200, n_eig=40, n_freq=16),
+}
+# FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
+FP64_OVER_BF16 = 1.25 / 2250.0
+
+
+def flops(w):
+    n_vc = w["n_v"] * w["n_c"]
+    return dict(chi0=4.0 * w["n_g"] ** 2 * n_vc,
+                proj=8.0 * w["n_eig"] * w["n_g"] * n_vc,
+                chis=4.0 * w["n_eig"] ** 2 * n_vc * w["n_freq"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus = (bus_id or "").lower()
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(", ") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 9]
+        if not rows:
+            return None
+        tail = lambda b: b.strip().lower()[-7:]
+        mine = [r for r in rows if self.bus and tail(r[1]) == tail(self.bus)]
+        if not mine:
+            mine = [r for r in rows if r[0] == rows[0][0]]
+        sm = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in mine if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in mine for i in range(4) if r[6 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(mine)}
+
+
+def setup_dist(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x, dist, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reported baseline; also the --impl reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, n_v_sample=4):
+    """Time the FP64 oracle stage by stage on a sample of the workload: full N_G,
+    N_eig and frequencies, n_v_sample of the N_v valence bands.  Stages linear in
+    N_vc are scaled by N_v / n_v_sample; the two eigen-stages are not.
+    Returns (seconds per full q-point, description, cores)."""
+    import numpy as np
+    import oracle.rpa_oracle as orc
+    from paper_2405_20258_gb300 import inputs
+    qp = inputs.make_qpoint(w["n_g"], n_v_sample, w["n_c"])
+    A = inputs.matrix_elements(qp)
+    delta = orc.transition_energies(qp.e_v, qp.e_c)
+    t = {}
+    t0 = time.perf_counter()
+    chit = orc.chi_tilde(A, qp.qg2, delta, 0.0, qp.omega_cell)
+    t["chi0"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam0, C, _ = orc.subspace_basis(chit, w["n_eig"])
+    t["eig0"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Mt = orc.project(A, qp.qg2, C)
+    t["proj"] = time.perf_counter() - t0
+    omega, weight = orc.frequency_grid(w["n_freq"])
+    t["chis"] = t["eigs"] = 0.0
+    for k in range(w["n_freq"]):
+        t0 = time.perf_counter()
+        cs = orc.chi_s(Mt, delta, omega[k], qp.omega_cell)
+        orc.trace_term(Mt, delta, omega[k], qp.omega_cell)
+        t1 = time.perf_counter()
+        np.linalg.eigvalsh(0.5 * (cs + cs.conj().T))
+        t["eigs"] += time.perf_counter() - t1
+        t["chis"] += t1 - t0
+    scale = w["n_v"] / n_v_sample
+    est = (t["chi0"] + t["proj"] + t["chis"]) * scale + t["eig0"] + t["eigs"]
+    measured = sum(t.values())
+    desc = ("oracle stages on N_G=%d, N_v=%d of %d, N_c=%d, N_eig=%d, %d freq (%.1f s measured); "
+            "vc-linear stages scaled x%g, eigensolves unscaled" %
+            (w["n_g"], n_v_sample, w["n_v"], w["n_c"], w["n_eig"], w["n_freq"], measured, scale))
+    return est, desc, os.cpu_count(), t
+
+
+def reference_arm(args, w, rank, dist):
+    if rank != 0:
+        return
+    steps = []
+    t_all = None
+    for s in range(args.warmup + args.steps):
+        est, desc, cores, t = oracle_sample(w, n_v_sample=2)
+        if s >= args.warmup:
+            steps.append(est)
+    sec = statistics.mean(steps)
+    val = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "q-points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **w},
+            "cpu_baseline": {"value": val, "unit": "q-points/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": val, "unit": "q-points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    rank, world, local, dist = setup_dist(args)
+    if args.impl == "reference":
+        reference_arm(args, w, rank, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_2405_20258_gb300 import inputs, rpa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rpa.load()
+    precision = rpa.RPA_MIXED if args.precision == "mixed" else rpa.RPA_FP64
+    route = rpa.RPA_ROUTE_CHOLESKY if args.route == "cholesky" else rpa.RPA_ROUTE_EIG
+    stream = torch.cuda.Stream(device=dev)
+    # each rank its own q-point of the 4x4x4 grid (weak scaling, no exchange)
+    iq = rank % 64
+    qp = inputs.make_qpoint(w["n_g"], w["n_v"], w["n_c"], iq=iq,
+                            q_twentieths=(1, 0, 0) if iq == 0 else inputs.qgrid_4x4x4()[iq])
+    n_vc = w["n_v"] * w["n_c"]
+    dq = rpa.device_qpoint(qp, w["n_eig"], w["n_freq"], device=dev)
+    A = torch.empty((n_vc, w["n_g"]), dtype=torch.complex128, device=dev)
+    with torch.cuda.stream(stream):
+        rpa.rpa_generate_m(dq, 0, w["n_v"], 0, w["n_c"], A, stream=stream)
+    stream.synchronize()
+    dq.m = A
+    plan = rpa.Plan([dq], precision=precision, energy_route=route, stream=stream, timing=True)
+    fl = flops(w)
+    fl_total = sum(fl.values())
+
+    # warm-up
+    ecs = []
+    for _ in range(args.warmup):
+        ecs.append(plan.run(0))
+    plan.timings()
+    torch.cuda.synchronize()
+    barrier(dist)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(bus) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ecs.append(plan.run(0))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    stage_ms, launches = plan.timings()
+    t_dev = max_over_ranks(t_dev, dist, dev)
+    sec_per_step = t_dev / args.steps
+    value = world * args.steps / t_dev
+    contraction_s = (stage_ms["chi0"] + stage_ms["proj"] + stage_ms["chis"]) / 1e3 / args.steps
+    contraction_tflops = fl_total / contraction_s / 1e12
+
+    # roofline of the dominant kernel (largest stage share among the contractions)
+    pk, pk_kind = peaks()
+    shares = {k: v / sum(stage_ms.values()) for k, v in stage_ms.items()}
+    dom = max(("chi0", "proj", "chis"), key=lambda k: stage_ms[k])
+    dom_s = stage_ms[dom] / 1e3 / args.steps
+    if precision == rpa.RPA_FP64:
+        peak = pk["bf16_tflops_sustained"] * FP64_OVER_BF16
+        peak_note = "%s bf16 sustained x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind
+    else:
+        peak = pk["bf16_tflops_sustained"]
+        peak_note = "%s bf16 sustained" % pk_kind
+    achieved = fl[dom] / dom_s / 1e12
+    roofline = {"bound": "tensor" if precision == rpa.RPA_MIXED else "alu", "kernel": dom,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": peak_note, "traffic": None,
+                "algorithmic_flops_per_launch": fl[dom]}
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back
+    e2e = None
+    if not args.no_e2e:
+        host_A = torch.empty_like(A, device="cpu").pin_memory()
+        host_A.copy_(A)
+        host_small = [t.cpu().pin_memory() for t in (dq.qg2, dq.e_v, dq.e_c)]
+        dev_small = [dq.qg2, dq.e_v, dq.e_c]
+        h2d = host_A.numel() * 16 + sum(t.numel() * t.element_size() for t in host_small)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                A.copy_(host_A, non_blocking=True)
+                for d_, h_ in zip(dev_small, host_small):
+                    d_.copy_(h_, non_blocking=True)
+            return plan.run(0)  # returns E_c to the host (8 bytes)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
+               "wall_s": time.perf_counter() - t0}
+        plan.timings()
+        del host_A
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, desc, cores, _ = oracle_sample(w)
+        cpu = {"value": 1.0 / est, "unit": "q-points/s", "cores": cores, "kind": "oracle",
+               "sample": desc}
+
+    clocks = clk.summary()
+    spread = max(ecs) - min(ecs)
+    line = {
+        "metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == rpa.RPA_FP64 else "bf16",
+        "data": "synthetic (splitmix64 matrix elements drawn on the device)",
+        "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
+                   "energy_route": args.route,
+                   "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * 16 / 1e9),
+                   "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
+        "contraction_tflops": contraction_tflops,
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "stage_share": shares,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "ec_ha": ecs[-1], "ec_spread_over_steps": spread,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,8 +86,22 @@ typedef struct {
   int precision;           /* rpa_precision                                          */
   int energy_route;        /* rpa_energy_route                                       */
   double omega_scale;      /* s of the frequency map w = s t/(1-t); <= 0 means 0.5 Ha */
-  int reserved[8];         /* zero                                                   */
+  int timing;              /* nonzero: record CUDA events around every stage kernel  */
+  int reserved[7];         /* zero                                                   */
 } rpa_options;
+
+/* Stage timers of rpa_plan_timings. */
+typedef enum {
+  RPA_T_CHI0 = 0,   /* chi~(0) contraction (incl. operand preparation on the mixed path) */
+  RPA_T_EIG0 = 1,   /* FP64 eigensolve of chi~(0) and gauge fixing                       */
+  RPA_T_PROJ = 2,   /* projection M~                                                     */
+  RPA_T_CHIS = 3,   /* chi_s(w_k) contraction for every k                                */
+  RPA_T_TRACE = 4,  /* FP64 trace term                                                   */
+  RPA_T_EIGS = 5,   /* eigenvalues (or Cholesky) of every chi_s(w_k)                     */
+  RPA_T_ENERGY = 6, /* final log-sum and quadrature                                      */
+  RPA_T_OTHER = 7,  /* scalars, mirrors, copies                                          */
+  RPA_N_TIMERS = 8
+} rpa_timer;
 
 typedef struct rpa_plan_s* rpa_plan_t;
 
@@ -141,6 +155,13 @@ rpa_status rpa_plan_frequencies(rpa_plan_t plan, int iq, double* omega_host, dou
  * Uses q->seed, q->iq, q->miller, q->qg2 (device).  Asynchronous on stream. */
 rpa_status rpa_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc,
                           void* out, int dtype, void* stream);
+
+/* Device time per stage (ms) accumulated since the previous call, from CUDA
+ * events on the plan's stream (plans created with opt->timing != 0; zeros
+ * otherwise), and the number of kernels the library itself launched since the
+ * previous call (library solvers' internal kernels not counted).  Synchronises
+ * the stream.  times_ms: host [RPA_N_TIMERS] or NULL; launches: host or NULL. */
+rpa_status rpa_plan_timings(rpa_plan_t plan, double* times_ms, long long* launches);
 
 /* Library version string. */
 const char* rpa_version(void);

@@ -55,6 +55,14 @@ struct rpa_plan_s {
   void* sol_host = nullptr;
   size_t sol_host_bytes = 0;
   rpa::tc::Workspace tcw;     // tensor-core path workspace
+  // stage timers (CUDA events on the plan stream) and the library's launch count
+  struct Pending {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Pending> pending;
+  long long launches = 0;
 };
 
 namespace {
@@ -102,6 +110,11 @@ rpa_status dalloc(rpa_plan_t p, T** ptr, size_t count) {
 
 void free_plan(rpa_plan_t p) {
   if (!p) return;
+  for (auto& e : p->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->omega, p->weight, p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev};
@@ -113,6 +126,40 @@ void free_plan(rpa_plan_t p) {
   if (p->sol) cusolverDnDestroy(p->sol);
   delete p;
 }
+
+cudaEvent_t get_event(rpa_plan_t p) {
+  if (!p->ev_pool.empty()) {
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records a pair of events around one stage when the plan times its stages.
+struct StageTimer {
+  rpa_plan_t p;
+  int id;
+  cudaEvent_t a = nullptr;
+  StageTimer(rpa_plan_t p_, int id_) : p(p_), id(id_) {
+    if (p->opt.timing && (a = get_event(p))) cudaEventRecord(a, p->st);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    cudaEvent_t b = get_event(p);
+    if (!b) {
+      p->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, p->st);
+    p->pending.push_back({id, a, b});
+  }
+};
 
 rpa_status check_qpoint(const rpa_qpoint& q, int i) {
   auto bad = [&](const char* what) {
@@ -147,7 +194,9 @@ rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
     return RPA_OK;
   }
   if (p->gen_iq != iq) {
+    StageTimer t(p, RPA_T_OTHER);
     CU(p, rpa::launch_generate_m(&q, 0, q.n_v, 0, q.n_c, p->gen_a, q.m_dtype, p->st));
+    p->launches += 1;
     p->gen_iq = iq;
   }
   *a = p->gen_a;
@@ -158,8 +207,12 @@ rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
 rpa_status prepare(rpa_plan_t p, int iq) {
   const rpa_qpoint& q = p->q[iq];
   CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
-  CU(p, rpa::launch_prepare_scalars(q.qg2, q.n_g, q.e_v, q.n_v, q.e_c, q.n_c, p->sv, p->delta,
-                                    p->sf0, p->flags, p->st));
+  {
+    StageTimer t(p, RPA_T_OTHER);
+    CU(p, rpa::launch_prepare_scalars(q.qg2, q.n_g, q.e_v, q.n_v, q.e_c, q.n_c, p->sv, p->delta,
+                                      p->sf0, p->flags, p->st));
+    p->launches += 1;
+  }
   int h = 0;
   CU(p, cudaMemcpyAsync(&h, p->flags, sizeof(int), cudaMemcpyDeviceToHost, p->st));
   CU(p, cudaStreamSynchronize(p->st));
@@ -362,14 +415,24 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   if (s != RPA_OK) return s;
   const long n_vc = (long)q.n_v * q.n_c;
   const double scale = -1.0 / q.omega_cell;
-  if (p->opt.precision == RPA_MIXED) {
-    s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
-                      p->err);
-    if (s != RPA_OK) return s;
-  } else {
-    CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
+  {
+    StageTimer t(p, RPA_T_CHI0);
+    if (p->opt.precision == RPA_MIXED) {
+      int nl = 0;
+      s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
+                        p->err, &nl);
+      p->launches += nl;
+      if (s != RPA_OK) return s;
+    } else {
+      CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
+      p->launches += 1;
+    }
   }
-  CU(p, rpa::launch_mirror_hermitian(p->chi, q.n_g, 1, p->st));
+  {
+    StageTimer t(p, RPA_T_OTHER);
+    CU(p, rpa::launch_mirror_hermitian(p->chi, q.n_g, 1, p->st));
+    p->launches += 1;
+  }
   if (chi_out)
     CU(p, cudaMemcpyAsync(chi_out, p->chi, sizeof(cplx) * (size_t)q.n_g * q.n_g,
                           cudaMemcpyDeviceToDevice, p->st));
@@ -383,6 +446,7 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   if (p->stage[iq] < ST_CHI0) return fail(p, RPA_ESTATE, "rpa_chi0_static(%d) must come first", iq);
   const rpa_qpoint& q = *qp(p, iq);
   const int n = q.n_g;
+  StageTimer timer(p, RPA_T_EIG0);
   CU(p, cudaMemcpyAsync(p->chi_work, p->chi, sizeof(cplx) * (size_t)n * n,
                         cudaMemcpyDeviceToDevice, p->st));
   double vl = 0.0, vu = 0.0;
@@ -401,6 +465,7 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   if (meig != q.n_eig) return fail(p, RPA_EEIG, "Xsyevdx returned %lld of %d eigenpairs",
                                    (long long)meig, q.n_eig);
   CU(p, rpa::launch_gauge(p->chi_work, n, n, q.n_eig, p->sv, p->C, p->B, p->st));
+  p->launches += 1;
   if (lambda_out)
     CU(p, cudaMemcpyAsync(lambda_out, p->lam_all, sizeof(double) * q.n_eig,
                           cudaMemcpyDeviceToDevice, p->st));
@@ -425,16 +490,39 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   const double scale = -1.0 / q.omega_cell;
   const double* om = p->omega + (size_t)iq * p->max_freq;
   if (p->opt.precision == RPA_MIXED) {
-    s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err);
-    if (s != RPA_OK) return s;
-    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err);
-    if (s != RPA_OK) return s;
+    int nl = 0;
+    {
+      StageTimer t(p, RPA_T_PROJ);
+      s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
+      if (s != RPA_OK) return s;
+    }
+    {
+      StageTimer t(p, RPA_T_CHIS);
+      s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err,
+                        &nl);
+      if (s != RPA_OK) return s;
+    }
+    p->launches += nl;
   } else {
-    CU(p, rpa::launch_project_fp64(A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st));
-    CU(p, rpa::launch_chis_fp64(p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st));
+    {
+      StageTimer t(p, RPA_T_PROJ);
+      CU(p, rpa::launch_project_fp64(A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st));
+    }
+    {
+      StageTimer t(p, RPA_T_CHIS);
+      CU(p, rpa::launch_chis_fp64(p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st));
+    }
+    p->launches += 2;
   }
-  CU(p, rpa::launch_mirror_hermitian(p->chis, E, F, p->st));
-  CU(p, rpa::launch_trace(p->mt, E, n_vc, p->delta, om, F, scale, p->w, p->trace, p->st));
+  {
+    StageTimer t(p, RPA_T_OTHER);
+    CU(p, rpa::launch_mirror_hermitian(p->chis, E, F, p->st));
+  }
+  {
+    StageTimer t(p, RPA_T_TRACE);
+    CU(p, rpa::launch_trace(p->mt, E, n_vc, p->delta, om, F, scale, p->w, p->trace, p->st));
+  }
+  p->launches += 3;
   if (mt_out)
     CU(p, cudaMemcpyAsync(mt_out, p->mt, sizeof(cplx) * (size_t)E * n_vc, cudaMemcpyDeviceToDevice,
                           p->st));
@@ -454,19 +542,32 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
   const double* wt = p->weight + (size_t)iq * p->max_freq;
   CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
   if (p->opt.energy_route == RPA_ROUTE_CHOLESKY) {
-    CU(p, rpa::launch_cholesky_logdet(p->chis_work, p->chis, E, F, p->logdet, p->flags + 1,
-                                      p->st));
-    CU(p, rpa::launch_logdet_sum(p->logdet, F, p->trace, wt, p->ec, p->flags + 1, p->st));
-  } else {
-    CU(p, cudaMemcpyAsync(p->chis_work, p->chis, sizeof(cplx) * (size_t)F * E * E,
-                          cudaMemcpyDeviceToDevice, p->st));
-    for (int k = 0; k < F; ++k) {
-      CS(p, cusolverDnXsyevd(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER,
-                             E, CUDA_C_64F, p->chis_work + (size_t)k * E * E, E, CUDA_R_64F,
-                             p->lam + (size_t)k * E, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
-                             p->sol_host, p->sol_host_bytes, p->flags + 2));
+    {
+      StageTimer t(p, RPA_T_EIGS);
+      CU(p, rpa::launch_cholesky_logdet(p->chis_work, p->chis, E, F, p->logdet, p->flags + 1,
+                                        p->st));
     }
-    CU(p, rpa::launch_logsum(p->lam, E, E, F, p->trace, wt, p->ec, p->flags + 1, p->st));
+    StageTimer t(p, RPA_T_ENERGY);
+    CU(p, rpa::launch_logdet_sum(p->logdet, F, p->trace, wt, p->ec, p->flags + 1, p->st));
+    p->launches += 2;
+  } else {
+    {
+      StageTimer t(p, RPA_T_EIGS);
+      CU(p, cudaMemcpyAsync(p->chis_work, p->chis, sizeof(cplx) * (size_t)F * E * E,
+                            cudaMemcpyDeviceToDevice, p->st));
+      for (int k = 0; k < F; ++k) {
+        CS(p, cusolverDnXsyevd(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR,
+                               CUBLAS_FILL_MODE_LOWER, E, CUDA_C_64F,
+                               p->chis_work + (size_t)k * E * E, E, CUDA_R_64F,
+                               p->lam + (size_t)k * E, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
+                               p->sol_host, p->sol_host_bytes, p->flags + 2));
+      }
+    }
+    {
+      StageTimer t(p, RPA_T_ENERGY);
+      CU(p, rpa::launch_logsum(p->lam, E, E, F, p->trace, wt, p->ec, p->flags + 1, p->st));
+    }
+    p->launches += 1;
     if (lam_out)
       CU(p, cudaMemcpyAsync(lam_out, p->lam, sizeof(double) * (size_t)F * E,
                             cudaMemcpyDeviceToDevice, p->st));
@@ -499,6 +600,25 @@ rpa_status rpa_ecorr(rpa_plan_t p, int iq, double* ec_host, double* lam_out) {
   if (s != RPA_OK) return s;
   if (p->stage[iq] < ST_FREQ) return fail(p, RPA_ESTATE, "rpa_chi_freq(%d) must come first", iq);
   return energy_one(p, iq, ec_host, lam_out);
+}
+
+rpa_status rpa_plan_timings(rpa_plan_t p, double* times_ms, long long* launches) {
+  if (!p) return RPA_EINVAL;
+  CU(p, cudaStreamSynchronize(p->st));
+  double acc[RPA_N_TIMERS] = {0};
+  for (auto& e : p->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess && e.id >= 0 && e.id < RPA_N_TIMERS)
+      acc[e.id] += ms;
+    p->ev_pool.push_back(e.a);
+    p->ev_pool.push_back(e.b);
+  }
+  p->pending.clear();
+  if (times_ms)
+    for (int i = 0; i < RPA_N_TIMERS; ++i) times_ms[i] = acc[i];
+  if (launches) *launches = p->launches;
+  p->launches = 0;
+  return RPA_OK;
 }
 
 rpa_status rpa_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,

@@ -18,17 +18,17 @@ void free_workspace(Workspace& w) {
 }
 
 rpa_status chi0(Workspace&, const void*, int, int, int, const double*, const double*, double,
-                cplx*, cudaStream_t, std::string& err) {
+                cplx*, cudaStream_t, std::string& err, int*) {
   err = "mixed-precision path not available";
   return RPA_EINVAL;
 }
 rpa_status project(Workspace&, const void*, int, int, int, const cplx*, int, cplx*, cudaStream_t,
-                   std::string& err) {
+                   std::string& err, int*) {
   err = "mixed-precision path not available";
   return RPA_EINVAL;
 }
 rpa_status chis(Workspace&, const cplx*, int, int, const double*, const double*, int, double,
-                cplx*, cudaStream_t, std::string& err) {
+                cplx*, cudaStream_t, std::string& err, int*) {
   err = "mixed-precision path not available";
   return RPA_EINVAL;
 }

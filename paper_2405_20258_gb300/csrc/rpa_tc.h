@@ -25,12 +25,12 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
 void free_workspace(Workspace& w);
 
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err);
+                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err, int* launches);
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
-                   int n_eig, cplx* mt, cudaStream_t st, std::string& err);
+                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
                 const double* omega, int n_freq, double scale, cplx* out, cudaStream_t st,
-                std::string& err);
+                std::string& err, int* launches);
 
 }  // namespace tc
 }  // namespace rpa

@@ -22,7 +22,8 @@ RPA_C128, RPA_C64 = 0, 1
 
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
-            "rpa_plan_frequencies", "rpa_generate_m", "rpa_version")
+            "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings")
+TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other")
 
 
 class rpa_qpoint(ctypes.Structure):
@@ -36,7 +37,8 @@ class rpa_qpoint(ctypes.Structure):
 
 class rpa_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("energy_route", ctypes.c_int),
-                ("omega_scale", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+                ("omega_scale", ctypes.c_double), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class RPAError(RuntimeError):
@@ -72,6 +74,7 @@ def load(path: str = LIB_PATH):
         "rpa_plan_frequencies": ([vp, i, vp, vp], i),
         "rpa_generate_m": ([ctypes.POINTER(rpa_qpoint), i, i, i, i, vp, i, vp], i),
         "rpa_version": ([], ctypes.c_char_p),
+        "rpa_plan_timings": ([vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -148,11 +151,11 @@ class Plan:
     """Owner of an ``rpa_plan_t``; methods mirror the C entry points."""
 
     def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
-                 stream=None):
+                 stream=None, timing=False):
         lib = load()
         self.qpoints = list(qpoints)
         self._structs = (rpa_qpoint * len(self.qpoints))(*[q.struct() for q in self.qpoints])
-        opt = rpa_options(precision, energy_route, omega_scale)
+        opt = rpa_options(precision, energy_route, omega_scale, int(bool(timing)))
         self._stream = _stream(stream)
         h = ctypes.c_void_p()
         st = lib.rpa_plan_create(ctypes.byref(h), self._structs, len(self.qpoints), ctypes.byref(opt),
@@ -198,6 +201,14 @@ class Plan:
         _check(load().rpa_plan_frequencies(self.handle, iq, om.ctypes.data_as(ctypes.c_void_p),
                                            wt.ctypes.data_as(ctypes.c_void_p)), self.handle)
         return om, wt
+
+    def timings(self):
+        """({stage: ms} since the previous call, kernel launches since the previous call)."""
+        t = (ctypes.c_double * len(TIMERS))()
+        n = ctypes.c_longlong()
+        _check(load().rpa_plan_timings(self.handle, ctypes.cast(t, ctypes.c_void_p),
+                                       ctypes.cast(ctypes.byref(n), ctypes.c_void_p)), self.handle)
+        return dict(zip(TIMERS, list(t))), n.value
 
     def run(self, iq=0):
         """All stages of one q-point; returns E_c (Ha)."""
