@@ -193,15 +193,26 @@ def reference_arm(args, w, rank, dist):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def products(S):
+    """BF16 digit-product contractions per algorithmic one: pairs (s, t), s + t <= S - 1."""
+    return S * (S + 1) // 2
+
+
+def run_steps(plan, n):
+    return [plan.run(0) for _ in range(n)]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
+    ap.add_argument("--slices", default="3,5,4", help="digit slices of chi0, projection, chi_s")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -220,8 +231,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rpa.load()
-    precision = rpa.RPA_MIXED if args.precision == "mixed" else rpa.RPA_FP64
+    mixed = args.precision == "mixed"
+    precision = rpa.RPA_MIXED if mixed else rpa.RPA_FP64
     route = rpa.RPA_ROUTE_CHOLESKY if args.route == "cholesky" else rpa.RPA_ROUTE_EIG
+    slices = tuple(int(x) for x in args.slices.split(","))
     stream = torch.cuda.Stream(device=dev)
     # each rank its own q-point of the 4x4x4 grid (weak scaling, no exchange)
     iq = rank % 64
@@ -234,14 +247,12 @@ def main():
         rpa.rpa_generate_m(dq, 0, w["n_v"], 0, w["n_c"], A, stream=stream)
     stream.synchronize()
     dq.m = A
-    plan = rpa.Plan([dq], precision=precision, energy_route=route, stream=stream, timing=True)
+    plan = rpa.Plan([dq], precision=precision, energy_route=route, stream=stream, timing=True,
+                    slices=slices if mixed else (0, 0, 0))
     fl = flops(w)
     fl_total = sum(fl.values())
 
-    # warm-up
-    ecs = []
-    for _ in range(args.warmup):
-        ecs.append(plan.run(0))
+    ecs = run_steps(plan, args.warmup)
     plan.timings()
     torch.cuda.synchronize()
     barrier(dist)
@@ -252,8 +263,7 @@ def main():
     with ClockSampler(bus) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
-            ecs.append(plan.run(0))
+        ecs += run_steps(plan, args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(dist)
@@ -265,22 +275,51 @@ def main():
     contraction_s = (stage_ms["chi0"] + stage_ms["proj"] + stage_ms["chis"]) / 1e3 / args.steps
     contraction_tflops = fl_total / contraction_s / 1e12
 
-    # roofline of the dominant kernel (largest stage share among the contractions)
+    # roofline of the dominant contraction kernel
     pk, pk_kind = peaks()
-    shares = {k: v / sum(stage_ms.values()) for k, v in stage_ms.items()}
+    tot_ms = sum(stage_ms.values())
+    shares = {k: v / tot_ms for k, v in stage_ms.items()}
     dom = max(("chi0", "proj", "chis"), key=lambda k: stage_ms[k])
     dom_s = stage_ms[dom] / 1e3 / args.steps
-    if precision == rpa.RPA_FP64:
-        peak = pk["bf16_tflops_sustained"] * FP64_OVER_BF16
-        peak_note = "%s bf16 sustained x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind
-    else:
+    if mixed:
+        nprod = products(dict(chi0=slices[0], proj=slices[1], chis=slices[2])[dom])
         peak = pk["bf16_tflops_sustained"]
-        peak_note = "%s bf16 sustained" % pk_kind
-    achieved = fl[dom] / dom_s / 1e12
-    roofline = {"bound": "tensor" if precision == rpa.RPA_MIXED else "alu", "kernel": dom,
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": peak_note, "traffic": None,
-                "algorithmic_flops_per_launch": fl[dom]}
+        achieved = fl[dom] * nprod / dom_s / 1e12
+        roofline = {"bound": "tensor", "kernel": "slice_gemm (%s)" % dom, "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "%s bf16 sustained (MEASURED_PEAKS.json)" % pk_kind,
+                    "traffic": None, "work_per_launch": "%d digit-product contractions x %.4g "
+                    "algorithmic flops" % (nprod, fl[dom]),
+                    "fp64_equivalent_tflops": fl[dom] / dom_s / 1e12}
+    else:
+        peak = pk["bf16_tflops"] * FP64_OVER_BF16
+        achieved = fl[dom] / dom_s / 1e12
+        roofline = {"bound": "alu", "kernel": "fp64 %s" % dom, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "%s bf16 burst x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind,
+                    "traffic": None, "work_per_launch": "%.4g algorithmic flops" % fl[dom]}
+
+    # the FP64 path on the same inputs: speed-up and |dE_c| of the mixed path
+    compare = None
+    if mixed and not args.no_fp64_compare:
+        p64 = rpa.Plan([dq], precision=rpa.RPA_FP64, energy_route=route, stream=stream, timing=True)
+        run_steps(p64, 1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ec64 = run_steps(p64, 1)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        st64, _ = p64.timings()
+        p64.close()
+        compare = {"fp64_q_per_s": 1.0 / t64, "fp64_ms_per_step": t64 * 1e3, "fp64_ec_ha": ec64,
+                   "mixed_ec_ha": ecs[-1], "abs_dEc_ha": abs(ecs[-1] - ec64),
+                   "rel_dEc": abs(ecs[-1] - ec64) / abs(ec64), "speedup": t64 / sec_per_step,
+                   "contraction_speedup": ((st64["chi0"] + st64["proj"] + st64["chis"]) / 1e3)
+                   / contraction_s,
+                   "fp64_steps": 1, "fp64_warmup": 1}
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back
     e2e = None
@@ -301,7 +340,6 @@ def main():
         e2e_step()
         torch.cuda.synchronize()
         barrier(dist)
-        t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -312,8 +350,7 @@ def main():
         barrier(dist)
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
-               "wall_s": time.perf_counter() - t0}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
         plan.timings()
         del host_A
 
@@ -324,26 +361,26 @@ def main():
                "sample": desc}
 
     clocks = clk.summary()
-    spread = max(ecs) - min(ecs)
     line = {
         "metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == rpa.RPA_FP64 else "bf16",
+        "dtype": "bf16" if mixed else "f64",
         "data": "synthetic (splitmix64 matrix elements drawn on the device)",
         "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
-                   "energy_route": args.route,
+                   "slices": list(slices) if mixed else None, "energy_route": args.route,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * 16 / 1e9),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
         "contraction_tflops": contraction_tflops,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "stage_share": shares,
         "roofline": roofline,
+        "mixed_vs_fp64": compare,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "ec_ha": ecs[-1], "ec_spread_over_steps": spread,
+        "ec_ha": ecs[-1], "ec_spread_over_steps": max(ecs) - min(ecs),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -87,12 +87,18 @@ typedef struct {
   int energy_route;        /* rpa_energy_route                                       */
   double omega_scale;      /* s of the frequency map w = s t/(1-t); <= 0 means 0.5 Ha */
   int timing;              /* nonzero: record CUDA events around every stage kernel  */
-  int reserved[7];         /* zero                                                   */
+  int slices_chi0;         /* RPA_MIXED: digit slices of chi~(0) operands (1..8; 0 = 3) */
+  int slices_proj;         /* RPA_MIXED: digit slices of the projection (1..8; 0 = 5)  */
+  int slices_chis;         /* RPA_MIXED: digit slices of chi_s operands (1..8; 0 = 4)  */
+  int debug_stall;         /* test hook, 0 in production: 1 makes the tensor-core
+                              producer issue no loads, so every bounded wait of the
+                              GEMM runs out and the stage reports RPA_ETIMEOUT     */
+  int reserved[3];         /* zero                                                   */
 } rpa_options;
 
 /* Stage timers of rpa_plan_timings. */
 typedef enum {
-  RPA_T_CHI0 = 0,   /* chi~(0) contraction (incl. operand preparation on the mixed path) */
+  RPA_T_CHI0 = 0,   /* chi~(0) contraction                                               */
   RPA_T_EIG0 = 1,   /* FP64 eigensolve of chi~(0) and gauge fixing                       */
   RPA_T_PROJ = 2,   /* projection M~                                                     */
   RPA_T_CHIS = 3,   /* chi_s(w_k) contraction for every k                                */
@@ -100,7 +106,8 @@ typedef enum {
   RPA_T_EIGS = 5,   /* eigenvalues (or Cholesky) of every chi_s(w_k)                     */
   RPA_T_ENERGY = 6, /* final log-sum and quadrature                                      */
   RPA_T_OTHER = 7,  /* scalars, mirrors, copies                                          */
-  RPA_N_TIMERS = 8
+  RPA_T_SLICE = 8,  /* mixed path: cutting FP64 operands into BF16 digit planes          */
+  RPA_N_TIMERS = 9
 } rpa_timer;
 
 typedef struct rpa_plan_s* rpa_plan_t;

@@ -62,6 +62,7 @@ struct rpa_plan_s {
   };
   std::vector<cudaEvent_t> ev_pool;
   std::vector<Pending> pending;
+  cudaEvent_t open_ev[RPA_N_TIMERS] = {};
   long long launches = 0;
 };
 
@@ -114,6 +115,8 @@ void free_plan(rpa_plan_t p) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
+  for (auto e : p->open_ev)
+    if (e) cudaEventDestroy(e);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->omega, p->weight, p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
@@ -161,6 +164,24 @@ struct StageTimer {
   }
 };
 
+// Timing hook used by the tensor-core path: begin/end marks of one timer id.
+void mark_event(void* ctx, int id, int begin) {
+  rpa_plan_t p = (rpa_plan_t)ctx;
+  if (!p->opt.timing || id < 0 || id >= RPA_N_TIMERS) return;
+  if (begin) {
+    if (!p->open_ev[id] && (p->open_ev[id] = get_event(p))) cudaEventRecord(p->open_ev[id], p->st);
+  } else if (p->open_ev[id]) {
+    cudaEvent_t b = get_event(p);
+    if (b) {
+      cudaEventRecord(b, p->st);
+      p->pending.push_back({id, p->open_ev[id], b});
+    } else {
+      p->ev_pool.push_back(p->open_ev[id]);
+    }
+    p->open_ev[id] = nullptr;
+  }
+}
+
 rpa_status check_qpoint(const rpa_qpoint& q, int i) {
   auto bad = [&](const char* what) {
     return fail(nullptr, RPA_EINVAL, "q-point %d: %s", i, what);
@@ -202,6 +223,18 @@ rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
   *a = p->gen_a;
   *dtype = q.m_dtype;
   return RPA_OK;
+}
+
+// A tensor-core kernel that gave up on a bounded wait leaves a code in the
+// status word; report it (and clear it) at the next host synchronisation.
+rpa_status tc_status(rpa_plan_t p) {
+  if (!p->tcw.status) return RPA_OK;
+  int code = 0;
+  CU(p, cudaMemcpyAsync(&code, p->tcw.status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  CU(p, cudaStreamSynchronize(p->st));
+  if (code == 0) return RPA_OK;
+  CU(p, cudaMemsetAsync(p->tcw.status, 0, sizeof(int), p->st));
+  return fail(p, RPA_ETIMEOUT, "a tensor-core kernel gave up waiting (code %d)", code);
 }
 
 rpa_status prepare(rpa_plan_t p, int iq) {
@@ -258,6 +291,9 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     return fail(nullptr, RPA_EINVAL, "unknown precision %d", o.precision);
   if (o.energy_route != RPA_ROUTE_EIG && o.energy_route != RPA_ROUTE_CHOLESKY)
     return fail(nullptr, RPA_EINVAL, "unknown energy route %d", o.energy_route);
+  for (int sl : {o.slices_chi0, o.slices_proj, o.slices_chis})
+    if (sl < 0 || sl > rpa::tc::MAX_SLICES)
+      return fail(nullptr, RPA_EINVAL, "digit slices must be in [0, %d]", rpa::tc::MAX_SLICES);
   for (int i = 0; i < n_q; ++i) {
     rpa_status s = check_qpoint(q[i], i);
     if (s != RPA_OK) return s;
@@ -321,11 +357,19 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     }
   }
   if (o.precision == RPA_MIXED) {
-    s = rpa::tc::alloc_workspace(p->tcw, G, E, V, F);
+    rpa::tc::Slices sl;
+    if (o.slices_chi0 > 0) sl.chi0 = o.slices_chi0;
+    if (o.slices_proj > 0) sl.proj = o.slices_proj;
+    if (o.slices_chis > 0) sl.chis = o.slices_chis;
+    std::string e;
+    s = rpa::tc::alloc_workspace(p->tcw, G, E, V, F, sl, e);
     if (s != RPA_OK) {
       free_plan(p);
-      return fail(nullptr, s, "tensor-core workspace allocation failed");
+      return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
     }
+    p->tcw.debug_stall = o.debug_stall;
+    p->tcw.hook.ctx = p;
+    p->tcw.hook.mark = mark_event;
   }
   if (cusolverDnCreate(&p->sol) != CUSOLVER_STATUS_SUCCESS ||
       cusolverDnCreateParams(&p->params) != CUSOLVER_STATUS_SUCCESS) {
@@ -415,18 +459,16 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   if (s != RPA_OK) return s;
   const long n_vc = (long)q.n_v * q.n_c;
   const double scale = -1.0 / q.omega_cell;
-  {
+  if (p->opt.precision == RPA_MIXED) {
+    int nl = 0;
+    s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
+                      p->err, &nl);
+    p->launches += nl;
+    if (s != RPA_OK) return s;
+  } else {
     StageTimer t(p, RPA_T_CHI0);
-    if (p->opt.precision == RPA_MIXED) {
-      int nl = 0;
-      s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
-                        p->err, &nl);
-      p->launches += nl;
-      if (s != RPA_OK) return s;
-    } else {
-      CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
-      p->launches += 1;
-    }
+    CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
+    p->launches += 1;
   }
   {
     StageTimer t(p, RPA_T_OTHER);
@@ -461,6 +503,7 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   int info = 0;
   CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
   CU(p, cudaStreamSynchronize(p->st));
+  if ((s = tc_status(p)) != RPA_OK) return s;
   if (info != 0) return fail(p, RPA_EEIG, "Xsyevdx info = %d", info);
   if (meig != q.n_eig) return fail(p, RPA_EEIG, "Xsyevdx returned %lld of %d eigenpairs",
                                    (long long)meig, q.n_eig);
@@ -491,17 +534,11 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   const double* om = p->omega + (size_t)iq * p->max_freq;
   if (p->opt.precision == RPA_MIXED) {
     int nl = 0;
-    {
-      StageTimer t(p, RPA_T_PROJ);
-      s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
-      if (s != RPA_OK) return s;
-    }
-    {
-      StageTimer t(p, RPA_T_CHIS);
-      s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err,
-                        &nl);
-      if (s != RPA_OK) return s;
-    }
+    s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
+    if (s != RPA_OK) return s;
+    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err,
+                      &nl);
+    if (s != RPA_OK) return s;
     p->launches += nl;
   } else {
     {
@@ -576,6 +613,8 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
   CU(p, cudaMemcpyAsync(fl, p->flags, sizeof fl, cudaMemcpyDeviceToHost, p->st));
   CU(p, cudaMemcpyAsync(ec_host, p->ec, sizeof(double), cudaMemcpyDeviceToHost, p->st));
   CU(p, cudaStreamSynchronize(p->st));
+  rpa_status ts = tc_status(p);
+  if (ts != RPA_OK) return ts;
   if (fl[2] != 0) return fail(p, RPA_EEIG, "Xsyevd info = %d", fl[2]);
   if (fl[1] != 0)
     return fail(p, RPA_ENUMERIC, "energy of q-point %d: 1 - lambda <= 0 or non-finite (bits %d)",

@@ -1,4 +1,14 @@
 // Tensor-core (tcgen05, BF16) contractions of the mixed-precision path.
+//
+// Every contraction D = A B^T (real, K-major operands) is evaluated on exact
+// digit slices: each operand row r is scaled by 2^-e_r (e_r from the row's
+// largest magnitude) and cut into S signed 8-bit integer digits, so
+//   x = 2^(e_r - 7) * sum_s d_s 2^(-8 s),   |d_s| <= 128  (exact in BF16).
+// Digit products are exact, and their FP32 sums over a drain interval of K
+// are exact integers below 2^24; the epilogue folds each interval into a
+// double-float accumulator.  The only approximation is the truncation of the
+// digit expansion and of the product triangle (s + t <= S - 1): about
+// 2^-(7 + 8(S-1)) relative to the row scales.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,22 +20,47 @@
 namespace rpa {
 namespace tc {
 
+constexpr int MAX_SLICES = 8;
+
+struct Slices {
+  int chi0 = 3, proj = 5, chis = 4;
+};
+
+// Optional stage-timing hook: mark(ctx, timer id, 1) before and (.., 0) after
+// a group of launches.
+struct Hook {
+  void* ctx = nullptr;
+  void (*mark)(void* ctx, int id, int begin) = nullptr;
+  void operator()(int id, int begin) const {
+    if (mark) mark(ctx, id, begin);
+  }
+};
+
 struct Workspace {
-  void* slices = nullptr;     // sliced BF16 operand planes
-  size_t slice_bytes = 0;
-  void* exps = nullptr;       // per-row power-of-two scales of the sliced operands
-  size_t exp_bytes = 0;
-  void* acc = nullptr;        // FP64 accumulation target
-  size_t acc_bytes = 0;
+  void* planes = nullptr;     // BF16 digit planes (largest stage)
+  size_t plane_bytes = 0;
+  void* planes2 = nullptr;    // second operand planes (projection B, chi_s A)
+  size_t plane2_bytes = 0;
+  int* exps = nullptr;        // per-row exponents
+  size_t exp_count = 0;
+  unsigned long long* rowmax = nullptr;  // per-row max |x| (double bits)
+  size_t rowmax_count = 0;
+  int4* work = nullptr;       // tile work list
+  size_t work_count = 0;
   int* status = nullptr;      // device error word of the bounded waits
+  Slices slices;
+  int freq_group = 8;
+  int debug_stall = 0;
+  Hook hook;
 };
 
 rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t max_vc,
-                           size_t max_freq);
+                           size_t max_freq, const Slices& s, std::string& err);
 void free_workspace(Workspace& w);
 
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err, int* launches);
+                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err,
+                int* launches);
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,

@@ -23,7 +23,7 @@ RPA_C128, RPA_C64 = 0, 1
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
             "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings")
-TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other")
+TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other", "slice")
 
 
 class rpa_qpoint(ctypes.Structure):
@@ -38,7 +38,9 @@ class rpa_qpoint(ctypes.Structure):
 class rpa_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("energy_route", ctypes.c_int),
                 ("omega_scale", ctypes.c_double), ("timing", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("slices_chi0", ctypes.c_int), ("slices_proj", ctypes.c_int),
+                ("slices_chis", ctypes.c_int), ("debug_stall", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class RPAError(RuntimeError):
@@ -151,11 +153,12 @@ class Plan:
     """Owner of an ``rpa_plan_t``; methods mirror the C entry points."""
 
     def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
-                 stream=None, timing=False):
+                 stream=None, timing=False, slices=(0, 0, 0), debug_stall=0):
         lib = load()
         self.qpoints = list(qpoints)
         self._structs = (rpa_qpoint * len(self.qpoints))(*[q.struct() for q in self.qpoints])
-        opt = rpa_options(precision, energy_route, omega_scale, int(bool(timing)))
+        opt = rpa_options(precision, energy_route, omega_scale, int(bool(timing)), *slices,
+                          int(debug_stall))
         self._stream = _stream(stream)
         h = ctypes.c_void_p()
         st = lib.rpa_plan_create(ctypes.byref(h), self._structs, len(self.qpoints), ctypes.byref(opt),
@@ -220,8 +223,8 @@ class Plan:
 
 # names of the C ABI, for callers that prefer the flat form
 def rpa_plan_create(qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
-                    stream=None):
-    return Plan(qpoints, precision, energy_route, omega_scale, stream)
+                    stream=None, timing=False, slices=(0, 0, 0)):
+    return Plan(qpoints, precision, energy_route, omega_scale, stream, timing, slices)
 
 
 def rpa_chi0_static(plan, iq, chi_out=None):

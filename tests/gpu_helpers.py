@@ -3,7 +3,8 @@ and return every intermediate on the host, and align eigenvector phases."""
 import numpy as np
 
 
-def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=False, m_dtype=None):
+def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=False, m_dtype=None,
+            slices=(0, 0, 0)):
     import torch
     from paper_2405_20258_gb300 import rpa
 
@@ -12,7 +13,7 @@ def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=Fals
     n_g, n_vc = qp.n_g, qp.n_v * qp.n_c
     dev = "cuda"
     out = {}
-    with rpa.Plan([dq], precision=precision, energy_route=route) as plan:
+    with rpa.Plan([dq], precision=precision, energy_route=route, slices=slices) as plan:
         chi = torch.empty((n_g, n_g), dtype=torch.complex128, device=dev) if keep else None
         lam0 = torch.empty(n_eig, dtype=torch.float64, device=dev) if keep else None
         C = torch.empty((n_g, n_eig), dtype=torch.complex128, device=dev) if keep else None
