@@ -54,6 +54,8 @@ struct rpa_plan_s {
   size_t sol_dev_bytes = 0;
   void* sol_host = nullptr;
   size_t sol_host_bytes = 0;
+  bool batched_eig = false;   // cusolverDnXsyevBatched usable for the chi_s eigenvalues
+  int* infos = nullptr;       // [max_freq] solver info of the batched solve
   rpa::tc::Workspace tcw;     // tensor-core path workspace
   // stage timers (CUDA events on the plan stream) and the library's launch count
   struct Pending {
@@ -120,7 +122,8 @@ void free_plan(rpa_plan_t p) {
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->omega, p->weight, p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
-                  p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev};
+                  p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
+                  p->infos};
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
@@ -403,6 +406,25 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     dmax = std::max(dmax, db);
     hmax = std::max(hmax, hb);
   }
+  // batched eigenvalue solve of all chi_s(w_k) of a q-point, when the library offers it
+  p->batched_eig = true;
+  for (int i = 0; i < n_q && p->batched_eig; ++i) {
+    size_t db = 0, hb = 0;
+    if (cusolverDnXsyevBatched_bufferSize(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR,
+                                          CUBLAS_FILL_MODE_LOWER, q[i].n_eig, CUDA_C_64F,
+                                          p->chis_work, q[i].n_eig, CUDA_R_64F, p->lam,
+                                          CUDA_C_64F, &db, &hb,
+                                          q[i].n_freq) != CUSOLVER_STATUS_SUCCESS) {
+      p->batched_eig = false;
+      break;
+    }
+    dmax = std::max(dmax, db);
+    hmax = std::max(hmax, hb);
+  }
+  if (dalloc(nullptr, &p->infos, (size_t)F) != RPA_OK) {
+    free_plan(p);
+    return RPA_ENOMEM;
+  }
   p->sol_dev_bytes = std::max<size_t>(dmax, 16);
   p->sol_host_bytes = std::max<size_t>(hmax, 16);
   if (cudaMalloc(&p->sol_dev, p->sol_dev_bytes) != cudaSuccess) {
@@ -592,12 +614,30 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
       StageTimer t(p, RPA_T_EIGS);
       CU(p, cudaMemcpyAsync(p->chis_work, p->chis, sizeof(cplx) * (size_t)F * E * E,
                             cudaMemcpyDeviceToDevice, p->st));
-      for (int k = 0; k < F; ++k) {
-        CS(p, cusolverDnXsyevd(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR,
-                               CUBLAS_FILL_MODE_LOWER, E, CUDA_C_64F,
-                               p->chis_work + (size_t)k * E * E, E, CUDA_R_64F,
-                               p->lam + (size_t)k * E, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
-                               p->sol_host, p->sol_host_bytes, p->flags + 2));
+      bool done = false;
+      if (p->batched_eig) {
+        CU(p, cudaMemsetAsync(p->infos, 0, sizeof(int) * F, p->st));
+        cusolverStatus_t cs = cusolverDnXsyevBatched(
+            p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, E, CUDA_C_64F,
+            p->chis_work, E, CUDA_R_64F, p->lam, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
+            p->sol_host, p->sol_host_bytes, p->infos, F);
+        if (cs == CUSOLVER_STATUS_SUCCESS) {
+          done = true;
+        } else {
+          p->batched_eig = false;  // fall back to one solve per frequency from now on
+          CU(p, cudaMemcpyAsync(p->chis_work, p->chis, sizeof(cplx) * (size_t)F * E * E,
+                                cudaMemcpyDeviceToDevice, p->st));
+        }
+      }
+      if (!done) {
+        CU(p, cudaMemsetAsync(p->infos, 0, sizeof(int) * F, p->st));
+        for (int k = 0; k < F; ++k) {
+          CS(p, cusolverDnXsyevd(p->sol, p->params, CUSOLVER_EIG_MODE_NOVECTOR,
+                                 CUBLAS_FILL_MODE_LOWER, E, CUDA_C_64F,
+                                 p->chis_work + (size_t)k * E * E, E, CUDA_R_64F,
+                                 p->lam + (size_t)k * E, CUDA_C_64F, p->sol_dev, p->sol_dev_bytes,
+                                 p->sol_host, p->sol_host_bytes, p->infos + k));
+        }
       }
     }
     {
@@ -615,7 +655,12 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
   CU(p, cudaStreamSynchronize(p->st));
   rpa_status ts = tc_status(p);
   if (ts != RPA_OK) return ts;
-  if (fl[2] != 0) return fail(p, RPA_EEIG, "Xsyevd info = %d", fl[2]);
+  if (p->opt.energy_route == RPA_ROUTE_EIG) {
+    std::vector<int> info(F);
+    CU(p, cudaMemcpy(info.data(), p->infos, sizeof(int) * F, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < F; ++k)
+      if (info[k] != 0) return fail(p, RPA_EEIG, "eigenvalues of chi_s(%d): info = %d", k, info[k]);
+  }
   if (fl[1] != 0)
     return fail(p, RPA_ENUMERIC, "energy of q-point %d: 1 - lambda <= 0 or non-finite (bits %d)",
                 iq, fl[1]);

@@ -380,20 +380,36 @@ __global__ void __launch_bounds__(THREADS, 1)
 // digit slicing (HBM-bound)
 // ---------------------------------------------------------------------------
 
-// x ~= 2^(e-7) sum_s d_s 2^(-8s) with |x| < 2^e and integer |d_s| <= 128.
+// Signed base-256 digits of Y = round(x 2^(7 + 8(S-1) - e)) for |x| < 2^e:
+// x ~= 2^(e-7) sum_s d_s 2^(-8s), integer |d_s| <= 128 (exact in BF16).
+// Pure integer arithmetic on the IEEE fields (GB300's FP64 pipe is narrow).
 __device__ __forceinline__ void cut_digits(double x, int e, int S, float* d) {
-  double y = ldexp(x, 7 - e);
-  for (int s = 0; s < S; ++s) {
-    double di = rint(y);
-    d[s] = (float)di;
-    y = (y - di) * 256.0;
+  const long long bits = __double_as_longlong(x);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  long long Y = 0;
+  if (bexp != 0) {  // zero and subnormals give zero digits
+    const long long mant = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+    const int sh = bexp - 1075 + 7 + 8 * (S - 1) - e;  // Y = mant 2^sh
+    if (sh >= 0)
+      Y = mant << sh;  // < 2^(7 + 8(S-1)) <= 2^63 since |x| < 2^e
+    else if (sh > -63)
+      Y = (mant + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) Y = -Y;
   }
+  for (int s = S - 1; s >= 1; --s) {
+    const int dd = (int)((Y + 128) & 255) - 128;
+    d[s] = (float)dd;
+    Y = (Y - dd) >> 8;
+  }
+  d[0] = (float)Y;
 }
 
+// e with m < 2^e (frexp exponent) for m > 0; 0 for m == 0.
 __device__ __forceinline__ int row_exponent(double m) {
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);
-  return e;
+  const long long bits = __double_as_longlong(m);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  if (bexp == 0) return m > 0.0 ? -1022 : 0;
+  return bexp - 1022;
 }
 
 __device__ __forceinline__ double2 load_any(const void* p, int dtype, long idx) {
@@ -546,27 +562,34 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
   }
 }
 
+// f[b][vc] = 4 D / (D^2 + w_{k0+b}^2) for the frequencies of one group.
+__global__ void freq_weights_kernel(const double* delta, const double* omega, int n_vc, int k0,
+                                    int nb, double* f) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)nb * n_vc) return;
+  const int b = (int)(i / n_vc), vc = (int)(i % n_vc);
+  const double d = delta[vc], w = omega[k0 + b];
+  f[i] = 4.0 * d / (d * d + w * w);
+}
+
 // chi_s B operand of frequencies k0 .. k0+nb-1: for row j, f_k(vc) M~[j][vc]
 // as rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); one block per j.
 constexpr int MAX_GROUP = 8;
 __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
-                                    long K, const double* delta, const double* omega, int k0,
-                                    int nb, int S, __nv_bfloat162* planes, int* exps,
-                                    int eb_stride) {
+                                    long K, const double* f, int nb, int S,
+                                    __nv_bfloat162* planes, int* exps, int eb_stride) {
   __shared__ double red[MAX_GROUP][32];
   const int j = blockIdx.x;
-  double w2[MAX_GROUP], m[MAX_GROUP];
-  for (int b = 0; b < MAX_GROUP; ++b) {
-    w2[b] = b < nb ? omega[k0 + b] * omega[k0 + b] : 0.0;
-    m[b] = 0.0;
-  }
+  double m[MAX_GROUP];
+#pragma unroll
+  for (int b = 0; b < MAX_GROUP; ++b) m[b] = 0.0;
   if (j < n_eig)
     for (int vc = threadIdx.x; vc < n_vc; vc += blockDim.x) {
-      double2 x = mt[(long)j * n_vc + vc];
-      double a = fmax(fabs(x.x), fabs(x.y)), d = delta[vc];
+      const double2 x = mt[(long)j * n_vc + vc];
+      const double a = fmax(fabs(x.x), fabs(x.y));
 #pragma unroll
       for (int b = 0; b < MAX_GROUP; ++b)
-        if (b < nb) m[b] = fmax(m[b], 4.0 * d / (d * d + w2[b]) * a);
+        if (b < nb) m[b] = fmax(m[b], f[(long)b * n_vc + vc] * a);
     }
 #pragma unroll
   for (int b = 0; b < MAX_GROUP; ++b) {
@@ -586,16 +609,15 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
   const long plane = (long)2 * n_eig_pad * (K / 2);
   for (long vc = threadIdx.x; vc < K / 2; vc += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
-    double d = 1.0;
-    if (j < n_eig && vc < n_vc) {
-      x = mt[(long)j * n_vc + vc];
-      d = delta[vc];
-    }
-    for (int b = 0; b < nb; ++b) {
-      double f = 4.0 * d / (d * d + w2[b]);
+    const bool in = j < n_eig && vc < n_vc;
+    if (in) x = mt[(long)j * n_vc + vc];
+#pragma unroll
+    for (int b = 0; b < MAX_GROUP; ++b) {
+      if (b >= nb) break;
+      const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
       float dr[MAX_SLICES], di[MAX_SLICES];
-      cut_digits(f * x.x, e[b], S, dr);
-      cut_digits(f * x.y, e[b], S, di);
+      cut_digits(fv * x.x, e[b], S, dr);
+      cut_digits(fv * x.y, e[b], S, di);
       for (int s = 0; s < S; ++s) {
         __nv_bfloat162* p0 = planes + (long)(b * S + s) * plane + (long)(2 * j) * (K / 2) + vc;
         p0[0] = __floats2bfloat162_rn(dr[s], di[s]);
@@ -756,6 +778,7 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
                 std::max((size_t)g_pad, (size_t)grp * e_pad);
   w.rowmax_count = g_pad;
   w.work_count = 1 << 20;
+  w.fweight_count = (size_t)grp * max_vc;
   auto al = [&](void** p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -769,7 +792,8 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   if (!al(&w.planes, w.plane_bytes) || !al(&w.planes2, w.plane2_bytes) ||
       !al((void**)&w.exps, w.exp_count * sizeof(int)) ||
       !al((void**)&w.rowmax, w.rowmax_count * sizeof(unsigned long long)) ||
-      !al((void**)&w.work, w.work_count * sizeof(int4)) || !al((void**)&w.status, sizeof(int))) {
+      !al((void**)&w.work, w.work_count * sizeof(int4)) || !al((void**)&w.status, sizeof(int)) ||
+      !al((void**)&w.fweights, w.fweight_count * sizeof(double))) {
     free_workspace(w);
     return RPA_ENOMEM;
   }
@@ -778,7 +802,7 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
 }
 
 void free_workspace(Workspace& w) {
-  void* b[] = {w.planes, w.planes2, w.exps, w.rowmax, w.work, w.status};
+  void* b[] = {w.planes, w.planes2, w.exps, w.rowmax, w.work, w.status, w.fweights};
   for (void* p : b)
     if (p) cudaFree(p);
   w = Workspace{};
@@ -898,11 +922,14 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   for (int k0 = 0; k0 < n_freq; k0 += w.freq_group) {
     const int nb = std::min(w.freq_group, n_freq - k0);
     w.hook(RPA_T_SLICE, 1);
+    freq_weights_kernel<<<cdiv((long)nb * n_vc, 256), 256, 0, st>>>(delta, omega, n_vc, k0, nb,
+                                                                    w.fweights);
+    CK(cudaGetLastError());
     chis_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)mt, n_eig, (int)e_pad,
-                                                         n_vc, K, delta, omega, k0, nb, S, pb, eb,
+                                                         n_vc, K, w.fweights, nb, S, pb, eb,
                                                          (int)e_pad);
     CK(cudaGetLastError());
-    if (launches) *launches += 1;
+    if (launches) *launches += 2;
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap tb;
     if (!make_map(&tb, w.planes, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, BN, err))

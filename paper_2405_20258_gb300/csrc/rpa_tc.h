@@ -48,6 +48,8 @@ struct Workspace {
   int4* work = nullptr;       // tile work list
   size_t work_count = 0;
   int* status = nullptr;      // device error word of the bounded waits
+  double* fweights = nullptr; // transition weights of one frequency group
+  size_t fweight_count = 0;
   Slices slices;
   int freq_group = 8;
   int debug_stall = 0;
