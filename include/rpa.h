@@ -170,6 +170,27 @@ rpa_status rpa_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc,
  * the stream.  times_ms: host [RPA_N_TIMERS] or NULL; launches: host or NULL. */
 rpa_status rpa_plan_timings(rpa_plan_t plan, double* times_ms, long long* launches);
 
+/* Allocation-free trace term, for callers that cannot allocate device memory
+ * where they call it (their device memory is fully reserved by their own pool
+ * allocator, or they must not cause the device-wide synchronisation that
+ * cudaMalloc/cudaFree can bring).  The paper has no counterpart: it is the
+ * trace term of rpa_chi_freq, T_k = -(1/Omega) sum_vc f_vc(w_k) |M~[:,vc]|^2,
+ * computed without a plan and without any allocation.
+ *   mtilde    [n_eig][n_v*n_c] complex128 (device), e.g. rpa_chi_freq's mtilde_out
+ *   e_v, e_c  [n_v], [n_c] band energies (device); omega [n_freq] (device)
+ *   trace_out [n_freq] float64 (device), written on `stream` (a cudaStream_t).
+ * Scratch is a fixed library array of RPA_STATIC_TRACE_MAX_VC doubles (4 MiB)
+ * that every GPU loading the library holds until the process exits; larger
+ * n_v*n_c is rejected with RPA_EINVAL (message in rpa_last_error(NULL)).  The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current): make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race;
+ * each call overwrites the entries it reads.  Asynchronous: no host sync. */
+#define RPA_STATIC_TRACE_MAX_VC 524288
+rpa_status rpa_trace_term_static(const void* mtilde, int n_eig, int n_v, int n_c,
+                                 const double* e_v, const double* e_c, const double* omega,
+                                 int n_freq, double omega_cell, double* trace_out, void* stream);
+
 /* Library version string. */
 const char* rpa_version(void);
 

@@ -30,6 +30,10 @@ struct DevBuf {
 
 }  // namespace
 
+namespace rpa {
+void set_call_error(const char* msg) { g_create_error = msg; }
+}  // namespace rpa
+
 struct rpa_plan_s {
   int n_q = 0;
   std::vector<rpa_qpoint> q;

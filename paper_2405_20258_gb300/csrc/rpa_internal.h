@@ -8,6 +8,9 @@
 
 namespace rpa {
 
+// Record the message that rpa_last_error(NULL) returns for plan-less calls.
+void set_call_error(const char* msg);
+
 struct cplx {
   double re, im;
 };

@@ -22,7 +22,9 @@ RPA_C128, RPA_C64 = 0, 1
 
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
-            "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings")
+            "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings",
+            "rpa_trace_term_static")
+STATIC_TRACE_MAX_VC = 524288
 TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other", "slice")
 
 
@@ -77,6 +79,7 @@ def load(path: str = LIB_PATH):
         "rpa_generate_m": ([ctypes.POINTER(rpa_qpoint), i, i, i, i, vp, i, vp], i),
         "rpa_version": ([], ctypes.c_char_p),
         "rpa_plan_timings": ([vp, vp, vp], i),
+        "rpa_trace_term_static": ([vp, i, i, i, vp, vp, vp, i, d, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +256,16 @@ def rpa_generate_m(dq: DeviceQPoint, v0, nv, c0, nc, out, stream=None):
     dt = RPA_C64 if out.dtype == torch.complex64 else RPA_C128
     s = dq.struct()
     _check(load().rpa_generate_m(ctypes.byref(s), v0, nv, c0, nc, _ptr(out), dt, _stream(stream)))
+
+
+def rpa_trace_term_static(mtilde, n_eig, n_v, n_c, e_v, e_c, omega, n_freq, omega_cell, trace_out,
+                          stream=None):
+    """Trace term of the subspace polarizability without a plan and without any
+    device allocation (for callers that cannot allocate): scratch is a fixed
+    library array of STATIC_TRACE_MAX_VC doubles.  All arrays are device tensors."""
+    _check(load().rpa_trace_term_static(_ptr(mtilde), int(n_eig), int(n_v), int(n_c), _ptr(e_v),
+                                        _ptr(e_c), _ptr(omega), int(n_freq), float(omega_cell),
+                                        _ptr(trace_out), _stream(stream)))
 
 
 def rpa_version():
