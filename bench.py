@@ -29,6 +29,8 @@ METRIC = "q-points/sec and contraction TFLOP/s, mixed vs FP64 path at |dE_c|<=1e
 WORKLOADS = {
     "qpoint-4000": dict(n_g=4000, n_v=128, n_c=2000, n_eig=400, n_freq=32),
     "qpoint-400": dict(n_g=400, n_v=16, n_c=200, n_eig=40, n_freq=16),
+    # small case for ncu captures (A is 0.5 GB, larger than L2)
+    "qpoint-1024": dict(n_g=1024, n_v=32, n_c=1000, n_eig=128, n_freq=16),
 }
 # FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
@@ -211,7 +213,7 @@ def main():
     ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
-    ap.add_argument("--slices", default="3,5,4", help="digit slices of chi0, projection, chi_s")
+    ap.add_argument("--slices", default="3,6,4", help="digit slices of chi0, projection, chi_s")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
