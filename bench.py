@@ -239,7 +239,8 @@ def main():
     slices = tuple(int(x) for x in args.slices.split(","))
     stream = torch.cuda.Stream(device=dev)
     # each rank its own q-point of the 4x4x4 grid (weak scaling, no exchange)
-    iq = rank % 64
+    from paper_2405_20258_gb300.shard import qpoints_for_rank
+    iq = qpoints_for_rank(64, rank % 64, min(world, 64))[0]
     qp = inputs.make_qpoint(w["n_g"], w["n_v"], w["n_c"], iq=iq,
                             q_twentieths=(1, 0, 0) if iq == 0 else inputs.qgrid_4x4x4()[iq])
     n_vc = w["n_v"] * w["n_c"]
