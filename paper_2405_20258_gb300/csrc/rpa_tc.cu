@@ -2,14 +2,15 @@
 // digit-sliced BF16 GEMM with TMEM accumulation and a double-float epilogue,
 // plus the HBM-bound kernels that cut FP64 operands into digit planes.
 //
-// GEMM kernel roles (320 threads, one output tile of 128 x 64 per CTA):
+// GEMM kernel roles (one output tile of 128 x BN per CTA, BN = 64, 96 or 128):
 //   warp 0      TMA producer: per 64-wide K-tile, all S digit planes of the B
 //               tile (double-buffered) and the S digit planes of the A tile
 //               through a 4-stage ring;
 //   warp 1      TMEM allocation and the single MMA-issuing thread: for every
 //               slice pair (s, t) with s + t <= S-1, four kind::f16 MMAs
 //               (K = 16 each) into the level accumulator L = s + t;
-//   warps 2..9  epilogue: at the end of each drain interval, read the S level
+//   BN/8 epilogue warps (4 lane quadrants x BN/32 column blocks): at the end
+//               of each drain interval, read the S level
 //               accumulators (exact integers) from TMEM, scale by 2^-8L and add
 //               them into per-thread double-float registers (one TMEM lane and
 //               32 columns per thread); finally apply the row scales and write
@@ -23,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "rpa_tc.h"
@@ -32,18 +34,35 @@ namespace tc {
 namespace {
 
 constexpr int BM = 128;  // A rows per tile = TMEM lanes = MMA M
-constexpr int BN = 64;   // B rows per tile = MMA N
 constexpr int BK = 64;   // K elements per tile: 128 bytes of BF16, one 128B swizzle row
-constexpr int NA = 4;    // A ring depth
-constexpr int THREADS = 320;  // producer, MMA, 8 epilogue warps
+// B rows per tile (= MMA N) is a template parameter: 128 when the S level
+// accumulators of 128 columns fit in TMEM (S <= 4), else 64.
+constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA)
+constexpr int MAX_NB = 3;   // B buffers (runtime, <= MAX_NB)
+size_t g_smem_limit = 0;    // dynamic shared memory a CTA of the GEMM may use (set at first use)
+// producer warp, MMA warp, and 4 x BN/32 epilogue warps (4 lane quadrants x
+// BN/32 column blocks of 32 accumulator columns)
+template <int BN>
+constexpr int threads_for() {
+  return 64 + 4 * BN;
+}
+
+// TMEM columns between level accumulators: BN, except N = 96 which keeps the
+// 128-column spacing of the N = 128 layout.
+template <int BN>
+constexpr int tmem_stride() {
+  return BN == 96 ? 128 : BN;
+}
 constexpr uint32_t A_TILE = BM * BK * 2;  // 16 KB
-constexpr uint32_t B_TILE = BN * BK * 2;  // 8 KB
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 
 // kind::f16 instruction descriptor: D = F32 (bits 4-5), A = B = BF16 (bits 7-9,
 // 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+template <int BN>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
 
 enum : int {
   ERR_WAIT_PRODUCER = 1,
@@ -53,6 +72,8 @@ enum : int {
 
 struct GemmArgs {
   int S;              // digit slices per operand
+  int na, nb;         // A ring depth, B buffers
+  int nacc;           // level-accumulator buffers in TMEM (1 or 2)
   int K;              // padded K (multiple of BK)
   int kd_tiles;       // K-tiles per drain interval
   int k_per_split;    // K elements per split (multiple of BK)
@@ -65,6 +86,8 @@ struct GemmArgs {
   double2* out;       // complex output
   long out_bstride, ld_row, ld_col;
   int conj, atomic;
+  const double* rsa;  // optional FP64 factor per A row (NULL: 1)
+  const double* rsb;  // optional FP64 factor per complex B column (NULL: 1)
   int stall;          // test hook: the producer issues nothing
   int* status;
 };
@@ -102,9 +125,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait on one phase of an mbarrier.  false: timed out (flag raised) or
-// another role of this CTA aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                          int code) {
+// another role of this CTA aborted.  The latency-critical producer and MMA
+// threads spin on try_wait (which suspends in hardware); epilogue warps also
+// back off with a short sleep.
+template <bool kSleep>
+__device__ __forceinline__ bool mbar_wait_t(uint64_t* bar, uint32_t parity,
+                                            volatile int* abort_flag, int* status, int code) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (true) {
@@ -115,9 +141,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
       atomicOr(status, code);
       return false;
     }
-    __nanosleep(64);
+    if (kSleep) __nanosleep(64);
   }
 }
+#define mbar_wait mbar_wait_t<false>
+#define mbar_wait_sleep mbar_wait_t<true>
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int c0, int c1, int c2) {
@@ -148,14 +176,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
+                                         uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
       " setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
       "}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -165,18 +193,23 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// 32 lanes x 32 consecutive columns of FP32 from TMEM.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+// 32 lanes x 8 consecutive columns of FP32 from TMEM.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+               "r"(r[7])
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
@@ -198,19 +231,25 @@ __device__ __forceinline__ void dfloat_add(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, err);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <int BN>
+__global__ void __launch_bounds__(threads_for<BN>(), 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
+  constexpr uint32_t B_TILE = BN * BK * 2;
+  constexpr uint32_t IDESC = idesc<BN>();
+  constexpr int CPT = 32;           // accumulator columns per epilogue thread
+  constexpr int EPI = BN / 8;       // epilogue warps: 4 lane quadrants x BN/32 column blocks
+  constexpr int TS = tmem_stride<BN>();
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_a[NA], empty_a[NA], full_b[2], empty_b[2];
-  __shared__ __align__(8) uint64_t acc_full, acc_empty;
+  __shared__ __align__(8) uint64_t full_a[MAX_NA], empty_a[MAX_NA], full_b[MAX_NB], empty_b[MAX_NB];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.S, NA = p.na, NB = p.nb, NACC = p.nacc;
   uint8_t* sA = smem;                         // NA x 16 KB
-  uint8_t* sB = smem + NA * A_TILE;           // 2 x S x 8 KB
-  const int S = p.S;
+  uint8_t* sB = smem + NA * A_TILE;           // NB x S x 8 KB
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 wk = p.work[blockIdx.x];
   const int tm = wk.x, tn = wk.y, batch = wk.z, ks = wk.w;
@@ -219,7 +258,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nkt = (k_end - k_begin) / BK;
   const int kdt = p.kd_tiles;
   const int niv = (nkt + kdt - 1) / kdt;
-  const uint32_t ncols = S * BN <= 32 ? 32 : (S * BN <= 64 ? 64 : (S * BN <= 128 ? 128 : (S * BN <= 256 ? 256 : 512)));
+  const int used = NACC * S * TS + (BN == 128 ? BN : 0);  // + low halves for BN = 128
+  const uint32_t ncols = used <= 32 ? 32 : (used <= 64 ? 64 : (used <= 128 ? 128 : (used <= 256 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -227,12 +267,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full_a[i], 1);
       mbar_init(&empty_a[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NB; ++i) {
       mbar_init(&full_b[i], 1);
       mbar_init(&empty_b[i], 1);
     }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 8);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], EPI);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -251,25 +293,29 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !p.stall) {
-      int ia = 0;
+      int slot = 0, aphase = 0, bb = 0, bphase = 0;
       for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
         const int k0 = k_begin + kt * BK;
-        const int bb = kt & 1;
-        if (!mbar_wait(&empty_b[bb], ((kt >> 1) & 1) ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER))
-          break;
+        if (!mbar_wait(&empty_b[bb], bphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) break;
         mbar_expect_tx(&full_b[bb], S * B_TILE);
         for (int t = 0; t < S; ++t)
           tma_load_3d(sB + (bb * S + t) * B_TILE, &tmB, &full_b[bb], k0, tn * BN, batch * S + t);
+        if (++bb == NB) {
+          bb = 0;
+          bphase ^= 1;
+        }
         bool ok = true;
-        for (int s = 0; s < S; ++s, ++ia) {
-          const int slot = ia % NA;
-          if (!mbar_wait(&empty_a[slot], ((ia / NA) & 1) ^ 1, &abort_flag, p.status,
-                         ERR_WAIT_PRODUCER)) {
+        for (int s = 0; s < S; ++s) {
+          if (!mbar_wait(&empty_a[slot], aphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
             ok = false;
             break;
           }
           mbar_expect_tx(&full_a[slot], A_TILE);
           tma_load_3d(sA + slot * A_TILE, &tmA, &full_a[slot], k0, tm * BM, s);
+          if (++slot == NA) {
+            slot = 0;
+            aphase ^= 1;
+          }
         }
         if (!ok) break;
       }
@@ -277,84 +323,156 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      int ia = 0;
       unsigned first = 0;
+      int slot = 0, aphase = 0, bb = 0, bphase = 0, ab = 0, accphase = 0, kin = 0;
+      uint32_t acc_base = tmem;
+      const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
       for (int kt = 0; kt < nkt; ++kt) {
-        if (kt % kdt == 0) {
-          const int iv = kt / kdt;
-          if (!mbar_wait(&acc_empty, (iv & 1) ^ 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
+        if (kin == 0) {
+          if (!mbar_wait(&acc_empty[ab], accphase ^ 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
           tc_fence_after();
           first = (1u << S) - 1;
+          acc_base = tmem + ab * S * TS;
         }
-        const int bb = kt & 1;
-        if (!mbar_wait(&full_b[bb], (kt >> 1) & 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
+        if (!mbar_wait(&full_b[bb], bphase, &abort_flag, p.status, ERR_WAIT_MMA)) break;
         bool ok = true;
-        for (int s = 0; s < S; ++s, ++ia) {
-          const int slot = ia % NA;
-          if (!mbar_wait(&full_a[slot], (ia / NA) & 1, &abort_flag, p.status, ERR_WAIT_MMA)) {
+        for (int s = 0; s < S; ++s) {
+          if (!mbar_wait(&full_a[slot], aphase, &abort_flag, p.status, ERR_WAIT_MMA)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint64_t ad = smem_desc(smem_u32(sA + slot * A_TILE));
+          const uint64_t ad = smem_desc(sA0 + slot * A_TILE);
           for (int t = 0; t + s < S; ++t) {
             const int L = s + t;
-            const uint64_t bd = smem_desc(smem_u32(sB + (bb * S + t) * B_TILE));
+            const uint64_t bd = smem_desc(sB0 + (bb * S + t) * B_TILE);
+            const uint32_t d = acc_base + L * TS;
+            mma_bf16(d, ad, bd, IDESC, (first >> L) & 1 ? 0u : 1u);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint32_t acc = (kk > 0 || !(first & (1u << L))) ? 1u : 0u;
-              mma_bf16(tmem + L * BN, ad + 2 * kk, bd + 2 * kk, acc);
-            }
+            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, IDESC, 1u);
             first &= ~(1u << L);
           }
           mma_commit(&empty_a[slot]);
+          if (++slot == NA) {
+            slot = 0;
+            aphase ^= 1;
+          }
         }
         if (!ok) break;
         mma_commit(&empty_b[bb]);
-        if (kt % kdt == kdt - 1 || kt == nkt - 1) mma_commit(&acc_full);
+        if (++bb == NB) {
+          bb = 0;
+          bphase ^= 1;
+        }
+        if (++kin == kdt || kt == nkt - 1) {
+          mma_commit(&acc_full[ab]);
+          kin = 0;
+          if (++ab == NACC) {
+            ab = 0;
+            accphase ^= 1;
+          }
+        }
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    // ---------------- epilogue (warps 2 .. 1 + BN/8) ----------------
+    // BN = 128 keeps the low halves of the double-float accumulators in the TMEM
+    // columns after the S level accumulators (registers are scarce with 576
+    // threads); BN = 64 keeps both halves in registers.  TMEM loads and stores
+    // are warp-collective, so every branch around them is warp-uniform.
+    constexpr bool kLoTmem = BN == 128;
+    constexpr int NLO = kLoTmem ? 1 : CPT;
     const int q = warp & 3;              // TMEM lane quadrant of this warp
-    const int h = (warp - 2) >> 2;       // which 32 of the 64 columns
-    float hi[32], lo[32];
+    const int h = (warp - 2) >> 2;       // which 32-column block of the BN columns
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t lo_base = lane_base + S * TS + CPT * h;  // used when kLoTmem
+    float hi[CPT], lo[NLO];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.f;
+    for (int c = 0; c < CPT; ++c) hi[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NLO; ++c) lo[c] = 0.f;
+    if (kLoTmem) {
+      const uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int c0 = 0; c0 < CPT; c0 += 8) tmem_st8(lo_base + c0, z);
+      tmem_wait_st();
+    }
     bool ok = true;
     for (int iv = 0; iv < niv; ++iv) {
-      if (!mbar_wait(&acc_full, iv & 1, &abort_flag, p.status, ERR_WAIT_EPILOGUE)) {
+      const int ab = iv % NACC;
+      const bool got = mbar_wait_sleep(&acc_full[ab], (iv / NACC) & 1, &abort_flag, p.status,
+                                       ERR_WAIT_EPILOGUE);
+      if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      for (int L = 0; L < S; ++L) {
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + L * BN + 32 * h;
-        const float sc = __int_as_float((127 - 8 * L) << 23);  // 2^-8L, exact
-        uint32_t r[32];
-        tmem_ld32(ta, r);
-        tmem_wait_ld();
+      if constexpr (kLoTmem) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) dfloat_add(hi[c], lo[c], __uint_as_float(r[c]) * sc);
+        for (int c0 = 0; c0 < CPT; c0 += 8) {
+          uint32_t lr[8];
+          tmem_ld8(lo_base + c0, lr);
+          tmem_wait_ld();
+          for (int L = 0; L < S; ++L) {
+            const float sc = __int_as_float((127 - 8 * L) << 23);  // 2^-8L, exact
+            uint32_t r[8];
+            tmem_ld8(lane_base + (ab * S + L) * TS + CPT * h + c0, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float l = __uint_as_float(lr[c]);
+              dfloat_add(hi[c0 + c], l, __uint_as_float(r[c]) * sc);
+              lr[c] = __float_as_uint(l);
+            }
+          }
+          tmem_st8(lo_base + c0, lr);
+        }
+        tmem_wait_st();
+      } else {
+        for (int L = 0; L < S; ++L) {
+          const float sc = __int_as_float((127 - 8 * L) << 23);  // 2^-8L, exact
+          const uint32_t ta = lane_base + (ab * S + L) * TS + CPT * h;
+#pragma unroll
+          for (int c0 = 0; c0 < CPT; c0 += 8) {
+            uint32_t r[8];
+            tmem_ld8(ta + c0, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              dfloat_add(hi[c0 + c], lo[(c0 + c) % NLO], __uint_as_float(r[c]) * sc);
+          }
+        }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
     }
     if (ok) {
       const int row = tm * BM + q * 32 + lane;
-      if (row < p.a_rows) {
-        const int ea = p.ea[row];
-        double2* out = p.out + (long)batch * p.out_bstride + (long)row * p.ld_row;
-        const int* eb = p.eb + (long)batch * p.eb_stride;
+      const bool row_ok = row < p.a_rows;
+      const int ea = row_ok ? p.ea[row] : 0;
+      const double ra = (row_ok && p.rsa) ? p.rsa[row] : 1.0;
+      double2* out = p.out + (long)batch * p.out_bstride + (long)(row_ok ? row : 0) * p.ld_row;
+      const int* eb = p.eb + (long)batch * p.eb_stride;
 #pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          const int col = tn * BN + 32 * h + c;
-          if (col < p.b_rows) {
+      for (int c0 = 0; c0 < CPT; c0 += 8) {
+        uint32_t lr[8];
+        if (kLoTmem) {
+          tmem_ld8(lo_base + c0, lr);  // warp-collective: before any per-row branch
+          tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) lr[c] = __float_as_uint(lo[kLoTmem ? 0 : c0 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+          const int col = tn * BN + CPT * h + c0 + c;
+          if (row_ok && col < p.b_rows) {
             const int j = col >> 1;
-            const double sc = p.alpha * pow2(ea + eb[j] - 14);
-            double re = ((double)hi[c] + (double)lo[c]) * sc;
-            double im = ((double)hi[c + 1] + (double)lo[c + 1]) * sc;
+            double sc = p.alpha * pow2(ea + eb[j] - 14) * ra;
+            if (p.rsb) sc *= p.rsb[j];
+            double re = ((double)hi[c0 + c] + (double)__uint_as_float(lr[c])) * sc;
+            double im = ((double)hi[c0 + c + 1] + (double)__uint_as_float(lr[c + 1])) * sc;
             if (p.conj) im = -im;
             double2* o = out + (long)j * p.ld_col;
             if (p.atomic) {
@@ -386,10 +504,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 __device__ __forceinline__ void cut_digits(double x, int e, int S, float* d) {
   const long long bits = __double_as_longlong(x);
   const int bexp = (int)((bits >> 52) & 0x7FF);
+  const int F = 7 + 8 * (S - 1);
   long long Y = 0;
   if (bexp != 0) {  // zero and subnormals give zero digits
     const long long mant = (bits & ((1LL << 52) - 1)) | (1LL << 52);
-    const int sh = bexp - 1075 + 7 + 8 * (S - 1) - e;  // Y = mant 2^sh
+    const int sh = bexp - 1075 + F - e;  // Y = mant 2^sh
     if (sh >= 0)
       Y = mant << sh;  // < 2^(7 + 8(S-1)) <= 2^63 since |x| < 2^e
     else if (sh > -63)
@@ -424,16 +543,16 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) 
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
-// chi0 operand X[vc][g] = sf[vc] sv[g] A[vc][g]: row maxima over vc per g.
+// chi0 operand X[vc][g] = sf[vc] A[vc][g] (v^1/2 is applied per output row in
+// the GEMM epilogue): row maxima over vc per g.
 __global__ void chi0_rowmax_kernel(const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                                   const double* sv, unsigned long long* rowmax) {
+                                   unsigned long long* rowmax) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_g) return;
-  const double w = sv[g];
   double m = 0.0;
   for (int vc = blockIdx.y; vc < n_vc; vc += gridDim.y) {
     double2 a = load_any(A, dtype, (long)vc * n_g + g);
-    double s = sf[vc] * w;
+    double s = sf[vc];
     m = fmax(m, fmax(fabs(a.x * s), fabs(a.y * s)));
   }
   atomic_max_pos(rowmax + g, m);
@@ -444,8 +563,8 @@ __global__ void chi0_rowmax_kernel(const void* A, int dtype, int n_vc, int n_g, 
 // Im chi = X_g . Y_h.  One 32 x 32 (vc, g) tile per block, transposed through
 // shared memory so that the plane rows are written contiguously.
 __global__ void chi0_slice_kernel(const void* A, int dtype, int n_vc, int n_g, int n_g_pad,
-                                  long K, const double* sf, const double* sv,
-                                  const unsigned long long* rowmax, int S,
+                                  long K, const double* sf, const unsigned long long* rowmax,
+                                  int S,
                                   __nv_bfloat162* planes, int* exps) {
   __shared__ double2 t[32][33];
   __shared__ int es[32];
@@ -462,7 +581,7 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, int n_vc, int n_g, i
     double2 x = make_double2(0.0, 0.0);
     if (vc < n_vc && g < n_g) {
       x = load_any(A, dtype, (long)vc * n_g + g);
-      double s = sf[vc] * sv[g];
+      double s = sf[vc];
       x.x *= s;
       x.y *= s;
     }
@@ -487,17 +606,18 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, int n_vc, int n_g, i
   }
 }
 
-// Generic row slicing: row r of a complex matrix (row stride `ld` complex
-// elements, n_cplx valid elements) scaled by `scale` (may be NULL), planes
-// [S][rows_pad][K] with K index 2 k + part.  One block per row.
-__global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_rows, int n_cplx,
-                                  int rows_pad, long K, int S, __nv_bfloat162* planes, int* exps) {
+constexpr int CHUNK = 2048;  // complex elements of one row handled by one block
+
+// Row maxima max_k max(|Re x|, |Im x|) of a complex matrix (row stride `ld`
+// complex elements, n_cplx valid columns); grid (rows, column chunks).
+__global__ void row_max_kernel(const void* src, int dtype, long ld, int n_rows, int n_cplx,
+                               unsigned long long* rowmax) {
   __shared__ double red[32];
   const int r = blockIdx.x;
-  if (r >= rows_pad) return;
+  const long k0 = (long)blockIdx.y * CHUNK, k1 = min((long)n_cplx, k0 + CHUNK);
   double m = 0.0;
   if (r < n_rows)
-    for (int k = threadIdx.x; k < n_cplx; k += blockDim.x) {
+    for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
       double2 x = load_any(src, dtype, (long)r * ld + k);
       m = fmax(m, fmax(fabs(x.x), fabs(x.y)));
     }
@@ -507,13 +627,22 @@ __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_row
   if (threadIdx.x == 0) {
     double mm = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
-    red[0] = mm;
+    if (r < n_rows && mm > 0.0) atomic_max_pos(rowmax + r, mm);
   }
-  __syncthreads();
-  const int e = row_exponent(red[0]);
-  if (threadIdx.x == 0) exps[r] = e;
+}
+
+// Row slicing: planes [S][rows_pad][K] with K index 2 k + part, from the row
+// maxima; grid (rows_pad, K/2 chunks).
+__global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_rows, int n_cplx,
+                                  int rows_pad, long K, int S,
+                                  const unsigned long long* rowmax, __nv_bfloat162* planes,
+                                  int* exps) {
+  const int r = blockIdx.x;
+  const int e = r < n_rows ? row_exponent(__longlong_as_double((long long)rowmax[r])) : 0;
+  if (blockIdx.y == 0 && threadIdx.x == 0) exps[r] = e;
   const long plane = (long)rows_pad * (K / 2);
-  for (long k = threadIdx.x; k < K / 2; k += blockDim.x) {
+  const long k0 = (long)blockIdx.y * CHUNK, k1 = min(K / 2, k0 + CHUNK);
+  for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
     if (r < n_rows && k < n_cplx) x = load_any(src, dtype, (long)r * ld + k);
     float dr[MAX_SLICES], di[MAX_SLICES];
@@ -572,25 +701,24 @@ __global__ void freq_weights_kernel(const double* delta, const double* omega, in
   f[i] = 4.0 * d / (d * d + w * w);
 }
 
-// chi_s B operand of frequencies k0 .. k0+nb-1: for row j, f_k(vc) M~[j][vc]
-// as rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); one block per j.
+// Row maxima of f_b(vc) |M~[j][vc]| for the nb frequencies of a group;
+// grid (n_eig, vc chunks); rowmax[b * stride + j].
 constexpr int MAX_GROUP = 8;
-__global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
-                                    long K, const double* f, int nb, int S,
-                                    __nv_bfloat162* planes, int* exps, int eb_stride) {
+__global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const double* f,
+                                     int nb, unsigned long long* rowmax, int stride) {
   __shared__ double red[MAX_GROUP][32];
   const int j = blockIdx.x;
+  const long v0 = (long)blockIdx.y * CHUNK, v1 = min((long)n_vc, v0 + CHUNK);
   double m[MAX_GROUP];
 #pragma unroll
   for (int b = 0; b < MAX_GROUP; ++b) m[b] = 0.0;
-  if (j < n_eig)
-    for (int vc = threadIdx.x; vc < n_vc; vc += blockDim.x) {
-      const double2 x = mt[(long)j * n_vc + vc];
-      const double a = fmax(fabs(x.x), fabs(x.y));
+  for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
+    const double2 x = mt[(long)j * n_vc + vc];
+    const double a = fmax(fabs(x.x), fabs(x.y));
 #pragma unroll
-      for (int b = 0; b < MAX_GROUP; ++b)
-        if (b < nb) m[b] = fmax(m[b], f[(long)b * n_vc + vc] * a);
-    }
+    for (int b = 0; b < MAX_GROUP; ++b)
+      if (b < nb) m[b] = fmax(m[b], f[(long)b * n_vc + vc] * a);
+  }
 #pragma unroll
   for (int b = 0; b < MAX_GROUP; ++b) {
     double v = m[b];
@@ -598,16 +726,31 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
     if ((threadIdx.x & 31) == 0) red[b][threadIdx.x >> 5] = v;
   }
   __syncthreads();
+  if (threadIdx.x < nb) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[threadIdx.x][w]);
+    if (mm > 0.0) atomic_max_pos(rowmax + (long)threadIdx.x * stride + j, mm);
+  }
+}
+
+// chi_s B operand of the group's frequencies: for row j, f_b(vc) M~[j][vc] as
+// rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); grid (n_eig_pad, chunks).
+__global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
+                                    long K, const double* f, int nb, int S,
+                                    const unsigned long long* rowmax, __nv_bfloat162* planes,
+                                    int* exps, int eb_stride) {
+  const int j = blockIdx.x;
   int e[MAX_GROUP];
 #pragma unroll
   for (int b = 0; b < MAX_GROUP; ++b) {
-    double mm = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[b][w]);
-    e[b] = row_exponent(mm);
-    if (threadIdx.x == 0 && b < nb) exps[b * eb_stride + j] = e[b];
+    e[b] = (b < nb && j < n_eig)
+               ? row_exponent(__longlong_as_double((long long)rowmax[(long)b * eb_stride + j]))
+               : 0;
+    if (blockIdx.y == 0 && threadIdx.x == 0 && b < nb) exps[b * eb_stride + j] = e[b];
   }
   const long plane = (long)2 * n_eig_pad * (K / 2);
-  for (long vc = threadIdx.x; vc < K / 2; vc += blockDim.x) {
+  const long v0 = (long)blockIdx.y * CHUNK, v1 = min(K / 2, v0 + CHUNK);
+  for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
     const bool in = j < n_eig && vc < n_vc;
     if (in) x = mt[(long)j * n_vc + vc];
@@ -679,13 +822,57 @@ bool make_map(CUtensorMap* m, void* base, long K, long rows, long planes, long r
   return true;
 }
 
-size_t gemm_smem(int S) { return 1024 + NA * A_TILE + 2 * S * B_TILE; }
+// Tuning knobs of the GEMM pipeline (environment overrides for autotuning):
+// RPA_TC_NA (A ring depth), RPA_TC_NB (B buffers), RPA_TC_NACC (TMEM level
+// accumulator sets), RPA_TC_GROUP (tile rows per rasterisation group).
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+
+// MMA N for S slices: 128 when S level accumulators of 128 columns and the 128
+// columns of double-float low halves fit in TMEM (S <= 3); 96 when S levels at
+// a 128-column stride fit (S = 4); else 64.
+int pick_bn(int S) {
+  const int cap = env_int("RPA_TC_BN", 128);
+  if (cap >= 128 && (S + 1) * 128 <= 512) return 128;
+  if (cap >= 96 && S * 128 <= 512) return 96;
+  return 64;
+}
+
+// Pipeline shape for S slices: the deepest A ring and B buffering that fit in
+// shared memory (up to the knobs), two TMEM accumulator sets when they fit.
+void gemm_shape(int S, int* na, int* nb, int* nacc) {
+  const int BN = pick_bn(S);
+  const size_t B_TILE = (size_t)BN * BK * 2;
+  const int want_na = std::min(MAX_NA, std::max(2, env_int("RPA_TC_NA", MAX_NA)));
+  const int want_nb = std::min(MAX_NB, std::max(2, env_int("RPA_TC_NB", MAX_NB)));
+  const int want_acc = std::min(2, std::max(1, env_int("RPA_TC_NACC", 2)));
+  *nacc = (want_acc == 2 && BN == 64 && 2 * S * BN <= 512) ? 2 : 1;  // BN 96/128: one set
+  for (int b = want_nb; b >= 2; --b)
+    for (int a = want_na; a >= 2; --a)
+      if (1024 + (size_t)a * A_TILE + (size_t)b * S * B_TILE <= g_smem_limit) {
+        *na = a;
+        *nb = b;
+        return;
+      }
+  *na = 2;
+  *nb = 2;
+}
+
+size_t gemm_smem(int S) {
+  int na, nb, nacc;
+  gemm_shape(S, &na, &nb, &nacc);
+  return 1024 + (size_t)na * A_TILE + (size_t)nb * S * ((size_t)pick_bn(S) * BK * 2);
+}
 
 // Build the work list (upper block triangle when `upper`), choose split-K, launch.
 rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, GemmArgs a,
-                    int tiles_m, int tiles_n, int batches, bool upper, void* zero_ptr,
+                    int tiles_m, int batches, bool upper, void* zero_ptr,
                     size_t zero_bytes, cudaStream_t st, std::string& err, int* launches) {
   std::vector<int4> work;
+  const int BN = pick_bn(a.S);
+  const int tiles_n = cdiv(a.b_rows, BN);
   const int kdt = drain_tiles(a.S);
   const int kd = kdt * BK;
   int tiles = 0;
@@ -710,11 +897,16 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
     }
     a.atomic = 1;
   }
+  // Rasterised order: groups of `grp` tile rows are walked column by column, so
+  // the CTAs resident at one time share a few A row-tiles and a few B row-tiles
+  // and the operands stream from HBM about once per group instead of per row.
+  const int grp = std::max(1, env_int("RPA_TC_GROUP", 8));
   for (int b = 0; b < batches; ++b)
-    for (int m = 0; m < tiles_m; ++m)
+    for (int m0 = 0; m0 < tiles_m; m0 += grp)
       for (int n = 0; n < tiles_n; ++n)
-        if (!upper || (long)n * BN / 2 + BN / 2 - 1 >= (long)m * BM)
-          for (int s = 0; s < split; ++s) work.push_back(make_int4(m, n, b, s));
+        for (int m = m0; m < std::min(tiles_m, m0 + grp); ++m)
+          if (!upper || (long)n * BN / 2 + BN / 2 - 1 >= (long)m * BM)
+            for (int s = 0; s < split; ++s) work.push_back(make_int4(m, n, b, s));
   if (work.size() > w.work_count) {
     err = "work list exceeds workspace";
     return RPA_ENOMEM;
@@ -729,21 +921,50 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   a.work = w.work;
   a.status = w.status;
   a.stall = w.debug_stall;
-  const size_t smem = gemm_smem(a.S);
-  static size_t configured = 0;
-  if (smem > configured) {
-    e = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gemm_smem(MAX_SLICES));
-    if (e != cudaSuccess) {
-      err = cudaGetErrorString(e);
+  if (!g_smem_limit) {
+    // opt-in shared memory per block minus the kernels' static shared memory
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa64{}, fa128{}, fa96{};
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+            cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa64, slice_gemm_kernel<64>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa128, slice_gemm_kernel<128>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa96, slice_gemm_kernel<96>)) != cudaSuccess) {
+      err = std::string("querying shared memory limits: ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
-    configured = gemm_smem(MAX_SLICES);
+    size_t lim = (size_t)optin -
+                 std::max({fa64.sharedSizeBytes, fa96.sharedSizeBytes, fa128.sharedSizeBytes});
+    if ((e = cudaFuncSetAttribute(slice_gemm_kernel<64>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(slice_gemm_kernel<128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(slice_gemm_kernel<96>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
+            cudaSuccess) {
+      err = std::string("cudaFuncSetAttribute(max dynamic smem): ") + cudaGetErrorString(e);
+      return RPA_ECUDA;
+    }
+    g_smem_limit = lim;
   }
-  slice_gemm_kernel<<<(unsigned)work.size(), THREADS, smem, st>>>(ta, tb, a);
+  gemm_shape(a.S, &a.na, &a.nb, &a.nacc);
+  const size_t smem = gemm_smem(a.S);
+  if (smem > g_smem_limit) {
+    err = "slice GEMM: shared memory of the pipeline exceeds the device limit";
+    return RPA_EINVAL;
+  }
+  if (BN == 128)
+    slice_gemm_kernel<128><<<(unsigned)work.size(), threads_for<128>(), smem, st>>>(ta, tb, a);
+  else if (BN == 96)
+    slice_gemm_kernel<96><<<(unsigned)work.size(), threads_for<96>(), smem, st>>>(ta, tb, a);
+  else
+    slice_gemm_kernel<64><<<(unsigned)work.size(), threads_for<64>(), smem, st>>>(ta, tb, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
-    err = cudaGetErrorString(e);
+    err = std::string("slice GEMM launch: ") + cudaGetErrorString(e);
     return RPA_ECUDA;
   }
   if (launches) *launches += 1;
@@ -776,7 +997,7 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.plane2_bytes = p2 * 2;
   w.exp_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)e_pad}) +
                 std::max((size_t)g_pad, (size_t)grp * e_pad);
-  w.rowmax_count = g_pad;
+  w.rowmax_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)grp * e_pad});
   w.work_count = 1 << 20;
   w.fweight_count = (size_t)grp * max_vc;
   auto al = [&](void** p, size_t bytes) {
@@ -817,13 +1038,13 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
   CK(cudaMemsetAsync(w.rowmax, 0, g_pad * sizeof(unsigned long long), st));
   {
     dim3 grid(cdiv(n_g, 128), std::min(cdiv(n_vc, 64), 512));
-    chi0_rowmax_kernel<<<grid, 128, 0, st>>>(A, dtype, n_vc, n_g, sf, sv, w.rowmax);
+    chi0_rowmax_kernel<<<grid, 128, 0, st>>>(A, dtype, n_vc, n_g, sf, w.rowmax);
     CK(cudaGetLastError());
   }
   __nv_bfloat162* planes = (__nv_bfloat162*)w.planes;
   {
     dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
-    chi0_slice_kernel<<<grid, dim3(32, 8), 0, st>>>(A, dtype, n_vc, n_g, (int)g_pad, K, sf, sv,
+    chi0_slice_kernel<<<grid, dim3(32, 8), 0, st>>>(A, dtype, n_vc, n_g, (int)g_pad, K, sf,
                                                     w.rowmax, S, planes, w.exps);
     CK(cudaGetLastError());
   }
@@ -833,7 +1054,8 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
   const long plane_bytes = 2 * g_pad * K * 2;
   // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
   if (!make_map(&ta, w.planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
-  if (!make_map(&tb, w.planes, K, 2 * g_pad, S, K * 2, plane_bytes, BN, err)) return RPA_ECUDA;
+  if (!make_map(&tb, w.planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
+    return RPA_ECUDA;
   GemmArgs a{};
   a.S = S;
   a.K = (int)K;
@@ -843,15 +1065,17 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
   a.a_rows = n_g;
   a.b_rows = 2 * n_g;
   a.alpha = scale;
+  a.rsa = sv;  // chi~ = v^1/2 chi0 v^1/2: the v^1/2 factors scale rows and columns
+  a.rsb = sv;
   a.out = (double2*)chi;
   a.out_bstride = 0;
   a.ld_row = n_g;
   a.ld_col = 1;
   a.conj = 0;
   a.atomic = 0;
-  const int tiles_m = cdiv(n_g, BM), tiles_n = cdiv(2L * n_g, BN);
+  const int tiles_m = cdiv(n_g, BM);
   w.hook(RPA_T_CHI0, 1);
-  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, tiles_n, 1, true, chi,
+  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, true, chi,
                           sizeof(cplx) * (size_t)n_g * n_g, st, err, launches);
   w.hook(RPA_T_CHI0, 0);
   return r;
@@ -866,17 +1090,21 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   int* ea = w.exps;
   int* eb = w.exps + std::max({rup(n_g, BM), vc_pad, e_pad});
   w.hook(RPA_T_SLICE, 1);
-  slice_rows_kernel<<<(unsigned)vc_pad, 256, 0, st>>>(A, dtype, n_g, n_vc, n_g, (int)vc_pad, K, S,
-                                                      pa, ea);
+  CK(cudaMemsetAsync(w.rowmax, 0, vc_pad * sizeof(unsigned long long), st));
+  row_max_kernel<<<dim3((unsigned)n_vc, cdiv(n_g, CHUNK)), 256, 0, st>>>(A, dtype, n_g, n_vc, n_g,
+                                                                          w.rowmax);
+  CK(cudaGetLastError());
+  slice_rows_kernel<<<dim3((unsigned)vc_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
+      A, dtype, n_g, n_vc, n_g, (int)vc_pad, K, S, w.rowmax, pa, ea);
   CK(cudaGetLastError());
   proj_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
                                                        K, S, pb, eb);
   CK(cudaGetLastError());
-  if (launches) *launches += 2;
+  if (launches) *launches += 3;
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta, tb;
   if (!make_map(&ta, w.planes, K, vc_pad, S, K * 2, vc_pad * K * 2, BM, err)) return RPA_ECUDA;
-  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, BN, err))
+  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S), err))
     return RPA_ECUDA;
   GemmArgs a{};
   a.S = S;
@@ -893,9 +1121,9 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   a.ld_col = n_vc;
   a.conj = 1;
   a.atomic = 0;
-  const int tiles_m = cdiv(n_vc, BM), tiles_n = cdiv(2L * n_eig, BN);
+  const int tiles_m = cdiv(n_vc, BM);
   w.hook(RPA_T_PROJ, 1);
-  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, tiles_n, 1, false, mt,
+  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, false, mt,
                           sizeof(cplx) * (size_t)n_eig * n_vc, st, err, launches);
   w.hook(RPA_T_PROJ, 0);
   return r;
@@ -911,28 +1139,37 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   int* ea = w.exps;
   int* eb = w.exps + e_pad;
   w.hook(RPA_T_SLICE, 1);
-  slice_rows_kernel<<<(unsigned)e_pad, 256, 0, st>>>(mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad,
-                                                     K, S, pa, ea);
+  CK(cudaMemsetAsync(w.rowmax, 0, e_pad * sizeof(unsigned long long), st));
+  row_max_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(mt, RPA_C128, n_vc,
+                                                                            n_eig, n_vc, w.rowmax);
   CK(cudaGetLastError());
-  if (launches) *launches += 1;
+  slice_rows_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
+      mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea);
+  CK(cudaGetLastError());
+  if (launches) *launches += 2;
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta;
   if (!make_map(&ta, w.planes2, K, e_pad, S, K * 2, e_pad * K * 2, BM, err)) return RPA_ECUDA;
-  const int tiles_m = cdiv(n_eig, BM), tiles_n = cdiv(2L * n_eig, BN);
+  const int tiles_m = cdiv(n_eig, BM);
   for (int k0 = 0; k0 < n_freq; k0 += w.freq_group) {
     const int nb = std::min(w.freq_group, n_freq - k0);
     w.hook(RPA_T_SLICE, 1);
     freq_weights_kernel<<<cdiv((long)nb * n_vc, 256), 256, 0, st>>>(delta, omega, n_vc, k0, nb,
                                                                     w.fweights);
     CK(cudaGetLastError());
-    chis_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)mt, n_eig, (int)e_pad,
-                                                         n_vc, K, w.fweights, nb, S, pb, eb,
-                                                         (int)e_pad);
+    CK(cudaMemsetAsync(w.rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), st));
+    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(
+        (const double2*)mt, n_eig, n_vc, w.fweights, nb, w.rowmax, (int)e_pad);
     CK(cudaGetLastError());
-    if (launches) *launches += 2;
+    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
+        (const double2*)mt, n_eig, (int)e_pad, n_vc, K, w.fweights, nb, S, w.rowmax, pb, eb,
+        (int)e_pad);
+    CK(cudaGetLastError());
+    if (launches) *launches += 3;
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap tb;
-    if (!make_map(&tb, w.planes, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, BN, err))
+    if (!make_map(&tb, w.planes, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S),
+                  err))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
@@ -949,7 +1186,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
     a.ld_col = 1;
     a.conj = 0;
     w.hook(RPA_T_CHIS, 1);
-    rpa_status s = run_gemm(w, ta, tb, a, tiles_m, tiles_n, nb, true, a.out,
+    rpa_status s = run_gemm(w, ta, tb, a, tiles_m, nb, true, a.out,
                             sizeof(cplx) * (size_t)nb * n_eig * n_eig, st, err, launches);
     w.hook(RPA_T_CHIS, 0);
     if (s != RPA_OK) return s;
