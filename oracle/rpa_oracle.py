@@ -30,6 +30,10 @@ Readings of the paper (each listed in the design notes):
   * Frequency quadrature: Gauss-Legendre nodes x on [-1, 1], t = (x + 1)/2,
     w = s t / (1 - t), weight (w_GL / 2) * s / (1 - t)^2, s = 0.5 Ha.
 
+Extensions (next rows of the scope): pair weights w_vck = g_k (f_v - f_c) for
+partial occupations and several k-points folded into the transition axis
+(Eq. chi0_partial_occs), and an optional slab-truncated Coulomb kernel.
+
 Parity pins (tests/test_oracle_pins.py): Hermitian and negative semidefinite
 chi0; closed-form rank-1 energy; full-basis equivalence against an LU
 log-determinant of the full matrix; chi_s(0) = diag(lambda); Sylvester
@@ -53,18 +57,44 @@ def coulomb(qg2):
     return FOUR_PI / np.asarray(qg2, dtype=np.float64)
 
 
+def coulomb_slab(qg_vec, z_c):
+    """Slab-truncated Coulomb kernel: the Fourier transform of 1/r cut off at
+    |z| > z_c, for (q+G)_z on the reciprocal lattice of a cell of height 2 z_c:
+    v = 4 pi/|q+G|^2 [1 - exp(-|q+G|_par z_c) cos((q+G)_z z_c)]  (Ismail-Beigi 2006).
+    The paper's surfaces are slabs with vacuum (Computational Details); it names no
+    truncation, so this is offered as an option."""
+    k = np.asarray(qg_vec, dtype=np.float64)
+    kpar = np.hypot(k[:, 0], k[:, 1])
+    k2 = np.sum(k * k, axis=1)
+    return FOUR_PI / k2 * (1.0 - np.exp(-kpar * z_c) * np.cos(k[:, 2] * z_c))
+
+
 def transition_energies(e_v, e_c):
-    """Delta_vc = e_c - e_v, row vc = v * N_c + c (Eq. (chi0_partial_occs) index pair)."""
-    e_v = np.asarray(e_v, dtype=np.float64)
-    e_c = np.asarray(e_c, dtype=np.float64)
-    return (e_c[None, :] - e_v[:, None]).reshape(-1)
+    """Delta_vc = e_c - e_v (Eq. (chi0_partial_occs) index pair).  1-D inputs: row
+    vc = v * N_c + c; 2-D inputs [n_k][n_v], [n_k][n_c]: k-points folded into the
+    transition axis, row (k * N_v + v) * N_c + c."""
+    e_v = np.atleast_2d(np.asarray(e_v, dtype=np.float64))
+    e_c = np.atleast_2d(np.asarray(e_c, dtype=np.float64))
+    return (e_c[:, None, :] - e_v[:, :, None]).reshape(-1)
 
 
-def freq_weight(delta, omega):
-    """f_vc(w) = 4 Delta / (Delta^2 + w^2): resonant plus anti-resonant term of
-    Delta_vck(q, iw) with spin factor 2 and integer occupations (sign carried by chi0)."""
+def pair_weights(occ_v, occ_c, k_weight=None):
+    """w_vck = g_k (f_v - f_c): k-point weight times occupation difference of
+    Eq. (chi0_partial_occs) (Delta_vck's numerator up to the spin factor), in the
+    row order of transition_energies.  Integer occupations (1, 0) give 1."""
+    occ_v = np.atleast_2d(np.asarray(occ_v, dtype=np.float64))
+    occ_c = np.atleast_2d(np.asarray(occ_c, dtype=np.float64))
+    g = np.ones(occ_v.shape[0]) if k_weight is None else np.asarray(k_weight, dtype=np.float64)
+    return (g[:, None, None] * (occ_v[:, :, None] - occ_c[:, None, :])).reshape(-1)
+
+
+def freq_weight(delta, omega, ow=None):
+    """f_vc(w) = w_vc 4 Delta / (Delta^2 + w^2): resonant plus anti-resonant term of
+    Delta_vck(q, iw) with spin factor 2 (sign carried by chi0); w_vc = g_k (f_v - f_c)
+    (1 for integer occupations)."""
     delta = np.asarray(delta, dtype=np.float64)
-    return 4.0 * delta / (delta * delta + omega * omega)
+    f = 4.0 * delta / (delta * delta + omega * omega)
+    return f if ow is None else np.asarray(ow, dtype=np.float64) * f
 
 
 def frequency_grid(n_freq: int, omega_scale: float = 0.5):
@@ -81,17 +111,17 @@ def frequency_grid(n_freq: int, omega_scale: float = 0.5):
 
 # --- full-basis polarizability ---------------------------------------------
 
-def chi0(A, delta, omega, omega_cell):
+def chi0(A, delta, omega, omega_cell, ow=None):
     """chi0_GG'(q, iw) = -(1/Omega) sum_vc f_vc(w) conj(M_vc(G)) M_vc(G')  (Eq. chi0_partial_occs)."""
     A = np.asarray(A, dtype=np.complex128)
-    f = freq_weight(delta, omega)
+    f = freq_weight(delta, omega, ow)
     return -(A.conj().T @ (f[:, None] * A)) / omega_cell
 
 
-def chi_tilde(A, qg2, delta, omega, omega_cell):
-    """chi~ = v^1/2 chi0 v^1/2, Hermitised as (X + X^H)/2."""
-    s = np.sqrt(coulomb(qg2))
-    x = s[:, None] * chi0(A, delta, omega, omega_cell) * s[None, :]
+def chi_tilde(A, qg2, delta, omega, omega_cell, ow=None, vg=None):
+    """chi~ = v^1/2 chi0 v^1/2, Hermitised as (X + X^H)/2 (vg: Coulomb kernel, default bare)."""
+    s = np.sqrt(coulomb(qg2) if vg is None else np.asarray(vg, dtype=np.float64))
+    x = s[:, None] * chi0(A, delta, omega, omega_cell, ow) * s[None, :]
     return 0.5 * (x + x.conj().T)
 
 
@@ -115,21 +145,21 @@ def subspace_basis(chit, n_eig):
     return lam[:n_eig].copy(), canonical_gauge(vec[:, :n_eig]), lam
 
 
-def project(A, qg2, C):
+def project(A, qg2, C, vg=None):
     """Projected matrix elements M~ = (A v^1/2 C)^H, shape [N_eig, N_vc]  (M_s = M C_s)."""
-    B = np.sqrt(coulomb(qg2))[:, None] * C
+    B = np.sqrt(coulomb(qg2) if vg is None else np.asarray(vg, dtype=np.float64))[:, None] * C
     return (np.asarray(A, dtype=np.complex128) @ B).conj().T
 
 
-def chi_s(Mt, delta, omega, omega_cell):
+def chi_s(Mt, delta, omega, omega_cell, ow=None):
     """Subspace polarizability chi_s(iw) = -(1/Omega) M~ diag(f(w)) M~^H  (chi0_s = M_s^+ Delta M_s)."""
-    f = freq_weight(delta, omega)
+    f = freq_weight(delta, omega, ow)
     return -(Mt * f[None, :]) @ Mt.conj().T / omega_cell
 
 
-def trace_term(Mt, delta, omega, omega_cell):
+def trace_term(Mt, delta, omega, omega_cell, ow=None):
     """Tr chi_s(iw) = -(1/Omega) sum_vc f_vc(w) ||M~[:, vc]||^2 (the chi0 v term of Eq. rpaE)."""
-    f = freq_weight(delta, omega)
+    f = freq_weight(delta, omega, ow)
     return -float(np.sum(f * np.sum(np.abs(Mt) ** 2, axis=0))) / omega_cell
 
 
@@ -149,28 +179,30 @@ def logdet_cholesky(chis):
 
 # --- the whole path ----------------------------------------------------------
 
-def ecorr(A, qg2, e_v, e_c, omega_cell, n_eig, n_freq, omega_scale=0.5, keep=False):
+def ecorr(A, qg2, e_v, e_c, omega_cell, n_eig, n_freq, omega_scale=0.5, keep=False, ow=None,
+          vg=None):
     """Static-subspace RPA correlation energy of one q-point (Method + Implementation).
 
     Steps in the paper's order: chi0(0) -> chi~(0) -> C_s -> M~ -> chi_s(iw_k)
     for every quadrature node -> eigenvalues -> E_c = (1/2pi) sum_k w_k sum [ln(1-l)+l].
+    ow: pair weights g_k (f_v - f_c) (default 1); vg: Coulomb kernel (default bare).
     Returns a dict with E_c and (if ``keep``) every intermediate.
     """
     delta = transition_energies(e_v, e_c)
-    chit = chi_tilde(A, qg2, delta, 0.0, omega_cell)
+    chit = chi_tilde(A, qg2, delta, 0.0, omega_cell, ow, vg)
     lam0, C, lam_all = subspace_basis(chit, n_eig)
-    Mt = project(A, qg2, C)
+    Mt = project(A, qg2, C, vg)
     omega, weight = frequency_grid(n_freq, omega_scale)
     lam_k = np.empty((n_freq, n_eig))
     trace_k = np.empty(n_freq)
     e_k = np.empty(n_freq)
     chis_all = [] if keep else None
     for k in range(n_freq):
-        chis = chi_s(Mt, delta, omega[k], omega_cell)
+        chis = chi_s(Mt, delta, omega[k], omega_cell, ow)
         chis = 0.5 * (chis + chis.conj().T)
         lam = np.linalg.eigvalsh(chis)
         lam_k[k] = lam
-        trace_k[k] = trace_term(Mt, delta, omega[k], omega_cell)
+        trace_k[k] = trace_term(Mt, delta, omega[k], omega_cell, ow)
         e_k[k] = float(np.sum(np.log1p(-lam))) + trace_k[k]
         if keep:
             chis_all.append(chis)
@@ -183,14 +215,14 @@ def ecorr(A, qg2, e_v, e_c, omega_cell, n_eig, n_freq, omega_scale=0.5, keep=Fal
     return out
 
 
-def ecorr_full_basis(A, qg2, e_v, e_c, omega_cell, n_freq, omega_scale=0.5):
+def ecorr_full_basis(A, qg2, e_v, e_c, omega_cell, n_freq, omega_scale=0.5, ow=None, vg=None):
     """E_c of Eq. (rpaE) in the full G basis, trace of the log by an LU
     log-determinant: Tr ln(1 - chi0 v) = ln det(1 - chi~) (Implementation)."""
     delta = transition_energies(e_v, e_c)
     omega, weight = frequency_grid(n_freq, omega_scale)
     tot = 0.0
     for k in range(n_freq):
-        x = chi_tilde(A, qg2, delta, omega[k], omega_cell)
+        x = chi_tilde(A, qg2, delta, omega[k], omega_cell, ow, vg)
         sign, ld = np.linalg.slogdet(np.eye(x.shape[0]) - x)
         tot += weight[k] * (ld + float(np.real(np.trace(x))))
     return tot / (2.0 * math.pi)

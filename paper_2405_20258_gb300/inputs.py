@@ -86,6 +86,7 @@ class QPoint:
     seed: int = DEFAULT_SEED
     q_twentieths: tuple = (1, 0, 0)
     a: float = 10.0
+    n_k: int = 1                 # k-points folded into the transition axis
     meta: dict = field(default_factory=dict)
 
     @property
@@ -94,11 +95,15 @@ class QPoint:
 
     @property
     def n_v(self):
-        return int(self.e_v.shape[0])
+        return int(self.e_v.shape[-1])
 
     @property
     def n_c(self):
-        return int(self.e_c.shape[0])
+        return int(self.e_c.shape[-1])
+
+    @property
+    def n_vc(self):
+        return self.n_k * self.n_v * self.n_c
 
     @property
     def omega_cell(self):
@@ -155,7 +160,14 @@ def matrix_elements(qp: QPoint, v_range=None, c_range=None, dtype=np.complex128)
     """A[vc, g] = M_vc(G_g) for v in v_range, c in c_range (row vc = v*n_c' + c).
 
     Returns an array of shape [len(v_range)*len(c_range), n_g], G contiguous.
+    With n_k > 1 k-points (and no ranges) the rows are [k][v][c]; the bands of
+    k-point k carry the generator indices k*n_v + v and k*n_c + c.
     """
+    if qp.n_k > 1 and v_range is None and c_range is None:
+        return np.concatenate([
+            matrix_elements(qp, np.arange(k * qp.n_v, (k + 1) * qp.n_v),
+                            np.arange(k * qp.n_c, (k + 1) * qp.n_c), dtype)
+            for k in range(qp.n_k)])
     vr = np.arange(qp.n_v) if v_range is None else np.asarray(v_range)
     cr = np.arange(qp.n_c) if c_range is None else np.asarray(c_range)
     pg = pack_miller(qp.miller)
@@ -174,11 +186,26 @@ def matrix_elements(qp: QPoint, v_range=None, c_range=None, dtype=np.complex128)
 
 
 def make_qpoint(n_g: int, n_v: int, n_c: int, seed: int = DEFAULT_SEED, iq: int = 0,
-                q_twentieths=(1, 0, 0), a: float = 10.0) -> QPoint:
+                q_twentieths=(1, 0, 0), a: float = 10.0, n_k: int = 1) -> QPoint:
+    """One synthetic q-point; with n_k > 1 the band energies are [n_k][n_v], [n_k][n_c]."""
     miller, qg2 = gvectors(n_g, q_twentieths, a)
-    e_v, e_c = band_energies(seed, n_v, n_c, iq)
+    e_v, e_c = band_energies(seed, n_k * n_v, n_k * n_c, iq)
+    if n_k > 1:
+        e_v, e_c = e_v.reshape(n_k, n_v), e_c.reshape(n_k, n_c)
     return QPoint(miller=miller, qg2=qg2, e_v=e_v, e_c=e_c, iq=iq, seed=seed,
-                  q_twentieths=tuple(int(x) for x in q_twentieths), a=a)
+                  q_twentieths=tuple(int(x) for x in q_twentieths), a=a, n_k=n_k)
+
+
+def fermi_occupations(e, mu: float, sigma: float) -> np.ndarray:
+    """Fermi-Dirac occupations 1/(1 + exp((e - mu)/sigma)) of band energies (Ha):
+    the smeared occupations a DFT run hands to the RPA step."""
+    return 1.0 / (1.0 + np.exp((np.asarray(e, dtype=np.float64) - mu) / sigma))
+
+
+def qg_vectors(qp: QPoint) -> np.ndarray:
+    """Cartesian q+G (bohr^-1) of the q-point's plane waves, [n_g][3]."""
+    q = np.asarray(qp.q_twentieths, dtype=np.float64) / 20.0
+    return (q[None, :] + qp.miller.astype(np.float64)) * (2.0 * math.pi / qp.a)
 
 
 def qgrid_4x4x4():

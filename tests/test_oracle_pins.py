@@ -226,9 +226,10 @@ def test_pins_pass_unmutated():
 def test_planted_mistake_is_caught(monkeypatch, mutation):
     if mutation == "transpose_chi0":
         orig = orc.chi0
-        monkeypatch.setattr(orc, "chi0", lambda A, d, o, om: orig(A, d, o, om).T)
+        monkeypatch.setattr(orc, "chi0", lambda *a, **k: orig(*a, **k).T)
     elif mutation == "drop_antiresonant":
-        monkeypatch.setattr(orc, "freq_weight", lambda d, o: 2.0 * np.asarray(d) / (np.asarray(d) ** 2 + o * o))
+        monkeypatch.setattr(orc, "freq_weight",
+                            lambda d, o, ow=None: 2.0 * np.asarray(d) / (np.asarray(d) ** 2 + o * o))
     elif mutation == "wrong_weight_jacobian":
         orig = orc.frequency_grid
         def fg(n, s=0.5):
@@ -237,8 +238,8 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
         monkeypatch.setattr(orc, "frequency_grid", fg)
     elif mutation == "project_no_conj":
         monkeypatch.setattr(orc, "project",
-                            lambda A, qg2, C: (np.asarray(A) @ (np.sqrt(orc.coulomb(qg2))[:, None] * C)).T)
+                            lambda A, qg2, C, vg=None: (np.asarray(A) @ (np.sqrt(orc.coulomb(qg2))[:, None] * C)).T)
     elif mutation == "sign_trace":
         orig = orc.trace_term
-        monkeypatch.setattr(orc, "trace_term", lambda *a: -orig(*a))
+        monkeypatch.setattr(orc, "trace_term", lambda *a, **k: -orig(*a, **k))
     assert _run_pins() > 0
