@@ -11,10 +11,11 @@
  *   chi_s(k) = -(1/Omega) M~ diag(f(w_k)) M~^H           Method, chi0_s = M_s^+ Delta M_s
  *   E_c      = (1/2pi) sum_k w_k sum_i [ln(1 - l_ki) + l_ki]   Eq. (rpaE), trace in the subspace
  *
- * with A[vc][g] = M_vc(G_g) (Eq. pwMat), row vc = v*n_c + c, and the transition
- * weight f_vc(w) = 4 D_vc / (D_vc^2 + w^2), D_vc = e_c[c] - e_v[v]: the
- * resonant and anti-resonant terms of Delta_vck(q, iw) for integer
- * occupations with the spin factor 2.  The frequencies w_k, weights are
+ * with A[vc][g] = M_vc(G_g) (Eq. pwMat), row vc = v*n_c + c (k-points first when
+ * there are several), and the transition weight f_vc(w) = w_vc 4 D_vc /
+ * (D_vc^2 + w^2), D_vc = e_c[c] - e_v[v], w_vc = g_k (f_v - f_c) (1 for integer
+ * occupations): the resonant and anti-resonant terms of Delta_vck(q, iw) with
+ * the spin factor 2.  The frequencies w_k, weights are
  * Gauss-Legendre points on [0,1] mapped by w = s t/(1-t) (Computational Details).
  *
  * Conventions shared by every entry point
@@ -63,6 +64,13 @@ typedef enum {
 
 typedef enum { RPA_C128 = 0, RPA_C64 = 1 } rpa_dtype;
 
+typedef enum {
+  RPA_COULOMB_BARE = 0,  /* v = 4 pi/|q+G|^2 (the interaction of Eq. rpaE)                  */
+  RPA_COULOMB_SLAB = 1   /* 1/r cut off at |z| > z_c: v = 4 pi/|q+G|^2 [1 - exp(-|q+G|_par z_c)
+                            cos((q+G)_z z_c)] for (q+G)_z on the lattice of a cell of height
+                            2 z_c (for slabs; the paper names no truncation)              */
+} rpa_coulomb;
+
 /* One q-point.  Arrays are device memory owned by the caller and must stay
  * valid and unchanged until the plan is destroyed. */
 typedef struct {
@@ -80,6 +88,18 @@ typedef struct {
   int iq;                  /* q index fed to the generator (m == NULL)              */
   unsigned long long seed; /* generator seed (m == NULL)                            */
   const int* miller;       /* [n_g][3] Miller indices of G (m == NULL)              */
+  /* k-points and occupations, Eq. (chi0_partial_occs): every transition carries the
+     pair weight w = g_k (f_v - f_c); zero / NULL fields give one k-point and integer
+     occupations (w = 1).  w * Delta must be >= 0, and Delta != 0 where w != 0. */
+  int n_k;                 /* k-points folded into the transitions (0 means 1): e_v is
+                              then [n_k][n_v], e_c [n_k][n_c], m [n_k][n_v][n_c][n_g]
+                              (the generator draws band indices k*n_v+v, k*n_c+c)     */
+  const double* k_weight;  /* [n_k] g_k (device); NULL: 1 for every k-point          */
+  const double* occ_v;     /* [n_k][n_v] occupations f_v (device); NULL: 1           */
+  const double* occ_c;     /* [n_k][n_c] occupations f_c (device); NULL: 0           */
+  int coulomb;             /* rpa_coulomb                                            */
+  double slab_zc;          /* RPA_COULOMB_SLAB: z_c > 0 (bohr)                       */
+  const double* qg_vec;    /* RPA_COULOMB_SLAB: [n_g][3] Cartesian q+G (bohr^-1, device) */
 } rpa_qpoint;
 
 typedef struct {

@@ -46,7 +46,7 @@ struct rpa_plan_s {
   int max_g = 0, max_eig = 0, max_freq = 0;
   long max_vc = 0;
   // device workspace
-  double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr;
+  double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr, *ow = nullptr;
   double *omega = nullptr, *weight = nullptr;  // [n_q][max_freq]
   double *lam_all = nullptr, *lam = nullptr, *trace = nullptr, *ec = nullptr, *logdet = nullptr;
   int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
@@ -124,7 +124,8 @@ void free_plan(rpa_plan_t p) {
   for (auto e : p->open_ev)
     if (e) cudaEventDestroy(e);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
-  void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->omega, p->weight, p->lam_all,
+  void* bufs[] = {p->sv,   p->delta, p->sf0,       p->w,     p->ow,    p->omega, p->weight,
+                  p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
                   p->infos};
@@ -195,7 +196,12 @@ rpa_status check_qpoint(const rpa_qpoint& q, int i) {
   };
   if (q.n_g < 1) return bad("n_g must be >= 1");
   if (q.n_v < 1 || q.n_c < 1) return bad("n_v and n_c must be >= 1");
-  if ((long)q.n_v * q.n_c > (1L << 31) - 1) return bad("n_v*n_c too large");
+  if (q.n_k < 0) return bad("n_k must be >= 0");
+  if (rpa::n_transitions(q) > (1L << 31) - 1) return bad("n_k*n_v*n_c too large");
+  if (q.coulomb != RPA_COULOMB_BARE && q.coulomb != RPA_COULOMB_SLAB)
+    return bad("unknown coulomb kernel");
+  if (q.coulomb == RPA_COULOMB_SLAB && (!q.qg_vec || !(q.slab_zc > 0.0)))
+    return bad("the slab Coulomb kernel needs qg_vec and slab_zc > 0");
   if (q.n_eig < 1 || q.n_eig > q.n_g) return bad("n_eig must be in [1, n_g]");
   if (q.n_freq < 1 || q.n_freq > 256) return bad("n_freq must be in [1, 256]");
   if (!(q.omega_cell > 0.0) || !std::isfinite(q.omega_cell)) return bad("omega_cell must be > 0");
@@ -223,8 +229,14 @@ rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
   }
   if (p->gen_iq != iq) {
     StageTimer t(p, RPA_T_OTHER);
-    CU(p, rpa::launch_generate_m(&q, 0, q.n_v, 0, q.n_c, p->gen_a, q.m_dtype, p->st));
-    p->launches += 1;
+    const int n_k = q.n_k > 1 ? q.n_k : 1;
+    const size_t blk = (size_t)q.n_v * q.n_c * q.n_g * (q.m_dtype == RPA_C64 ? 8 : 16);
+    for (int k = 0; k < n_k; ++k) {
+      // k-point k draws the generator's band indices k*n_v + v and k*n_c + c
+      CU(p, rpa::launch_generate_m(&q, k * q.n_v, q.n_v, k * q.n_c, q.n_c,
+                                   (char*)p->gen_a + k * blk, q.m_dtype, p->st));
+      p->launches += 1;
+    }
     p->gen_iq = iq;
   }
   *a = p->gen_a;
@@ -249,15 +261,20 @@ rpa_status prepare(rpa_plan_t p, int iq) {
   CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
   {
     StageTimer t(p, RPA_T_OTHER);
-    CU(p, rpa::launch_prepare_scalars(q.qg2, q.n_g, q.e_v, q.n_v, q.e_c, q.n_c, p->sv, p->delta,
-                                      p->sf0, p->flags, p->st));
+    CU(p, rpa::launch_prepare_scalars(q, p->sv, p->delta, p->ow, p->sf0, p->flags, p->st));
     p->launches += 1;
   }
   int h = 0;
   CU(p, cudaMemcpyAsync(&h, p->flags, sizeof(int), cudaMemcpyDeviceToHost, p->st));
   CU(p, cudaStreamSynchronize(p->st));
   if (h & 1) return fail(p, RPA_EINVAL, "q-point %d: |q+G|^2 must be finite and > 0", iq);
-  if (h & 2) return fail(p, RPA_EINVAL, "q-point %d: e_c[c] - e_v[v] must be finite and > 0", iq);
+  if (h & 2) return fail(p, RPA_EINVAL, "q-point %d: e_c[c] - e_v[v] must be finite", iq);
+  if (h & 4)
+    return fail(p, RPA_EINVAL,
+                "q-point %d: pair weights g_k (f_v - f_c) must be finite, of the sign of "
+                "e_c - e_v, and zero where e_c = e_v",
+                iq);
+  if (h & 8) return fail(p, RPA_EINVAL, "q-point %d: slab Coulomb kernel not positive", iq);
   return RPA_OK;
 }
 
@@ -317,7 +334,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     p->max_g = std::max(p->max_g, q[i].n_g);
     p->max_eig = std::max(p->max_eig, q[i].n_eig);
     p->max_freq = std::max(p->max_freq, q[i].n_freq);
-    long nvc = (long)q[i].n_v * q[i].n_c;
+    long nvc = rpa::n_transitions(q[i]);
     p->max_vc = std::max(p->max_vc, nvc);
     if (!q[i].m) {
       need_gen = true;
@@ -338,6 +355,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   ALLOC(delta, V);
   ALLOC(sf0, V);
   ALLOC(w, V);
+  ALLOC(ow, V);
   ALLOC(omega, (size_t)n_q * F);
   ALLOC(weight, (size_t)n_q * F);
   ALLOC(lam_all, G);
@@ -483,7 +501,7 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   int dt;
   s = matrix_a(p, iq, &A, &dt);
   if (s != RPA_OK) return s;
-  const long n_vc = (long)q.n_v * q.n_c;
+  const long n_vc = rpa::n_transitions(q);
   const double scale = -1.0 / q.omega_cell;
   if (p->opt.precision == RPA_MIXED) {
     int nl = 0;
@@ -555,14 +573,15 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   int dt;
   s = matrix_a(p, iq, &A, &dt);
   if (s != RPA_OK) return s;
-  const int n_vc = q.n_v * q.n_c, E = q.n_eig, F = q.n_freq;
+  const int n_vc = (int)rpa::n_transitions(q), E = q.n_eig, F = q.n_freq;
   const double scale = -1.0 / q.omega_cell;
   const double* om = p->omega + (size_t)iq * p->max_freq;
   if (p->opt.precision == RPA_MIXED) {
     int nl = 0;
     s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
     if (s != RPA_OK) return s;
-    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st, p->err,
+    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, p->ow, om, F, scale, p->chis, p->st,
+                      p->err,
                       &nl);
     if (s != RPA_OK) return s;
     p->launches += nl;
@@ -573,7 +592,8 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
     }
     {
       StageTimer t(p, RPA_T_CHIS);
-      CU(p, rpa::launch_chis_fp64(p->mt, E, n_vc, p->delta, om, F, scale, p->chis, p->st));
+      CU(p, rpa::launch_chis_fp64(p->mt, E, n_vc, p->delta, p->ow, om, F, scale, p->chis,
+                                  p->st));
     }
     p->launches += 2;
   }
@@ -583,7 +603,8 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   }
   {
     StageTimer t(p, RPA_T_TRACE);
-    CU(p, rpa::launch_trace(p->mt, E, n_vc, p->delta, om, F, scale, p->w, p->trace, p->st));
+    CU(p, rpa::launch_trace(p->mt, E, n_vc, p->delta, p->ow, om, F, scale, p->w, p->trace,
+                            p->st));
   }
   p->launches += 3;
   if (mt_out)

@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const void* __restrict
 // (chi0_s = M_s^+ Delta M_s of the Method section, one launch for every frequency).
 __global__ void __launch_bounds__(NT) chis_fp64_kernel(const cplx* __restrict__ mt, int n_eig,
                                                        int n_vc, const double* __restrict__ delta,
+                                                       const double* __restrict__ ow,
                                                        const double* __restrict__ omega,
                                                        int n_freq, double scale,
                                                        cplx* __restrict__ chis, int nb,
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(NT) chis_fp64_kernel(const cplx* __restrict__ 
     if (threadIdx.x < BK) {
       int vc = vb + threadIdx.x;
       double d = vc < v1 ? delta[vc] : 1.0;
-      fk[threadIdx.x] = vc < v1 ? 4.0 * d / (d * d + w2) : 0.0;
+      double o = vc < v1 ? ow[vc] : 0.0;
+      fk[threadIdx.x] = o != 0.0 ? o * (4.0 * d / (d * d + w2)) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -328,8 +330,8 @@ cudaError_t launch_project_fp64(const void* A, int a_dtype, int n_vc, int n_g, c
 }
 
 cudaError_t launch_chis_fp64(const cplx* mt, int n_eig, int n_vc, const double* delta,
-                             const double* omega, int n_freq, double scale, cplx* chis,
-                             cudaStream_t st) {
+                             const double* ow, const double* omega, int n_freq, double scale,
+                             cplx* chis, cudaStream_t st) {
   int nb = ceil_div(n_eig, TILE);
   int tiles = nb * (nb + 1) / 2;
   int want = 152 * 6;
@@ -343,8 +345,8 @@ cudaError_t launch_chis_fp64(const cplx* mt, int n_eig, int n_vc, const double* 
     if (e != cudaSuccess) return e;
   }
   dim3 grid(tiles, n_freq * split);
-  chis_fp64_kernel<<<grid, NT, 0, st>>>(mt, n_eig, n_vc, delta, omega, n_freq, scale, chis, nb,
-                                        split, kchunk, split > 1);
+  chis_fp64_kernel<<<grid, NT, 0, st>>>(mt, n_eig, n_vc, delta, ow, omega, n_freq, scale, chis,
+                                        nb, split, kchunk, split > 1);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,11 @@ struct cplx {
   double re, im;
 };
 
+// Transitions of a q-point: k-points x valence x conduction.
+inline long n_transitions(const rpa_qpoint& q) {
+  return (long)(q.n_k > 1 ? q.n_k : 1) * q.n_v * q.n_c;
+}
+
 // ---- FP64 SIMT contractions (rpa_fp64.cu) ---------------------------------
 
 // chi[g][h] (+)= -(1/Omega) sum_vc conj(X[vc,g]) X[vc,h],  X = sf[vc] sv[g] A[vc,g].
@@ -26,10 +31,11 @@ cudaError_t launch_herk_fp64(const void* A, int a_dtype, int n_vc, int n_g, cons
 cudaError_t launch_project_fp64(const void* A, int a_dtype, int n_vc, int n_g, const cplx* B,
                                 int n_eig, cplx* mt, cudaStream_t st);
 
-// chis[k][i][j] (+)= scale sum_vc f_k(vc) mt[i][vc] conj(mt[j][vc]) for all k; upper triangle.
+// chis[k][i][j] (+)= scale sum_vc f_k(vc) mt[i][vc] conj(mt[j][vc]) for all k; upper triangle;
+// f_k(vc) = ow[vc] 4 D/(D^2 + w_k^2).
 cudaError_t launch_chis_fp64(const cplx* mt, int n_eig, int n_vc, const double* delta,
-                             const double* omega, int n_freq, double scale, cplx* chis,
-                             cudaStream_t st);
+                             const double* ow, const double* omega, int n_freq, double scale,
+                             cplx* chis, cudaStream_t st);
 
 // Fill the strictly lower triangle of `batch` n x n Hermitian matrices from the upper one,
 // and zero the imaginary part of the diagonal.
@@ -37,8 +43,10 @@ cudaError_t launch_mirror_hermitian(cplx* m, int n, int batch, cudaStream_t st);
 
 // ---- small kernels (rpa_small.cu) -------------------------------------------
 
-cudaError_t launch_prepare_scalars(const double* qg2, int n_g, const double* e_v, int n_v,
-                                   const double* e_c, int n_c, double* sv, double* delta,
+// Per q-point scalars: sv[g] = sqrt(v(G)) (bare or slab-truncated), and per
+// transition delta = e_c - e_v, pair weight ow = g_k (f_v - f_c), sf0 = sqrt(f(0)).
+// bad |= 1 (|q+G|^2), 2 (transition energy), 4 (pair weight sign), 8 (slab kernel).
+cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delta, double* ow,
                                    double* sf0, int* bad, cudaStream_t st);
 cudaError_t launch_freq_grid(int n_freq, double s, double* omega, double* weight,
                              cudaStream_t st);
@@ -47,8 +55,8 @@ cudaError_t launch_gauge(const cplx* U, int ldu, int n_g, int n_eig, const doubl
                          cplx* B, cudaStream_t st);
 // w[vc] = sum_i |mt[i][vc]|^2 ; trace[k] = scale sum_vc f_k(vc) w[vc]
 cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delta,
-                         const double* omega, int n_freq, double scale, double* w,
-                         double* trace, cudaStream_t st);
+                         const double* ow, const double* omega, int n_freq, double scale,
+                         double* w, double* trace, cudaStream_t st);
 // ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam[k][i]) + trace_k]; bad |= 1 if 1 - lam <= 0.
 cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
                           const double* trace, const double* weight, double* ec, int* bad,

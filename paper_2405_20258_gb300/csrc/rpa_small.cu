@@ -35,24 +35,41 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
-// sv[g] = sqrt(4 pi / |q+G|^2); delta[vc] = e_c[c] - e_v[v]; sf0[vc] = sqrt(f_vc(0)) = sqrt(4/delta)
-__global__ void prepare_kernel(const double* qg2, int n_g, const double* e_v, int n_v,
-                               const double* e_c, int n_c, double* sv, double* delta,
-                               double* sf0, int* bad) {
-  long n_vc = (long)n_v * n_c;
+// sv[g] = sqrt(v(q+G)) with the bare or the slab-truncated Coulomb kernel;
+// per transition vc = (k n_v + v) n_c + c: delta = e_c - e_v, pair weight
+// ow = g_k (f_v - f_c) (Eq. chi0_partial_occs), sf0 = sqrt(ow f(0)) = sqrt(4 ow / delta).
+__global__ void prepare_kernel(rpa_qpoint q, double* sv, double* delta, double* ow, double* sf0,
+                               int* bad) {
+  const int n_k = q.n_k > 1 ? q.n_k : 1;
+  const long per_k = (long)q.n_v * q.n_c;
+  const long n_vc = n_k * per_k;
   long stride = (long)gridDim.x * blockDim.x;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_g + n_vc; i += stride) {
-    if (i < n_g) {
-      double q = qg2[i];
-      if (!(q > 0.0) || !isfinite(q)) atomicOr(bad, 1);
-      sv[i] = sqrt(4.0 * kPi / q);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < q.n_g + n_vc; i += stride) {
+    if (i < q.n_g) {
+      double k2 = q.qg2[i];
+      if (!(k2 > 0.0) || !isfinite(k2)) atomicOr(bad, 1);
+      double v = 4.0 * kPi / k2;
+      if (q.coulomb == RPA_COULOMB_SLAB) {
+        const double* kv = q.qg_vec + 3 * i;
+        double kpar = hypot(kv[0], kv[1]);
+        v *= 1.0 - exp(-kpar * q.slab_zc) * cos(kv[2] * q.slab_zc);
+        if (!(v > 0.0) || !isfinite(v)) atomicOr(bad, 8);
+      }
+      sv[i] = sqrt(v);
     } else {
-      long vc = i - n_g;
-      int v = (int)(vc / n_c), c = (int)(vc % n_c);
-      double d = e_c[c] - e_v[v];
-      if (!(d > 0.0) || !isfinite(d)) atomicOr(bad, 2);
+      long vc = i - q.n_g;
+      int k = (int)(vc / per_k);
+      long r = vc % per_k;
+      int v = (int)(r / q.n_c), c = (int)(r % q.n_c);
+      double d = q.e_c[(long)k * q.n_c + c] - q.e_v[(long)k * q.n_v + v];
+      double fv = q.occ_v ? q.occ_v[(long)k * q.n_v + v] : 1.0;
+      double fc = q.occ_c ? q.occ_c[(long)k * q.n_c + c] : 0.0;
+      double w = (q.k_weight ? q.k_weight[k] : 1.0) * (fv - fc);
+      if (!isfinite(d)) atomicOr(bad, 2);
+      if (!isfinite(w) || w * d < 0.0 || (d == 0.0 && w != 0.0)) atomicOr(bad, 4);
       delta[vc] = d;
-      sf0[vc] = sqrt(4.0 / d);
+      ow[vc] = w;
+      sf0[vc] = w != 0.0 ? sqrt(4.0 * w / d) : 0.0;
     }
   }
 }
@@ -163,15 +180,15 @@ __global__ void colnorm_kernel(const cplx* mt, int n_eig, int n_vc, double* w) {
 }
 
 // trace[k] = scale sum_vc f_k(vc) w[vc]; one block per frequency, fixed order.
-__global__ void trace_kernel(const double* w, const double* delta, int n_vc,
+__global__ void trace_kernel(const double* w, const double* delta, const double* ow, int n_vc,
                              const double* omega, double scale, double* trace) {
   __shared__ double sh[33];
   const int k = blockIdx.x;
   const double w2 = omega[k] * omega[k];
   double s = 0.0;
   for (int vc = threadIdx.x; vc < n_vc; vc += blockDim.x) {
-    double d = delta[vc];
-    s += 4.0 * d / (d * d + w2) * w[vc];
+    double d = delta[vc], o = ow[vc];
+    if (o != 0.0) s += o * (4.0 * d / (d * d + w2)) * w[vc];
   }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) trace[k] = scale * s;
@@ -304,12 +321,10 @@ inline int grid_for(long n, int bs) {
 
 }  // namespace
 
-cudaError_t launch_prepare_scalars(const double* qg2, int n_g, const double* e_v, int n_v,
-                                   const double* e_c, int n_c, double* sv, double* delta,
+cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delta, double* ow,
                                    double* sf0, int* bad, cudaStream_t st) {
-  long n = n_g + (long)n_v * n_c;
-  prepare_kernel<<<grid_for(n, 256), 256, 0, st>>>(qg2, n_g, e_v, n_v, e_c, n_c, sv, delta, sf0,
-                                                    bad);
+  long n = q.n_g + n_transitions(q);
+  prepare_kernel<<<grid_for(n, 256), 256, 0, st>>>(q, sv, delta, ow, sf0, bad);
   return cudaGetLastError();
 }
 
@@ -326,10 +341,10 @@ cudaError_t launch_gauge(const cplx* U, int ldu, int n_g, int n_eig, const doubl
 }
 
 cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delta,
-                         const double* omega, int n_freq, double scale, double* w,
-                         double* trace, cudaStream_t st) {
+                         const double* ow, const double* omega, int n_freq, double scale,
+                         double* w, double* trace, cudaStream_t st) {
   colnorm_kernel<<<(n_vc + 255) / 256, 256, 0, st>>>(mt, n_eig, n_vc, w);
-  trace_kernel<<<n_freq, 1024, 0, st>>>(w, delta, n_vc, omega, scale, trace);
+  trace_kernel<<<n_freq, 1024, 0, st>>>(w, delta, ow, n_vc, omega, scale, trace);
   return cudaGetLastError();
 }
 

@@ -691,14 +691,14 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
   }
 }
 
-// f[b][vc] = 4 D / (D^2 + w_{k0+b}^2) for the frequencies of one group.
-__global__ void freq_weights_kernel(const double* delta, const double* omega, int n_vc, int k0,
-                                    int nb, double* f) {
+// f[b][vc] = ow[vc] 4 D / (D^2 + w_{k0+b}^2) for the frequencies of one group.
+__global__ void freq_weights_kernel(const double* delta, const double* ow, const double* omega,
+                                    int n_vc, int k0, int nb, double* f) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= (long)nb * n_vc) return;
   const int b = (int)(i / n_vc), vc = (int)(i % n_vc);
-  const double d = delta[vc], w = omega[k0 + b];
-  f[i] = 4.0 * d / (d * d + w * w);
+  const double d = delta[vc], w = omega[k0 + b], o = ow[vc];
+  f[i] = o != 0.0 ? o * (4.0 * d / (d * d + w * w)) : 0.0;
 }
 
 // Row maxima of f_b(vc) |M~[j][vc]| for the nb frequencies of a group;
@@ -1130,8 +1130,8 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
 }
 
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
-                const double* omega, int n_freq, double scale, cplx* out, cudaStream_t st,
-                std::string& err, int* launches) {
+                const double* ow, const double* omega, int n_freq, double scale, cplx* out,
+                cudaStream_t st, std::string& err, int* launches) {
   const int S = w.slices.chis;
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_vc, BK);
   __nv_bfloat162* pa = (__nv_bfloat162*)w.planes2;
@@ -1154,8 +1154,8 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   for (int k0 = 0; k0 < n_freq; k0 += w.freq_group) {
     const int nb = std::min(w.freq_group, n_freq - k0);
     w.hook(RPA_T_SLICE, 1);
-    freq_weights_kernel<<<cdiv((long)nb * n_vc, 256), 256, 0, st>>>(delta, omega, n_vc, k0, nb,
-                                                                    w.fweights);
+    freq_weights_kernel<<<cdiv((long)nb * n_vc, 256), 256, 0, st>>>(delta, ow, omega, n_vc, k0,
+                                                                    nb, w.fweights);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(w.rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), st));
     chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(

@@ -66,8 +66,8 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
-                const double* omega, int n_freq, double scale, cplx* out, cudaStream_t st,
-                std::string& err, int* launches);
+                const double* ow, const double* omega, int n_freq, double scale, cplx* out,
+                cudaStream_t st, std::string& err, int* launches);
 
 }  // namespace tc
 }  // namespace rpa

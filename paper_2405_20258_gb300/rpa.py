@@ -19,6 +19,7 @@ RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_EEIG, RPA_ENUMERIC, RPA_ETIMEOUT,
 RPA_FP64, RPA_MIXED = 0, 1
 RPA_ROUTE_EIG, RPA_ROUTE_CHOLESKY = 0, 1
 RPA_C128, RPA_C64 = 0, 1
+RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
 
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
@@ -34,7 +35,10 @@ class rpa_qpoint(ctypes.Structure):
                 ("omega_cell", ctypes.c_double),
                 ("qg2", ctypes.c_void_p), ("e_v", ctypes.c_void_p), ("e_c", ctypes.c_void_p),
                 ("m", ctypes.c_void_p), ("m_dtype", ctypes.c_int), ("iq", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong), ("miller", ctypes.c_void_p)]
+                ("seed", ctypes.c_ulonglong), ("miller", ctypes.c_void_p),
+                ("n_k", ctypes.c_int), ("k_weight", ctypes.c_void_p), ("occ_v", ctypes.c_void_p),
+                ("occ_c", ctypes.c_void_p), ("coulomb", ctypes.c_int),
+                ("slab_zc", ctypes.c_double), ("qg_vec", ctypes.c_void_p)]
 
 
 class rpa_options(ctypes.Structure):
@@ -124,21 +128,34 @@ class DeviceQPoint:
     seed: int = 0
     iq: int = 0
     m_dtype: int = RPA_C128
+    n_k: int = 1
+    k_weight: object = None   # [n_k] float64 or None
+    occ_v: object = None      # [n_k, n_v] float64 or None (1)
+    occ_c: object = None      # [n_k, n_c] float64 or None (0)
+    coulomb: int = RPA_COULOMB_BARE
+    slab_zc: float = 0.0
+    qg_vec: object = None     # [n_g, 3] float64 (slab kernel)
 
     def struct(self):
         import torch
-        n_g, n_v, n_c = self.qg2.shape[0], self.e_v.shape[0], self.e_c.shape[0]
+        n_g, n_v, n_c = self.qg2.shape[0], self.e_v.shape[-1], self.e_c.shape[-1]
         dt = self.m_dtype
         if self.m is not None:
             dt = RPA_C64 if self.m.dtype == torch.complex64 else RPA_C128
         return rpa_qpoint(n_g, n_v, n_c, self.n_eig, self.n_freq, float(self.omega_cell),
                           _ptr(self.qg2), _ptr(self.e_v), _ptr(self.e_c), _ptr(self.m), dt,
-                          int(self.iq), int(self.seed), _ptr(self.miller))
+                          int(self.iq), int(self.seed), _ptr(self.miller), int(self.n_k),
+                          _ptr(self.k_weight), _ptr(self.occ_v), _ptr(self.occ_c),
+                          int(self.coulomb), float(self.slab_zc), _ptr(self.qg_vec))
 
 
-def device_qpoint(qp, n_eig, n_freq, A=None, device="cuda", m_dtype=None, generate=False):
-    """Upload a host ``inputs.QPoint`` (and optionally A) to the device."""
+def device_qpoint(qp, n_eig, n_freq, A=None, device="cuda", m_dtype=None, generate=False,
+                  k_weight=None, occ_v=None, occ_c=None, slab_zc=None, qg_vec=None):
+    """Upload a host ``inputs.QPoint`` (and optionally A, k-point weights,
+    occupations, a slab Coulomb kernel's q+G vectors) to the device."""
     import torch
+    f64 = lambda x: None if x is None else torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64),
+                                                            device=device)
     dq = DeviceQPoint(
         qg2=torch.as_tensor(qp.qg2, dtype=torch.float64, device=device),
         e_v=torch.as_tensor(qp.e_v, dtype=torch.float64, device=device),
@@ -146,7 +163,10 @@ def device_qpoint(qp, n_eig, n_freq, A=None, device="cuda", m_dtype=None, genera
         m=None if A is None else torch.as_tensor(A, device=device),
         n_eig=n_eig, n_freq=n_freq, omega_cell=qp.omega_cell,
         miller=torch.as_tensor(np.ascontiguousarray(qp.miller, dtype=np.int32), device=device),
-        seed=qp.seed, iq=qp.iq)
+        seed=qp.seed, iq=qp.iq, n_k=getattr(qp, "n_k", 1),
+        k_weight=f64(k_weight), occ_v=f64(occ_v), occ_c=f64(occ_c))
+    if slab_zc is not None:
+        dq.coulomb, dq.slab_zc, dq.qg_vec = RPA_COULOMB_SLAB, float(slab_zc), f64(qg_vec)
     if m_dtype is not None:
         dq.m_dtype = m_dtype
     return dq

@@ -4,13 +4,13 @@ import numpy as np
 
 
 def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=False, m_dtype=None,
-            slices=(0, 0, 0)):
+            slices=(0, 0, 0), **extra):
     import torch
     from paper_2405_20258_gb300 import rpa
 
     dq = rpa.device_qpoint(qp, n_eig, n_freq, A=None if generate else A,
-                           m_dtype=m_dtype)
-    n_g, n_vc = qp.n_g, qp.n_v * qp.n_c
+                           m_dtype=m_dtype, **extra)
+    n_g, n_vc = qp.n_g, qp.n_vc
     dev = "cuda"
     out = {}
     with rpa.Plan([dq], precision=precision, energy_route=route, slices=slices) as plan:

@@ -48,7 +48,9 @@ def _q(**kw):
     (dict(n_eig=11), "n_eig"), (dict(n_eig=0), "n_eig"), (dict(n_g=0), "n_g"),
     (dict(n_freq=0), "n_freq"), (dict(n_freq=300), "n_freq"), (dict(omega_cell=-1.0), "omega_cell"),
     (dict(qg2=None), "device pointers"), (dict(m_dtype=5), "m_dtype"),
-    (dict(m=None), "miller"), (dict(n_v=0), "n_v")])
+    (dict(m=None), "miller"), (dict(n_v=0), "n_v"), (dict(n_k=-1), "n_k"),
+    (dict(coulomb=3), "coulomb"), (dict(coulomb=1, slab_zc=5.0), "qg_vec"),
+    (dict(coulomb=1, qg_vec=1, slab_zc=0.0), "slab_zc")])
 def test_plan_create_rejects_bad_descriptors(lib, bad, msg):
     q = _q(**bad)
     h = ctypes.c_void_p()
