@@ -47,6 +47,7 @@ struct rpa_plan_s {
   long max_vc = 0;
   // device workspace
   double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr, *ow = nullptr;
+  double* fall = nullptr;  // [max_freq][max_vc] transition weights (mixed path's FP64 diagonal)
   double *omega = nullptr, *weight = nullptr;  // [n_q][max_freq]
   double *lam_all = nullptr, *lam = nullptr, *trace = nullptr, *ec = nullptr, *logdet = nullptr;
   int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
@@ -128,7 +129,7 @@ void free_plan(rpa_plan_t p) {
                   p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
-                  p->infos};
+                  p->infos, p->fall};
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
@@ -393,6 +394,10 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
       return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
     }
     p->tcw.debug_stall = o.debug_stall;
+    if (dalloc(nullptr, &p->fall, F * V) != RPA_OK) {
+      free_plan(p);
+      return RPA_ENOMEM;
+    }
     p->tcw.hook.ctx = p;
     p->tcw.hook.mark = mark_event;
   }
@@ -581,10 +586,17 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
     s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
     if (s != RPA_OK) return s;
     s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, p->ow, om, F, scale, p->chis, p->st,
-                      p->err,
-                      &nl);
+                      p->err, &nl);
     if (s != RPA_OK) return s;
     p->launches += nl;
+    {
+      // the diagonal of every chi_s in FP64: the rounding of the digit-sliced
+      // products then leaves Tr chi_s exact and moves E_c only at second order
+      StageTimer t(p, RPA_T_TRACE);
+      CU(p, rpa::launch_all_freq_weights(p->delta, p->ow, n_vc, om, F, p->fall, p->st));
+      CU(p, rpa::launch_chis_diagonal(p->mt, E, n_vc, p->fall, F, scale, p->chis, p->st));
+      p->launches += 2;
+    }
   } else {
     {
       StageTimer t(p, RPA_T_PROJ);

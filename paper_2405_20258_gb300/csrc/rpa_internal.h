@@ -57,6 +57,13 @@ cudaError_t launch_gauge(const cplx* U, int ldu, int n_g, int n_eig, const doubl
 cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delta,
                          const double* ow, const double* omega, int n_freq, double scale,
                          double* w, double* trace, cudaStream_t st);
+// f[k][vc] = ow[vc] 4 D/(D^2 + w_k^2) for every frequency.
+cudaError_t launch_all_freq_weights(const double* delta, const double* ow, int n_vc,
+                                    const double* omega, int n_freq, double* f, cudaStream_t st);
+// chis[k][i][i] := (scale sum_vc f[k][vc] |mt[i][vc]|^2, 0) in FP64: the exact diagonal of
+// every chi_s(w_k), so that the tensor-core rounding leaves Tr chi_s untouched.
+cudaError_t launch_chis_diagonal(const cplx* mt, int n_eig, int n_vc, const double* f,
+                                 int n_freq, double scale, cplx* chis, cudaStream_t st);
 // ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam[k][i]) + trace_k]; bad |= 1 if 1 - lam <= 0.
 cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
                           const double* trace, const double* weight, double* ec, int* bad,

@@ -194,6 +194,50 @@ __global__ void trace_kernel(const double* w, const double* delta, const double*
   if (threadIdx.x == 0) trace[k] = scale * s;
 }
 
+// f[k][vc] = ow[vc] 4 D / (D^2 + w_k^2)
+__global__ void all_freq_weights_kernel(const double* delta, const double* ow, int n_vc,
+                                        const double* omega, int n_freq, double* f) {
+  long n = (long)n_freq * n_vc;
+  long stride = (long)gridDim.x * blockDim.x;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    int k = (int)(i / n_vc), vc = (int)(i % n_vc);
+    double d = delta[vc], o = ow[vc], w = omega[k];
+    f[i] = o != 0.0 ? o * (4.0 * d / (d * d + w * w)) : 0.0;
+  }
+}
+
+// One block per (row i, group of DIAG_K frequencies): the FP64 diagonal of chi_s.
+constexpr int DIAG_K = 16;
+__global__ void chis_diagonal_kernel(const cplx* mt, int n_eig, int n_vc, const double* f,
+                                     int n_freq, double scale, cplx* chis) {
+  __shared__ double red[DIAG_K][33];
+  const int i = blockIdx.x, k0 = blockIdx.y * DIAG_K;
+  const int nk = min(DIAG_K, n_freq - k0);
+  double acc[DIAG_K];
+#pragma unroll
+  for (int b = 0; b < DIAG_K; ++b) acc[b] = 0.0;
+  for (int vc = threadIdx.x; vc < n_vc; vc += blockDim.x) {
+    cplx m = mt[(size_t)i * n_vc + vc];
+    double a = fma(m.re, m.re, m.im * m.im);
+#pragma unroll
+    for (int b = 0; b < DIAG_K; ++b)
+      if (b < nk) acc[b] = fma(f[(size_t)(k0 + b) * n_vc + vc], a, acc[b]);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int b = 0; b < DIAG_K; ++b) {
+    double v = warp_sum(acc[b]);
+    if (l == 0) red[b][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nk) {
+    double t = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[threadIdx.x][j];
+    cplx* o = chis + ((size_t)(k0 + threadIdx.x) * n_eig + i) * n_eig + i;
+    *o = {scale * t, 0.0};
+  }
+}
+
 // ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam_ki) + trace_k]
 __global__ void logsum_kernel(const double* lam, int n_eig, int ld, int n_freq,
                               const double* trace, const double* weight, double* ec, int* bad) {
@@ -345,6 +389,20 @@ cudaError_t launch_trace(const cplx* mt, int n_eig, int n_vc, const double* delt
                          double* w, double* trace, cudaStream_t st) {
   colnorm_kernel<<<(n_vc + 255) / 256, 256, 0, st>>>(mt, n_eig, n_vc, w);
   trace_kernel<<<n_freq, 1024, 0, st>>>(w, delta, ow, n_vc, omega, scale, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_all_freq_weights(const double* delta, const double* ow, int n_vc,
+                                    const double* omega, int n_freq, double* f, cudaStream_t st) {
+  all_freq_weights_kernel<<<grid_for((long)n_freq * n_vc, 256), 256, 0, st>>>(delta, ow, n_vc,
+                                                                              omega, n_freq, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chis_diagonal(const cplx* mt, int n_eig, int n_vc, const double* f,
+                                 int n_freq, double scale, cplx* chis, cudaStream_t st) {
+  dim3 grid(n_eig, (n_freq + DIAG_K - 1) / DIAG_K);
+  chis_diagonal_kernel<<<grid, 256, 0, st>>>(mt, n_eig, n_vc, f, n_freq, scale, chis);
   return cudaGetLastError();
 }
 

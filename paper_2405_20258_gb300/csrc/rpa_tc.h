@@ -23,7 +23,7 @@ namespace tc {
 constexpr int MAX_SLICES = 8;
 
 struct Slices {
-  int chi0 = 4, proj = 6, chis = 3;
+  int chi0 = 5, proj = 6, chis = 3;
 };
 
 // Optional stage-timing hook: mark(ctx, timer id, 1) before and (.., 0) after
