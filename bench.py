@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
-    ap.add_argument("--slices", default="5,6,3", help="digit slices of chi0, projection, chi_s")
+    ap.add_argument("--slices", default="4,6,3", help="digit slices of chi0, projection, chi_s")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -107,7 +107,7 @@ typedef struct {
   int energy_route;        /* rpa_energy_route                                       */
   double omega_scale;      /* s of the frequency map w = s t/(1-t); <= 0 means 0.5 Ha */
   int timing;              /* nonzero: record CUDA events around every stage kernel  */
-  int slices_chi0;         /* RPA_MIXED: digit slices of chi~(0) operands (1..8; 0 = 5) */
+  int slices_chi0;         /* RPA_MIXED: digit slices of chi~(0) operands (1..8; 0 = 4) */
   int slices_proj;         /* RPA_MIXED: digit slices of the projection (1..8; 0 = 6)  */
   int slices_chis;         /* RPA_MIXED: digit slices of chi_s operands (1..8; 0 = 3)  */
   int debug_stall;         /* test hook, 0 in production: 1 makes the tensor-core

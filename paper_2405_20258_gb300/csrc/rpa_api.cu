@@ -48,6 +48,8 @@ struct rpa_plan_s {
   // device workspace
   double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr, *ow = nullptr;
   double* fall = nullptr;  // [max_freq][max_vc] transition weights (mixed path's FP64 diagonal)
+  int* order = nullptr;    // [max_vc] transitions sorted by sqrt f(0) (mixed path's chi~ blocks)
+  int order_iq = -1;       // q-point whose order `order` holds
   double *omega = nullptr, *weight = nullptr;  // [n_q][max_freq]
   double *lam_all = nullptr, *lam = nullptr, *trace = nullptr, *ec = nullptr, *logdet = nullptr;
   int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
@@ -129,7 +131,7 @@ void free_plan(rpa_plan_t p) {
                   p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
-                  p->infos, p->fall};
+                  p->infos, p->fall, p->order};
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
@@ -255,6 +257,45 @@ rpa_status tc_status(rpa_plan_t p) {
   if (code == 0) return RPA_OK;
   CU(p, cudaMemsetAsync(p->tcw.status, 0, sizeof(int), p->st));
   return fail(p, RPA_ETIMEOUT, "a tensor-core kernel gave up waiting (code %d)", code);
+}
+
+// Transitions of q-point iq ordered by decreasing f_vc(0) = 4 w/Delta (stable,
+// from the small band arrays copied to the host once per q-point): the K-blocks
+// of the tensor-core chi~(0) then group transitions of similar weight.
+rpa_status transition_order(rpa_plan_t p, int iq) {
+  if (p->order_iq == iq) return RPA_OK;
+  const rpa_qpoint& q = p->q[iq];
+  const int n_k = q.n_k > 1 ? q.n_k : 1;
+  const long nv = (long)n_k * q.n_v, nc = (long)n_k * q.n_c, n = rpa::n_transitions(q);
+  std::vector<double> ev(nv), ec(nc), fv, fc, kw;
+  CU(p, cudaMemcpy(ev.data(), q.e_v, nv * sizeof(double), cudaMemcpyDeviceToHost));
+  CU(p, cudaMemcpy(ec.data(), q.e_c, nc * sizeof(double), cudaMemcpyDeviceToHost));
+  if (q.occ_v) {
+    fv.resize(nv);
+    CU(p, cudaMemcpy(fv.data(), q.occ_v, nv * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (q.occ_c) {
+    fc.resize(nc);
+    CU(p, cudaMemcpy(fc.data(), q.occ_c, nc * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (q.k_weight) {
+    kw.resize(n_k);
+    CU(p, cudaMemcpy(kw.data(), q.k_weight, n_k * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  std::vector<double> key(n);
+  for (long vc = 0; vc < n; ++vc) {
+    const long k = vc / ((long)q.n_v * q.n_c), r = vc % ((long)q.n_v * q.n_c);
+    const long v = k * q.n_v + r / q.n_c, c = k * q.n_c + r % q.n_c;
+    const double d = ec[c] - ev[v];
+    const double w = (kw.empty() ? 1.0 : kw[k]) * ((fv.empty() ? 1.0 : fv[v]) - (fc.empty() ? 0.0 : fc[c]));
+    key[vc] = (w != 0.0 && d != 0.0) ? std::fabs(w / d) : 0.0;
+  }
+  std::vector<int> idx(n);
+  for (long i = 0; i < n; ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key[a] > key[b]; });
+  CU(p, cudaMemcpy(p->order, idx.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  p->order_iq = iq;
+  return RPA_OK;
 }
 
 rpa_status prepare(rpa_plan_t p, int iq) {
@@ -394,7 +435,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
       return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
     }
     p->tcw.debug_stall = o.debug_stall;
-    if (dalloc(nullptr, &p->fall, F * V) != RPA_OK) {
+    if (dalloc(nullptr, &p->fall, F * V) != RPA_OK || dalloc(nullptr, &p->order, V) != RPA_OK) {
       free_plan(p);
       return RPA_ENOMEM;
     }
@@ -510,8 +551,9 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   const double scale = -1.0 / q.omega_cell;
   if (p->opt.precision == RPA_MIXED) {
     int nl = 0;
-    s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st,
-                      p->err, &nl);
+    if ((s = transition_order(p, iq)) != RPA_OK) return s;
+    s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->order, p->sv, scale, p->chi,
+                      p->st, p->err, &nl);
     p->launches += nl;
     if (s != RPA_OK) return s;
   } else {

@@ -86,6 +86,7 @@ struct GemmArgs {
   double2* out;       // complex output
   long out_bstride, ld_row, ld_col;
   int conj, atomic;
+  int accumulate;     // add into the output with FP64 atomics, never zero it
   const double* rsa;  // optional FP64 factor per A row (NULL: 1)
   const double* rsb;  // optional FP64 factor per complex B column (NULL: 1)
   int stall;          // test hook: the producer issues nothing
@@ -543,14 +544,16 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) 
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
-// chi0 operand X[vc][g] = sf[vc] A[vc][g] (v^1/2 is applied per output row in
-// the GEMM epilogue): row maxima over vc per g.
-__global__ void chi0_rowmax_kernel(const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                                   unsigned long long* rowmax) {
+// chi0 operand X[r][g] = sf[vc] A[vc][g] for the transitions vc = order[r],
+// r < n_rows, of one K-block (v^1/2 is applied per output row in the GEMM
+// epilogue): row maxima over the block per g.
+__global__ void chi0_rowmax_kernel(const void* A, int dtype, const int* order, int n_rows,
+                                   int n_g, const double* sf, unsigned long long* rowmax) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_g) return;
   double m = 0.0;
-  for (int vc = blockIdx.y; vc < n_vc; vc += gridDim.y) {
+  for (int r = blockIdx.y; r < n_rows; r += gridDim.y) {
+    const int vc = order[r];
     double2 a = load_any(A, dtype, (long)vc * n_g + g);
     double s = sf[vc];
     m = fmax(m, fmax(fabs(a.x * s), fabs(a.y * s)));
@@ -562,9 +565,9 @@ __global__ void chi0_rowmax_kernel(const void* A, int dtype, int n_vc, int n_g, 
 // (x_r, x_i), row 2g+1 holds (x_i, -x_r), so that Re chi = X_g . X_h and
 // Im chi = X_g . Y_h.  One 32 x 32 (vc, g) tile per block, transposed through
 // shared memory so that the plane rows are written contiguously.
-__global__ void chi0_slice_kernel(const void* A, int dtype, int n_vc, int n_g, int n_g_pad,
-                                  long K, const double* sf, const unsigned long long* rowmax,
-                                  int S,
+__global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, int n_vc, int n_g,
+                                  int n_g_pad, long K, const double* sf,
+                                  const unsigned long long* rowmax, int S,
                                   __nv_bfloat162* planes, int* exps) {
   __shared__ double2 t[32][33];
   __shared__ int es[32];
@@ -577,9 +580,10 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, int n_vc, int n_g, i
     if (blockIdx.x == 0 && g < n_g_pad) exps[g] = e;
   }
   for (int r = ty; r < 32; r += 8) {
-    int vc = vc0 + r, g = g0 + tx;
+    int vr = vc0 + r, g = g0 + tx;
     double2 x = make_double2(0.0, 0.0);
-    if (vc < n_vc && g < n_g) {
+    if (vr < n_vc && g < n_g) {
+      const int vc = order[vr];
       x = load_any(A, dtype, (long)vc * n_g + g);
       double s = sf[vc];
       x.x *= s;
@@ -888,7 +892,9 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   a.k_per_split = (int)kps;
   a.kd_tiles = kdt;
   a.atomic = 0;
-  if (split > 1) {
+  if (a.accumulate) {
+    a.atomic = 1;  // the caller zeroed the output and adds several K-blocks
+  } else if (split > 1) {
     // split-K partial tiles are summed with FP64 atomics into a zeroed output
     cudaError_t ez = cudaMemsetAsync(zero_ptr, 0, zero_bytes, st);
     if (ez != cudaSuccess) {
@@ -990,7 +996,9 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   const long k_vc = rup(2 * max_vc, BK), k_g = rup(2 * max_g, BK);
   const int grp = (int)std::min<size_t>(MAX_GROUP, max_freq);
   w.freq_group = grp;
-  size_t p1 = std::max({(size_t)s.chi0 * 2 * g_pad * k_vc, (size_t)s.proj * vc_pad * k_g,
+  w.chi0_blocks = std::max(1, env_int("RPA_TC_CHI0_BLOCKS", 32));
+  const long k_blk = rup(2 * rup(cdiv(max_vc, w.chi0_blocks), 32), BK);
+  size_t p1 = std::max({(size_t)s.chi0 * 2 * g_pad * k_blk, (size_t)s.proj * vc_pad * k_g,
                         (size_t)grp * s.chis * 2 * e_pad * k_vc});
   size_t p2 = std::max((size_t)s.proj * 2 * e_pad * k_g, (size_t)s.chis * e_pad * k_vc);
   w.plane_bytes = p1 * 2;
@@ -1030,55 +1038,65 @@ void free_workspace(Workspace& w) {
 }
 
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err,
-                int* launches) {
+                const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
+                std::string& err, int* launches) {
   const int S = w.slices.chi0;
-  const long g_pad = rup(n_g, BM), K = rup(2L * n_vc, BK);
-  w.hook(RPA_T_SLICE, 1);
-  CK(cudaMemsetAsync(w.rowmax, 0, g_pad * sizeof(unsigned long long), st));
-  {
-    dim3 grid(cdiv(n_g, 128), std::min(cdiv(n_vc, 64), 512));
-    chi0_rowmax_kernel<<<grid, 128, 0, st>>>(A, dtype, n_vc, n_g, sf, w.rowmax);
-    CK(cudaGetLastError());
+  const long g_pad = rup(n_g, BM);
+  // K-blocks of the transitions in `order` (sorted by sqrt f(0)): each block has
+  // its own per-row digit exponents, so rows keep more significant bits where
+  // the transition weights of the block are smaller than the overall maximum.
+  const int nblk = std::max(1, std::min(w.chi0_blocks, cdiv(n_vc, 32)));
+  const long per = rup(cdiv(n_vc, nblk), 32);
+  CK(cudaMemsetAsync(chi, 0, sizeof(cplx) * (size_t)n_g * n_g, st));
+  for (long r0 = 0; r0 < n_vc; r0 += per) {
+    const int nr = (int)std::min<long>(per, n_vc - r0);
+    const long K = rup(2L * nr, BK);
+    w.hook(RPA_T_SLICE, 1);
+    CK(cudaMemsetAsync(w.rowmax, 0, g_pad * sizeof(unsigned long long), st));
+    {
+      dim3 grid(cdiv(n_g, 128), std::min(cdiv(nr, 64), 512));
+      chi0_rowmax_kernel<<<grid, 128, 0, st>>>(A, dtype, order + r0, nr, n_g, sf, w.rowmax);
+      CK(cudaGetLastError());
+    }
+    __nv_bfloat162* planes = (__nv_bfloat162*)w.planes;
+    {
+      dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
+      chi0_slice_kernel<<<grid, dim3(32, 8), 0, st>>>(A, dtype, order + r0, nr, n_g, (int)g_pad,
+                                                      K, sf, w.rowmax, S, planes, w.exps);
+      CK(cudaGetLastError());
+    }
+    if (launches) *launches += 2;
+    w.hook(RPA_T_SLICE, 0);
+    CUtensorMap ta, tb;
+    const long plane_bytes = 2 * g_pad * K * 2;
+    // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
+    if (!make_map(&ta, w.planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
+    if (!make_map(&tb, w.planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
+      return RPA_ECUDA;
+    GemmArgs a{};
+    a.S = S;
+    a.K = (int)K;
+    a.ea = w.exps;
+    a.eb = w.exps;
+    a.eb_stride = 0;
+    a.a_rows = n_g;
+    a.b_rows = 2 * n_g;
+    a.alpha = scale;
+    a.rsa = sv;  // chi~ = v^1/2 chi0 v^1/2: the v^1/2 factors scale rows and columns
+    a.rsb = sv;
+    a.out = (double2*)chi;
+    a.out_bstride = 0;
+    a.ld_row = n_g;
+    a.ld_col = 1;
+    a.conj = 0;
+    a.accumulate = 1;
+    const int tiles_m = cdiv(n_g, BM);
+    w.hook(RPA_T_CHI0, 1);
+    rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, true, chi, 0, st, err, launches);
+    w.hook(RPA_T_CHI0, 0);
+    if (r != RPA_OK) return r;
   }
-  __nv_bfloat162* planes = (__nv_bfloat162*)w.planes;
-  {
-    dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
-    chi0_slice_kernel<<<grid, dim3(32, 8), 0, st>>>(A, dtype, n_vc, n_g, (int)g_pad, K, sf,
-                                                    w.rowmax, S, planes, w.exps);
-    CK(cudaGetLastError());
-  }
-  if (launches) *launches += 2;
-  w.hook(RPA_T_SLICE, 0);
-  CUtensorMap ta, tb;
-  const long plane_bytes = 2 * g_pad * K * 2;
-  // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
-  if (!make_map(&ta, w.planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
-  if (!make_map(&tb, w.planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
-    return RPA_ECUDA;
-  GemmArgs a{};
-  a.S = S;
-  a.K = (int)K;
-  a.ea = w.exps;
-  a.eb = w.exps;
-  a.eb_stride = 0;
-  a.a_rows = n_g;
-  a.b_rows = 2 * n_g;
-  a.alpha = scale;
-  a.rsa = sv;  // chi~ = v^1/2 chi0 v^1/2: the v^1/2 factors scale rows and columns
-  a.rsb = sv;
-  a.out = (double2*)chi;
-  a.out_bstride = 0;
-  a.ld_row = n_g;
-  a.ld_col = 1;
-  a.conj = 0;
-  a.atomic = 0;
-  const int tiles_m = cdiv(n_g, BM);
-  w.hook(RPA_T_CHI0, 1);
-  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, true, chi,
-                          sizeof(cplx) * (size_t)n_g * n_g, st, err, launches);
-  w.hook(RPA_T_CHI0, 0);
-  return r;
+  return RPA_OK;
 }
 
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,

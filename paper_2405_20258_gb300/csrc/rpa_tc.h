@@ -23,7 +23,7 @@ namespace tc {
 constexpr int MAX_SLICES = 8;
 
 struct Slices {
-  int chi0 = 5, proj = 6, chis = 3;
+  int chi0 = 4, proj = 6, chis = 3;
 };
 
 // Optional stage-timing hook: mark(ctx, timer id, 1) before and (.., 0) after
@@ -52,6 +52,7 @@ struct Workspace {
   size_t fweight_count = 0;
   Slices slices;
   int freq_group = 8;
+  int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int debug_stall = 0;
   Hook hook;
 };
@@ -60,9 +61,11 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
                            size_t max_freq, const Slices& s, std::string& err);
 void free_workspace(Workspace& w);
 
+// chi~(0) from the transitions in `order` (a permutation of 0..n_vc-1, device),
+// processed in w.chi0_blocks K-blocks with their own digit exponents.
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
-                const double* sv, double scale, cplx* chi, cudaStream_t st, std::string& err,
-                int* launches);
+                const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
+                std::string& err, int* launches);
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,

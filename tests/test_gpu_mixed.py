@@ -3,7 +3,7 @@
 * With 7 digit slices per operand the slicing error (about 2^-55 of the row
   scales) is below FP64 rounding, so the mixed path must reproduce the FP64
   CUDA path to FP64 accuracy: this pins the TMA/MMA/TMEM machinery exactly.
-* With the default slices (5, 6, 3) the error is set by the digit truncation;
+* With the default slices (4, 6, 3) the error is set by the digit truncation;
   at the 400-plane-wave workload it must stay within 1e-6 Ha of the oracle.
 * Errors fall monotonically as slices are added.
 * A stalled producer (test hook) makes every bounded wait run out: the stage
