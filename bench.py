@@ -302,6 +302,48 @@ def main():
                     "peak_source": "%s bf16 burst x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind,
                     "traffic": None, "work_per_launch": "%.4g algorithmic flops" % fl[dom]}
 
+    # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back
+    e2e = None
+    if not args.no_e2e:
+        host_A = torch.empty_like(A, device="cpu").pin_memory()
+        host_A.copy_(A)
+        host_small = [t.cpu().pin_memory() for t in (dq.qg2, dq.e_v, dq.e_c)]
+        dev_small = [dq.qg2, dq.e_v, dq.e_c]
+        h2d = host_A.numel() * 16 + sum(t.numel() * t.element_size() for t in host_small)
+
+        h2d_ms = []
+
+        def e2e_step():
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                c0.record(stream)
+                A.copy_(host_A, non_blocking=True)
+                for d_, h_ in zip(dev_small, host_small):
+                    d_.copy_(h_, non_blocking=True)
+                c1.record(stream)
+            ec = plan.run(0)  # returns E_c to the host (8 bytes)
+            h2d_ms.append(c0.elapsed_time(c1))
+            return ec
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
+               "h2d_ms_per_step": statistics.mean(h2d_ms[1:]) if len(h2d_ms) > 1 else None}
+        plan.timings()
+        del host_A
+
     # the FP64 path on the same inputs: speed-up and |dE_c| of the mixed path
     compare = None
     if mixed and not args.no_fp64_compare:
@@ -323,39 +365,6 @@ def main():
                    "contraction_speedup": ((st64["chi0"] + st64["proj"] + st64["chis"]) / 1e3)
                    / contraction_s,
                    "fp64_steps": 1, "fp64_warmup": 1}
-
-    # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back
-    e2e = None
-    if not args.no_e2e:
-        host_A = torch.empty_like(A, device="cpu").pin_memory()
-        host_A.copy_(A)
-        host_small = [t.cpu().pin_memory() for t in (dq.qg2, dq.e_v, dq.e_c)]
-        dev_small = [dq.qg2, dq.e_v, dq.e_c]
-        h2d = host_A.numel() * 16 + sum(t.numel() * t.element_size() for t in host_small)
-
-        def e2e_step():
-            with torch.cuda.stream(stream):
-                A.copy_(host_A, non_blocking=True)
-                for d_, h_ in zip(dev_small, host_small):
-                    d_.copy_(h_, non_blocking=True)
-            return plan.run(0)  # returns E_c to the host (8 bytes)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        barrier(dist)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(dist)
-        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
-        e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
-        plan.timings()
-        del host_A
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
