@@ -2,13 +2,15 @@
 // digit-sliced BF16 GEMM with TMEM accumulation and a double-float epilogue,
 // plus the HBM-bound kernels that cut FP64 operands into digit planes.
 //
-// GEMM kernel roles (one output tile of 128 x BN per CTA, BN = 64, 96 or 128):
+// GEMM kernel roles (one output tile of 128 x BN per CTA, BN = 64 or 128):
 //   warp 0      TMA producer: per 64-wide K-tile, all S digit planes of the B
 //               tile (double-buffered) and the S digit planes of the A tile
 //               through a 4-stage ring;
-//   warp 1      TMEM allocation and the single MMA-issuing thread: for every
-//               slice pair (s, t) with s + t <= S-1, four kind::f16 MMAs
-//               (K = 16 each) into the level accumulator L = s + t;
+//   warp 1      TMEM allocation and the single MMA-issuing thread: per A digit
+//               plane s, kind::f16 MMAs (K = 16 each) against the B planes
+//               t = 0 .. S-1-s taken together as one operand of BN (S - s)
+//               rows, whose output columns land in the level accumulators
+//               L = s + t (levels sit BN columns apart in TMEM);
 //   BN/8 epilogue warps (4 lane quadrants x BN/32 column blocks): at the end
 //               of each drain interval, read the S level
 //               accumulators (exact integers) from TMEM, scale by 2^-8L and add
@@ -47,20 +49,21 @@ constexpr int threads_for() {
   return 64 + 4 * BN;
 }
 
-// TMEM columns between level accumulators: BN, except N = 96 which keeps the
-// 128-column spacing of the N = 128 layout.
+// TMEM columns between level accumulators: BN, so that the columns of B plane
+// t in an MMA that covers planes 0 .. S-1-s fall into level s + t.
 template <int BN>
 constexpr int tmem_stride() {
-  return BN == 96 ? 128 : BN;
+  static_assert(BN % 64 == 0, "level accumulators start at multiples of 64 TMEM columns");
+  return BN;
 }
+constexpr int MMA_N_MAX = 256;  // largest N of a cta_group::1 kind::f16 MMA with M = 128
 constexpr uint32_t A_TILE = BM * BK * 2;  // 16 KB
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 
 // kind::f16 instruction descriptor: D = F32 (bits 4-5), A = B = BF16 (bits 7-9,
 // 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
-template <int BN>
-constexpr uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
 
@@ -237,7 +240,6 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
   constexpr uint32_t B_TILE = BN * BK * 2;
-  constexpr uint32_t IDESC = idesc<BN>();
   constexpr int CPT = 32;           // accumulator columns per epilogue thread
   constexpr int EPI = BN / 8;       // epilogue warps: 4 lane quadrants x BN/32 column blocks
   constexpr int TS = tmem_stride<BN>();
@@ -332,11 +334,17 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         if (kin == 0) {
           if (!mbar_wait(&acc_empty[ab], accphase ^ 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
           tc_fence_after();
-          first = (1u << S) - 1;
+          first = 1;
           acc_base = tmem + ab * S * TS;
         }
         if (!mbar_wait(&full_b[bb], bphase, &abort_flag, p.status, ERR_WAIT_MMA)) break;
         bool ok = true;
+        // The B planes of this stage are contiguous (plane t at rows t BN ..), so
+        // the rows of planes 0 .. S-1-s form one K-major operand; its output
+        // column t BN + j goes to TMEM column (s + t) BN + j = level s + t.
+        // The MMAs of plane s = 0 cover every level column: at the start of a
+        // drain interval they overwrite instead of accumulating.
+        const uint64_t bd0 = smem_desc(sB0 + bb * S * B_TILE);
         for (int s = 0; s < S; ++s) {
           if (!mbar_wait(&full_a[slot], aphase, &abort_flag, p.status, ERR_WAIT_MMA)) {
             ok = false;
@@ -344,15 +352,17 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           }
           tc_fence_after();
           const uint64_t ad = smem_desc(sA0 + slot * A_TILE);
-          for (int t = 0; t + s < S; ++t) {
-            const int L = s + t;
-            const uint64_t bd = smem_desc(sB0 + (bb * S + t) * B_TILE);
-            const uint32_t d = acc_base + L * TS;
-            mma_bf16(d, ad, bd, IDESC, (first >> L) & 1 ? 0u : 1u);
+          const int rows = BN * (S - s);
+          for (int c0 = 0; c0 < rows; c0 += MMA_N_MAX) {
+            const int n = min(MMA_N_MAX, rows - c0);
+            const uint32_t id = idesc_n(n);
+            const uint64_t bd = bd0 + (uint64_t)((c0 * BK * 2) >> 4);
+            const uint32_t d = acc_base + s * TS + c0;
+            mma_bf16(d, ad, bd, id, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
-            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, IDESC, 1u);
-            first &= ~(1u << L);
+            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
           }
+          if (s == 0) first = 0;
           mma_commit(&empty_a[slot]);
           if (++slot == NA) {
             slot = 0;
@@ -834,13 +844,12 @@ int env_int(const char* name, int dflt) {
   return v && *v ? atoi(v) : dflt;
 }
 
-// MMA N for S slices: 128 when S level accumulators of 128 columns and the 128
-// columns of double-float low halves fit in TMEM (S <= 3); 96 when S levels at
-// a 128-column stride fit (S = 4); else 64.
+// B rows per tile for S slices: 128 when the S level accumulators of 128
+// columns and the 128 columns of double-float low halves fit in TMEM (S <= 3),
+// else 64.  Level accumulators start at multiples of 64 TMEM columns.
 int pick_bn(int S) {
   const int cap = env_int("RPA_TC_BN", 128);
   if (cap >= 128 && (S + 1) * 128 <= 512) return 128;
-  if (cap >= 96 && S * 128 <= 512) return 96;
   return 64;
 }
 
@@ -852,7 +861,7 @@ void gemm_shape(int S, int* na, int* nb, int* nacc) {
   const int want_na = std::min(MAX_NA, std::max(2, env_int("RPA_TC_NA", MAX_NA)));
   const int want_nb = std::min(MAX_NB, std::max(2, env_int("RPA_TC_NB", MAX_NB)));
   const int want_acc = std::min(2, std::max(1, env_int("RPA_TC_NACC", 2)));
-  *nacc = (want_acc == 2 && BN == 64 && 2 * S * BN <= 512) ? 2 : 1;  // BN 96/128: one set
+  *nacc = (want_acc == 2 && BN == 64 && 2 * S * BN <= 512) ? 2 : 1;  // BN 128: one set
   for (int b = want_nb; b >= 2; --b)
     for (int a = want_na; a >= 2; --a)
       if (1024 + (size_t)a * A_TILE + (size_t)b * S * B_TILE <= g_smem_limit) {
@@ -930,25 +939,20 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   if (!g_smem_limit) {
     // opt-in shared memory per block minus the kernels' static shared memory
     int dev = 0, optin = 0;
-    cudaFuncAttributes fa64{}, fa128{}, fa96{};
+    cudaFuncAttributes fa64{}, fa128{};
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
             cudaSuccess ||
         (e = cudaFuncGetAttributes(&fa64, slice_gemm_kernel<64>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa128, slice_gemm_kernel<128>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa96, slice_gemm_kernel<96>)) != cudaSuccess) {
+        (e = cudaFuncGetAttributes(&fa128, slice_gemm_kernel<128>)) != cudaSuccess) {
       err = std::string("querying shared memory limits: ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
-    size_t lim = (size_t)optin -
-                 std::max({fa64.sharedSizeBytes, fa96.sharedSizeBytes, fa128.sharedSizeBytes});
+    size_t lim = (size_t)optin - std::max(fa64.sharedSizeBytes, fa128.sharedSizeBytes);
     if ((e = cudaFuncSetAttribute(slice_gemm_kernel<64>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(slice_gemm_kernel<128>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
-            cudaSuccess ||
-        (e = cudaFuncSetAttribute(slice_gemm_kernel<96>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
             cudaSuccess) {
       err = std::string("cudaFuncSetAttribute(max dynamic smem): ") + cudaGetErrorString(e);
@@ -964,8 +968,6 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   }
   if (BN == 128)
     slice_gemm_kernel<128><<<(unsigned)work.size(), threads_for<128>(), smem, st>>>(ta, tb, a);
-  else if (BN == 96)
-    slice_gemm_kernel<96><<<(unsigned)work.size(), threads_for<96>(), smem, st>>>(ta, tb, a);
   else
     slice_gemm_kernel<64><<<(unsigned)work.size(), threads_for<64>(), smem, st>>>(ta, tb, a);
   e = cudaGetLastError();
