@@ -579,6 +579,16 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   if (p->stage[iq] < ST_CHI0) return fail(p, RPA_ESTATE, "rpa_chi0_static(%d) must come first", iq);
   const rpa_qpoint& q = *qp(p, iq);
   const int n = q.n_g;
+  if (p->opt.precision == RPA_MIXED) {
+    // the projection's A planes are cut on the side stream during the eigensolve
+    const void* A;
+    int dt, nl = 0;
+    if ((s = matrix_a(p, iq, &A, &dt)) != RPA_OK) return s;
+    s = rpa::tc::project_prepare(p->tcw, A, dt, (int)rpa::n_transitions(q), n, p->st, p->err,
+                                 &nl);
+    p->launches += nl;
+    if (s != RPA_OK) return s;
+  }
   StageTimer timer(p, RPA_T_EIG0);
   CU(p, cudaMemcpyAsync(p->chi_work, p->chi, sizeof(cplx) * (size_t)n * n,
                         cudaMemcpyDeviceToDevice, p->st));
@@ -593,6 +603,9 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
                           p->sol_dev_bytes, p->sol_host, p->sol_host_bytes, p->flags + 2));
   int info = 0;
   CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  if (p->opt.precision == RPA_MIXED &&
+      (s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK)
+    return s;
   CU(p, cudaStreamSynchronize(p->st));
   if ((s = tc_status(p)) != RPA_OK) return s;
   if (info != 0) return fail(p, RPA_EEIG, "Xsyevdx info = %d", info);

@@ -1000,14 +1000,15 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.freq_group = grp;
   w.chi0_blocks = std::max(1, env_int("RPA_TC_CHI0_BLOCKS", 32));
   const long k_blk = rup(2 * rup(cdiv(max_vc, w.chi0_blocks), 32), BK);
-  size_t p1 = std::max({(size_t)s.chi0 * 2 * g_pad * k_blk, (size_t)s.proj * vc_pad * k_g,
+  // chi~(0) double-buffers the planes of its K-blocks (one cut while the other multiplies)
+  size_t p1 = std::max({(size_t)2 * s.chi0 * 2 * g_pad * k_blk, (size_t)s.proj * vc_pad * k_g,
                         (size_t)grp * s.chis * 2 * e_pad * k_vc});
   size_t p2 = std::max((size_t)s.proj * 2 * e_pad * k_g, (size_t)s.chis * e_pad * k_vc);
   w.plane_bytes = p1 * 2;
   w.plane2_bytes = p2 * 2;
   w.exp_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)e_pad}) +
                 std::max((size_t)g_pad, (size_t)grp * e_pad);
-  w.rowmax_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)grp * e_pad});
+  w.rowmax_count = std::max({(size_t)2 * g_pad, (size_t)vc_pad, (size_t)grp * e_pad});
   w.work_count = 1 << 20;
   w.fweight_count = (size_t)grp * max_vc;
   auto al = [&](void** p, size_t bytes) {
@@ -1028,15 +1029,45 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
     free_workspace(w);
     return RPA_ENOMEM;
   }
-  cudaMemset(w.status, 0, sizeof(int));
+  cudaError_t e = cudaMemset(w.status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking);
+  cudaEvent_t* evs[] = {&w.ev_in, &w.ev_side_last, &w.ev_sliced[0], &w.ev_sliced[1],
+                        &w.ev_gemm[0], &w.ev_gemm[1]};
+  for (cudaEvent_t* ev : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  // a completed marker: the first join waits for nothing
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev_side_last, w.side);
+  if (e != cudaSuccess) {
+    err = std::string("tensor-core workspace streams and events: ") + cudaGetErrorString(e);
+    free_workspace(w);
+    return RPA_ECUDA;
+  }
   return RPA_OK;
 }
 
 void free_workspace(Workspace& w) {
+  if (w.side) cudaStreamSynchronize(w.side);
   void* b[] = {w.planes, w.planes2, w.exps, w.rowmax, w.work, w.status, w.fweights};
   for (void* p : b)
     if (p) cudaFree(p);
+  cudaEvent_t evs[] = {w.ev_in, w.ev_side_last, w.ev_sliced[0], w.ev_sliced[1], w.ev_gemm[0],
+                       w.ev_gemm[1]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (w.side) cudaStreamDestroy(w.side);
   w = Workspace{};
+}
+
+rpa_status join_side(Workspace& w, cudaStream_t st, std::string& err) {
+  CK(cudaStreamWaitEvent(st, w.ev_side_last, 0));
+  return RPA_OK;
+}
+
+// The side stream waits for the work queued so far on the caller's stream.
+static rpa_status side_fork(Workspace& w, cudaStream_t st, std::string& err) {
+  CK(cudaEventRecord(w.ev_in, st));
+  CK(cudaStreamWaitEvent(w.side, w.ev_in, 0));
+  return RPA_OK;
 }
 
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
@@ -1049,37 +1080,52 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
   // the transition weights of the block are smaller than the overall maximum.
   const int nblk = std::max(1, std::min(w.chi0_blocks, cdiv(n_vc, 32)));
   const long per = rup(cdiv(n_vc, nblk), 32);
+  // Two plane buffers: block b is cut on the side stream while block b-1 is
+  // multiplied on `st`; buffer b % 2 is reused once the GEMM of block b-2 is done.
+  const size_t buf_elems = (size_t)S * 2 * g_pad * rup(2 * per, BK);  // BF16 pairs / 2
+  w.proj_a.valid = false;
   CK(cudaMemsetAsync(chi, 0, sizeof(cplx) * (size_t)n_g * n_g, st));
-  for (long r0 = 0; r0 < n_vc; r0 += per) {
+  if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
+  int b = 0;
+  for (long r0 = 0; r0 < n_vc; r0 += per, ++b) {
+    const int buf = b & 1;
     const int nr = (int)std::min<long>(per, n_vc - r0);
     const long K = rup(2L * nr, BK);
-    w.hook(RPA_T_SLICE, 1);
-    CK(cudaMemsetAsync(w.rowmax, 0, g_pad * sizeof(unsigned long long), st));
+    __nv_bfloat162* planes = (__nv_bfloat162*)w.planes + buf * (buf_elems / 2);
+    int* exps = w.exps + buf * g_pad;
+    unsigned long long* rowmax = w.rowmax + buf * g_pad;
+    if (b >= 2) CK(cudaStreamWaitEvent(w.side, w.ev_gemm[buf], 0));
+    CK(cudaMemsetAsync(rowmax, 0, g_pad * sizeof(unsigned long long), w.side));
     {
       dim3 grid(cdiv(n_g, 128), std::min(cdiv(nr, 64), 512));
-      chi0_rowmax_kernel<<<grid, 128, 0, st>>>(A, dtype, order + r0, nr, n_g, sf, w.rowmax);
+      chi0_rowmax_kernel<<<grid, 128, 0, w.side>>>(A, dtype, order + r0, nr, n_g, sf, rowmax);
       CK(cudaGetLastError());
     }
-    __nv_bfloat162* planes = (__nv_bfloat162*)w.planes;
     {
       dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
-      chi0_slice_kernel<<<grid, dim3(32, 8), 0, st>>>(A, dtype, order + r0, nr, n_g, (int)g_pad,
-                                                      K, sf, w.rowmax, S, planes, w.exps);
+      chi0_slice_kernel<<<grid, dim3(32, 8), 0, w.side>>>(A, dtype, order + r0, nr, n_g,
+                                                          (int)g_pad, K, sf, rowmax, S, planes,
+                                                          exps);
       CK(cudaGetLastError());
     }
+    CK(cudaEventRecord(w.ev_sliced[buf], w.side));
+    CK(cudaEventRecord(w.ev_side_last, w.side));
     if (launches) *launches += 2;
+    // the slice timer measures how long `st` waits for the cut planes
+    w.hook(RPA_T_SLICE, 1);
+    CK(cudaStreamWaitEvent(st, w.ev_sliced[buf], 0));
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap ta, tb;
     const long plane_bytes = 2 * g_pad * K * 2;
     // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
-    if (!make_map(&ta, w.planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
-    if (!make_map(&tb, w.planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
+    if (!make_map(&ta, planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
+    if (!make_map(&tb, planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
     a.K = (int)K;
-    a.ea = w.exps;
-    a.eb = w.exps;
+    a.ea = exps;
+    a.eb = exps;
     a.eb_stride = 0;
     a.a_rows = n_g;
     a.b_rows = 2 * n_g;
@@ -1097,7 +1143,40 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
     rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, true, chi, 0, st, err, launches);
     w.hook(RPA_T_CHI0, 0);
     if (r != RPA_OK) return r;
+    CK(cudaEventRecord(w.ev_gemm[buf], st));
   }
+  return RPA_OK;
+}
+
+// rows of A -> S digit planes of the projection's A operand and exponents ea
+static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+                               cudaStream_t s, std::string& err, int* launches) {
+  const int S = w.slices.proj;
+  const long vc_pad = rup(n_vc, BM), K = rup(2L * n_g, BK);
+  CK(cudaMemsetAsync(w.rowmax, 0, vc_pad * sizeof(unsigned long long), s));
+  row_max_kernel<<<dim3((unsigned)n_vc, cdiv(n_g, CHUNK)), 256, 0, s>>>(A, dtype, n_g, n_vc, n_g,
+                                                                         w.rowmax);
+  CK(cudaGetLastError());
+  slice_rows_kernel<<<dim3((unsigned)vc_pad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
+      A, dtype, n_g, n_vc, n_g, (int)vc_pad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps);
+  CK(cudaGetLastError());
+  if (launches) *launches += 2;
+  return RPA_OK;
+}
+
+rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+                           cudaStream_t st, std::string& err, int* launches) {
+  w.proj_a.valid = false;
+  if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
+  rpa_status r = slice_proj_a(w, A, dtype, n_vc, n_g, w.side, err, launches);
+  if (r != RPA_OK) return r;
+  CK(cudaEventRecord(w.ev_side_last, w.side));
+  w.proj_a.valid = true;
+  w.proj_a.a = A;
+  w.proj_a.dtype = dtype;
+  w.proj_a.n_vc = n_vc;
+  w.proj_a.n_g = n_g;
+  w.proj_a.S = w.slices.proj;
   return RPA_OK;
 }
 
@@ -1105,22 +1184,22 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches) {
   const int S = w.slices.proj;
   const long vc_pad = rup(n_vc, BM), e_pad = rup(n_eig, BM), K = rup(2L * n_g, BK);
-  __nv_bfloat162* pa = (__nv_bfloat162*)w.planes;
   __nv_bfloat162* pb = (__nv_bfloat162*)w.planes2;
   int* ea = w.exps;
   int* eb = w.exps + std::max({rup(n_g, BM), vc_pad, e_pad});
+  const bool ready = w.proj_a.valid && w.proj_a.a == A && w.proj_a.dtype == dtype &&
+                     w.proj_a.n_vc == n_vc && w.proj_a.n_g == n_g && w.proj_a.S == S;
+  w.proj_a.valid = false;  // the chi_s stage reuses the planes next
   w.hook(RPA_T_SLICE, 1);
-  CK(cudaMemsetAsync(w.rowmax, 0, vc_pad * sizeof(unsigned long long), st));
-  row_max_kernel<<<dim3((unsigned)n_vc, cdiv(n_g, CHUNK)), 256, 0, st>>>(A, dtype, n_g, n_vc, n_g,
-                                                                          w.rowmax);
-  CK(cudaGetLastError());
-  slice_rows_kernel<<<dim3((unsigned)vc_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
-      A, dtype, n_g, n_vc, n_g, (int)vc_pad, K, S, w.rowmax, pa, ea);
-  CK(cudaGetLastError());
+  if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
+  if (!ready) {
+    rpa_status r = slice_proj_a(w, A, dtype, n_vc, n_g, st, err, launches);
+    if (r != RPA_OK) return r;
+  }
   proj_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
                                                        K, S, pb, eb);
   CK(cudaGetLastError());
-  if (launches) *launches += 3;
+  if (launches) *launches += 1;
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta, tb;
   if (!make_map(&ta, w.planes, K, vc_pad, S, K * 2, vc_pad * K * 2, BM, err)) return RPA_ECUDA;
@@ -1158,7 +1237,9 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   __nv_bfloat162* pb = (__nv_bfloat162*)w.planes;
   int* ea = w.exps;
   int* eb = w.exps + e_pad;
+  w.proj_a.valid = false;
   w.hook(RPA_T_SLICE, 1);
+  if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
   CK(cudaMemsetAsync(w.rowmax, 0, e_pad * sizeof(unsigned long long), st));
   row_max_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(mt, RPA_C128, n_vc,
                                                                             n_eig, n_vc, w.rowmax);

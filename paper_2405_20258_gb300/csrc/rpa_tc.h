@@ -55,6 +55,19 @@ struct Workspace {
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int debug_stall = 0;
   Hook hook;
+  // Side stream for digit slicing that overlaps the GEMMs and the eigensolve
+  // on the caller's stream.  ev_side_last marks the end of the latest batch of
+  // side-stream work; the caller's stream waits on it before it writes the
+  // shared planes, exponents or row maxima itself.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_side_last = nullptr;
+  cudaEvent_t ev_sliced[2] = {nullptr, nullptr}, ev_gemm[2] = {nullptr, nullptr};
+  // Projection A planes cut ahead of time (valid while nothing else wrote the planes).
+  struct {
+    bool valid = false;
+    const void* a = nullptr;
+    int dtype = 0, n_vc = 0, n_g = 0, S = 0;
+  } proj_a;
 };
 
 rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t max_vc,
@@ -66,6 +79,17 @@ void free_workspace(Workspace& w);
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
                 const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
                 std::string& err, int* launches);
+// The caller's stream `st` waits for all side-stream work queued so far.
+rpa_status join_side(Workspace& w, cudaStream_t st, std::string& err);
+
+// Cut the projection's A operand (the rows of A) into the digit planes on the
+// side stream, after the work queued so far on `st`, so that it overlaps the
+// eigensolve that follows on `st`; the caller joins the side stream before it
+// returns control to its user.  project() uses these planes when its A is
+// the same and no other stage wrote the planes in between; otherwise it cuts
+// them again.
+rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+                           cudaStream_t st, std::string& err, int* launches);
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
