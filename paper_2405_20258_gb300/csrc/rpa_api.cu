@@ -640,17 +640,20 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
     int nl = 0;
     s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
     if (s != RPA_OK) return s;
-    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->delta, p->ow, om, F, scale, p->chis, p->st,
-                      p->err, &nl);
+    {
+      StageTimer t(p, RPA_T_TRACE);
+      CU(p, rpa::launch_all_freq_weights(p->delta, p->ow, n_vc, om, F, p->fall, p->st));
+      p->launches += 1;
+    }
+    s = rpa::tc::chis(p->tcw, p->mt, E, n_vc, p->fall, F, scale, p->chis, p->st, p->err, &nl);
     if (s != RPA_OK) return s;
     p->launches += nl;
     {
       // the diagonal of every chi_s in FP64: the rounding of the digit-sliced
       // products then leaves Tr chi_s exact and moves E_c only at second order
       StageTimer t(p, RPA_T_TRACE);
-      CU(p, rpa::launch_all_freq_weights(p->delta, p->ow, n_vc, om, F, p->fall, p->st));
       CU(p, rpa::launch_chis_diagonal(p->mt, E, n_vc, p->fall, F, scale, p->chis, p->st));
-      p->launches += 2;
+      p->launches += 1;
     }
   } else {
     {

@@ -4,8 +4,12 @@
 //
 // GEMM kernel roles (one output tile of 128 x BN per CTA, BN = 64 or 128):
 //   warp 0      TMA producer: per 64-wide K-tile, all S digit planes of the B
-//               tile (double-buffered) and the S digit planes of the A tile
-//               through a 4-stage ring;
+//               tile (double- or triple-buffered) and the S digit planes of the
+//               A tile through a ring of slots in groups of G = min(S, NA/2);
+//               each group has one full and one empty barrier, so the MMA
+//               thread waits and commits once per group rather than per plane
+//               (G <= S keeps a group within two K-tiles, which the B buffers
+//               always cover, so the producer can fill it);
 //   warp 1      TMEM allocation and the single MMA-issuing thread: per A digit
 //               plane s, kind::f16 MMAs (K = 16 each) against the B planes
 //               t = 0 .. S-1-s taken together as one operand of BN (S - s)
@@ -39,7 +43,7 @@ constexpr int BM = 128;  // A rows per tile = TMEM lanes = MMA M
 constexpr int BK = 64;   // K elements per tile: 128 bytes of BF16, one 128B swizzle row
 // B rows per tile (= MMA N) is a template parameter: 128 when the S level
 // accumulators of 128 columns fit in TMEM (S <= 4), else 64.
-constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA)
+constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA), in groups of G slots
 constexpr int MAX_NB = 3;   // B buffers (runtime, <= MAX_NB)
 size_t g_smem_limit = 0;    // dynamic shared memory a CTA of the GEMM may use (set at first use)
 // producer warp, MMA warp, and 4 x BN/32 epilogue warps (4 lane quadrants x
@@ -251,6 +255,8 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.S, NA = p.na, NB = p.nb, NACC = p.nacc;
+  const int G = min(S, NA / 2);               // A slots per barrier group
+  const int NG = NA / G;                      // barrier groups in the ring (>= 2)
   uint8_t* sA = smem;                         // NA x 16 KB
   uint8_t* sB = smem + NA * A_TILE;           // NB x S x 8 KB
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int i = 0; i < NA; ++i) {
+    for (int i = 0; i < NG; ++i) {
       mbar_init(&full_a[i], 1);
       mbar_init(&empty_a[i], 1);
     }
@@ -296,7 +302,9 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !p.stall) {
-      int slot = 0, aphase = 0, bb = 0, bphase = 0;
+      // A planes in K order i = kt S + s fill group h = (i / G) % NG of the ring
+      const int total = nkt * S;
+      int i = 0, pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0;
       for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
         const int k0 = k_begin + kt * BK;
         if (!mbar_wait(&empty_b[bb], bphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) break;
@@ -308,16 +316,21 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           bphase ^= 1;
         }
         bool ok = true;
-        for (int s = 0; s < S; ++s) {
-          if (!mbar_wait(&empty_a[slot], aphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
-            ok = false;
-            break;
+        for (int s = 0; s < S; ++s, ++i) {
+          if (pos == 0) {
+            if (!mbar_wait(&empty_a[h], aphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full_a[h], (uint32_t)min(G, total - i) * A_TILE);
           }
-          mbar_expect_tx(&full_a[slot], A_TILE);
-          tma_load_3d(sA + slot * A_TILE, &tmA, &full_a[slot], k0, tm * BM, s);
-          if (++slot == NA) {
-            slot = 0;
-            aphase ^= 1;
+          tma_load_3d(sA + (h * G + pos) * A_TILE, &tmA, &full_a[h], k0, tm * BM, s);
+          if (++pos == G) {
+            pos = 0;
+            if (++h == NG) {
+              h = 0;
+              aphase ^= 1;
+            }
           }
         }
         if (!ok) break;
@@ -327,7 +340,8 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       unsigned first = 0;
-      int slot = 0, aphase = 0, bb = 0, bphase = 0, ab = 0, accphase = 0, kin = 0;
+      const int total = nkt * S;
+      int i = 0, pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0, ab = 0, accphase = 0, kin = 0;
       uint32_t acc_base = tmem;
       const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
       for (int kt = 0; kt < nkt; ++kt) {
@@ -338,6 +352,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           acc_base = tmem + ab * S * TS;
         }
         if (!mbar_wait(&full_b[bb], bphase, &abort_flag, p.status, ERR_WAIT_MMA)) break;
+        tc_fence_after();
         bool ok = true;
         // The B planes of this stage are contiguous (plane t at rows t BN ..), so
         // the rows of planes 0 .. S-1-s form one K-major operand; its output
@@ -345,13 +360,15 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         // The MMAs of plane s = 0 cover every level column: at the start of a
         // drain interval they overwrite instead of accumulating.
         const uint64_t bd0 = smem_desc(sB0 + bb * S * B_TILE);
-        for (int s = 0; s < S; ++s) {
-          if (!mbar_wait(&full_a[slot], aphase, &abort_flag, p.status, ERR_WAIT_MMA)) {
-            ok = false;
-            break;
+        for (int s = 0; s < S; ++s, ++i) {
+          if (pos == 0) {
+            if (!mbar_wait(&full_a[h], aphase, &abort_flag, p.status, ERR_WAIT_MMA)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
           }
-          tc_fence_after();
-          const uint64_t ad = smem_desc(sA0 + slot * A_TILE);
+          const uint64_t ad = smem_desc(sA0 + (h * G + pos) * A_TILE);
           const int rows = BN * (S - s);
           for (int c0 = 0; c0 < rows; c0 += MMA_N_MAX) {
             const int n = min(MMA_N_MAX, rows - c0);
@@ -363,10 +380,13 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
           }
           if (s == 0) first = 0;
-          mma_commit(&empty_a[slot]);
-          if (++slot == NA) {
-            slot = 0;
-            aphase ^= 1;
+          if (++pos == G || i == total - 1) {
+            mma_commit(&empty_a[h]);  // frees the group once its MMAs complete
+            pos = 0;
+            if (++h == NG) {
+              h = 0;
+              aphase ^= 1;
+            }
           }
         }
         if (!ok) break;
@@ -509,6 +529,17 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 // digit slicing (HBM-bound)
 // ---------------------------------------------------------------------------
 
+// Signed base-256 digits d_0 .. d_{S-1} of the integer Y: Y = sum_s d_s 256^(S-1-s),
+// |d_s| <= 128 for s >= 1 (and for s = 0 when |Y| < 2^(7 + 8(S-1))).
+__device__ __forceinline__ void split_digits(long long Y, int S, float* d) {
+  for (int s = S - 1; s >= 1; --s) {
+    const int dd = (int)((Y + 128) & 255) - 128;
+    d[s] = (float)dd;
+    Y = (Y - dd) >> 8;
+  }
+  d[0] = (float)Y;
+}
+
 // Signed base-256 digits of Y = round(x 2^(7 + 8(S-1) - e)) for |x| < 2^e:
 // x ~= 2^(e-7) sum_s d_s 2^(-8s), integer |d_s| <= 128 (exact in BF16).
 // Pure integer arithmetic on the IEEE fields (GB300's FP64 pipe is narrow).
@@ -526,12 +557,28 @@ __device__ __forceinline__ void cut_digits(double x, int e, int S, float* d) {
       Y = (mant + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) Y = -Y;
   }
-  for (int s = S - 1; s >= 1; --s) {
-    const int dd = (int)((Y + 128) & 255) - 128;
-    d[s] = (float)dd;
-    Y = (Y - dd) >> 8;
+  split_digits(Y, S, d);
+}
+
+// Digits of Y = round(x f 2^(7 + 8(S-1) - e)) for |x f| < 2^e and S <= 3
+// without an FP64 multiply: the product of the leading 31 bits of both
+// significands (relative error below 2^-29) is rounded to the at most 23-bit Y,
+// so Y can differ from the digits of the FP64 product only where x f 2^(F-e)
+// lies within 2^-6 of a rounding tie, by one unit of the last digit.
+constexpr int PROD_DIGITS_MAX_S = 3;
+__device__ __forceinline__ void cut_digits_prod(double x, double f, int e, int S, float* d) {
+  const long long bx = __double_as_longlong(x), bf = __double_as_longlong(f);
+  const int ex = (int)((bx >> 52) & 0x7FF), ef = (int)((bf >> 52) & 0x7FF);
+  long long Y = 0;
+  if (ex != 0 && ef != 0) {  // zero and subnormal factors give zero digits
+    const unsigned long long mx = ((bx & ((1LL << 52) - 1)) | (1LL << 52)) >> 22;  // [2^30, 2^31)
+    const unsigned long long mf = ((bf & ((1LL << 52) - 1)) | (1LL << 52)) >> 22;
+    const unsigned long long m = mx * mf;  // x f ~= m 2^(ex + ef - 2106), m < 2^62
+    const int sh = ex + ef - 2106 + 7 + 8 * (S - 1) - e;  // Y = m 2^sh, sh < -36
+    if (sh > -63) Y = (long long)((m + (1ULL << (-sh - 1))) >> (-sh));
+    if ((bx ^ bf) < 0) Y = -Y;
   }
-  d[0] = (float)Y;
+  split_digits(Y, S, d);
 }
 
 // e with m < 2^e (frexp exponent) for m > 0; 0 for m == 0.
@@ -706,36 +753,43 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
 }
 
 // f[b][vc] = ow[vc] 4 D / (D^2 + w_{k0+b}^2) for the frequencies of one group.
-__global__ void freq_weights_kernel(const double* delta, const double* ow, const double* omega,
-                                    int n_vc, int k0, int nb, double* f) {
-  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i >= (long)nb * n_vc) return;
-  const int b = (int)(i / n_vc), vc = (int)(i % n_vc);
-  const double d = delta[vc], w = omega[k0 + b], o = ow[vc];
-  f[i] = o != 0.0 ? o * (4.0 * d / (d * d + w * w)) : 0.0;
-}
-
 // Row maxima of f_b(vc) |M~[j][vc]| for the nb frequencies of a group;
-// grid (n_eig, vc chunks); rowmax[b * stride + j].
-constexpr int MAX_GROUP = 8;
-__global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const double* f,
-                                     int nb, unsigned long long* rowmax, int stride) {
+// grid (n_eig, vc chunks); rowmax[b * stride + j].  The products are formed in
+// FP32 from copies of f and |M~| rounded up and are rounded up themselves, so
+// each maximum bounds the FP64 one from above (a row exponent may come out one
+// larger, never smaller); a product above the FP32 range is taken in FP64.
+constexpr int MAX_GROUP = 8;   // frequencies per chis_b kernel launch (upper bound)
+constexpr int FREQ_GROUP = 4;  // frequencies per chi_s GEMM launch
+__global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const float* f_up,
+                                     const double* f, int nb, unsigned long long* rowmax,
+                                     int stride) {
   __shared__ double red[MAX_GROUP][32];
   const int j = blockIdx.x;
   const long v0 = (long)blockIdx.y * CHUNK, v1 = min((long)n_vc, v0 + CHUNK);
-  double m[MAX_GROUP];
+  float m[MAX_GROUP];
+  double mbig[MAX_GROUP];
 #pragma unroll
-  for (int b = 0; b < MAX_GROUP; ++b) m[b] = 0.0;
+  for (int b = 0; b < MAX_GROUP; ++b) {
+    m[b] = 0.f;
+    mbig[b] = 0.0;
+  }
   for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
     const double2 x = mt[(long)j * n_vc + vc];
-    const double a = fmax(fabs(x.x), fabs(x.y));
+    const double ad = fmax(fabs(x.x), fabs(x.y));
+    const float a = __double2float_ru(ad);
 #pragma unroll
     for (int b = 0; b < MAX_GROUP; ++b)
-      if (b < nb) m[b] = fmax(m[b], f[(long)b * n_vc + vc] * a);
+      if (b < nb) {
+        const float pr = __fmul_ru(f_up[(long)b * n_vc + vc], a);
+        if (pr <= 3.0e38f)
+          m[b] = fmaxf(m[b], pr);
+        else
+          mbig[b] = fmax(mbig[b], f[(long)b * n_vc + vc] * ad);
+      }
   }
 #pragma unroll
   for (int b = 0; b < MAX_GROUP; ++b) {
-    double v = m[b];
+    double v = fmax((double)m[b], mbig[b]);
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[b][threadIdx.x >> 5] = v;
   }
@@ -745,6 +799,12 @@ __global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, con
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[threadIdx.x][w]);
     if (mm > 0.0) atomic_max_pos(rowmax + (long)threadIdx.x * stride + j, mm);
   }
+}
+
+// f rounded up to FP32 (finite f >= 0)
+__global__ void float_up_kernel(const double* f, long n, float* out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = __double2float_ru(f[i]);
 }
 
 // chi_s B operand of the group's frequencies: for row j, f_b(vc) M~[j][vc] as
@@ -773,8 +833,13 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
       if (b >= nb) break;
       const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
       float dr[MAX_SLICES], di[MAX_SLICES];
-      cut_digits(fv * x.x, e[b], S, dr);
-      cut_digits(fv * x.y, e[b], S, di);
+      if (S <= PROD_DIGITS_MAX_S) {
+        cut_digits_prod(x.x, fv, e[b], S, dr);
+        cut_digits_prod(x.y, fv, e[b], S, di);
+      } else {
+        cut_digits(fv * x.x, e[b], S, dr);
+        cut_digits(fv * x.y, e[b], S, di);
+      }
       for (int s = 0; s < S; ++s) {
         __nv_bfloat162* p0 = planes + (long)(b * S + s) * plane + (long)(2 * j) * (K / 2) + vc;
         p0[0] = __floats2bfloat162_rn(dr[s], di[s]);
@@ -859,7 +924,7 @@ void gemm_shape(int S, int* na, int* nb, int* nacc) {
   const int BN = pick_bn(S);
   const size_t B_TILE = (size_t)BN * BK * 2;
   const int want_na = std::min(MAX_NA, std::max(2, env_int("RPA_TC_NA", MAX_NA)));
-  const int want_nb = std::min(MAX_NB, std::max(2, env_int("RPA_TC_NB", MAX_NB)));
+  const int want_nb = std::min(MAX_NB, std::max(2, env_int("RPA_TC_NB", 2)));
   const int want_acc = std::min(2, std::max(1, env_int("RPA_TC_NACC", 2)));
   *nacc = (want_acc == 2 && BN == 64 && 2 * S * BN <= 512) ? 2 : 1;  // BN 128: one set
   for (int b = want_nb; b >= 2; --b)
@@ -996,21 +1061,22 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.slices = s;
   const long g_pad = rup(max_g, BM), e_pad = rup(max_eig, BM), vc_pad = rup(max_vc, BM);
   const long k_vc = rup(2 * max_vc, BK), k_g = rup(2 * max_g, BK);
-  const int grp = (int)std::min<size_t>(MAX_GROUP, max_freq);
+  // chi_s: two alternating buffers of the B planes of FREQ_GROUP frequencies
+  const int grp = (int)std::min<size_t>(FREQ_GROUP, max_freq);
   w.freq_group = grp;
   w.chi0_blocks = std::max(1, env_int("RPA_TC_CHI0_BLOCKS", 32));
   const long k_blk = rup(2 * rup(cdiv(max_vc, w.chi0_blocks), 32), BK);
   // chi~(0) double-buffers the planes of its K-blocks (one cut while the other multiplies)
   size_t p1 = std::max({(size_t)2 * s.chi0 * 2 * g_pad * k_blk, (size_t)s.proj * vc_pad * k_g,
-                        (size_t)grp * s.chis * 2 * e_pad * k_vc});
+                        (size_t)2 * grp * s.chis * 2 * e_pad * k_vc});
   size_t p2 = std::max((size_t)s.proj * 2 * e_pad * k_g, (size_t)s.chis * e_pad * k_vc);
   w.plane_bytes = p1 * 2;
   w.plane2_bytes = p2 * 2;
   w.exp_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)e_pad}) +
-                std::max((size_t)g_pad, (size_t)grp * e_pad);
-  w.rowmax_count = std::max({(size_t)2 * g_pad, (size_t)vc_pad, (size_t)grp * e_pad});
+                std::max((size_t)g_pad, (size_t)2 * grp * e_pad);
+  w.rowmax_count = std::max({(size_t)2 * g_pad, (size_t)vc_pad, (size_t)2 * grp * e_pad});
   w.work_count = 1 << 20;
-  w.fweight_count = (size_t)grp * max_vc;
+  w.fweight_count = max_freq * max_vc;
   auto al = [&](void** p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -1025,7 +1091,7 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
       !al((void**)&w.exps, w.exp_count * sizeof(int)) ||
       !al((void**)&w.rowmax, w.rowmax_count * sizeof(unsigned long long)) ||
       !al((void**)&w.work, w.work_count * sizeof(int4)) || !al((void**)&w.status, sizeof(int)) ||
-      !al((void**)&w.fweights, w.fweight_count * sizeof(double))) {
+      !al((void**)&w.fweights, w.fweight_count * sizeof(float))) {
     free_workspace(w);
     return RPA_ENOMEM;
   }
@@ -1228,15 +1294,14 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   return r;
 }
 
-rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
-                const double* ow, const double* omega, int n_freq, double scale, cplx* out,
-                cudaStream_t st, std::string& err, int* launches) {
+rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
+                int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
+                int* launches) {
   const int S = w.slices.chis;
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_vc, BK);
+  const int grp = w.freq_group;
   __nv_bfloat162* pa = (__nv_bfloat162*)w.planes2;
-  __nv_bfloat162* pb = (__nv_bfloat162*)w.planes;
   int* ea = w.exps;
-  int* eb = w.exps + e_pad;
   w.proj_a.valid = false;
   w.hook(RPA_T_SLICE, 1);
   if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
@@ -1247,30 +1312,42 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   slice_rows_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
       mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea);
   CK(cudaGetLastError());
-  if (launches) *launches += 2;
+  float_up_kernel<<<std::min(cdiv((long)n_freq * n_vc, 256), 4096), 256, 0, st>>>(
+      f, (long)n_freq * n_vc, w.fweights);
+  CK(cudaGetLastError());
+  if (launches) *launches += 3;
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta;
   if (!make_map(&ta, w.planes2, K, e_pad, S, K * 2, e_pad * K * 2, BM, err)) return RPA_ECUDA;
   const int tiles_m = cdiv(n_eig, BM);
-  for (int k0 = 0; k0 < n_freq; k0 += w.freq_group) {
-    const int nb = std::min(w.freq_group, n_freq - k0);
+  // B planes of frequency groups in two alternating buffers: group g + 1 is cut
+  // on the side stream while group g is multiplied on `st`.
+  const size_t buf_pairs = (size_t)grp * S * 2 * e_pad * (K / 2);  // BF16 pairs per buffer
+  if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
+  int g = 0;
+  for (int k0 = 0; k0 < n_freq; k0 += grp, ++g) {
+    const int nb = std::min(grp, n_freq - k0), buf = g & 1;
+    __nv_bfloat162* pb = (__nv_bfloat162*)w.planes + buf * buf_pairs;
+    int* eb = w.exps + e_pad + (size_t)buf * grp * e_pad;
+    unsigned long long* rowmax = w.rowmax + (size_t)buf * grp * e_pad;
+    if (g >= 2) CK(cudaStreamWaitEvent(w.side, w.ev_gemm[buf], 0));
+    CK(cudaMemsetAsync(rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), w.side));
+    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, w.side>>>(
+        (const double2*)mt, n_eig, n_vc, w.fweights + (size_t)k0 * n_vc, f + (size_t)k0 * n_vc,
+        nb, rowmax, (int)e_pad);
+    CK(cudaGetLastError());
+    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, w.side>>>(
+        (const double2*)mt, n_eig, (int)e_pad, n_vc, K, f + (size_t)k0 * n_vc, nb, S, rowmax, pb,
+        eb, (int)e_pad);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(w.ev_sliced[buf], w.side));
+    CK(cudaEventRecord(w.ev_side_last, w.side));
+    if (launches) *launches += 2;
     w.hook(RPA_T_SLICE, 1);
-    freq_weights_kernel<<<cdiv((long)nb * n_vc, 256), 256, 0, st>>>(delta, ow, omega, n_vc, k0,
-                                                                    nb, w.fweights);
-    CK(cudaGetLastError());
-    CK(cudaMemsetAsync(w.rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), st));
-    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(
-        (const double2*)mt, n_eig, n_vc, w.fweights, nb, w.rowmax, (int)e_pad);
-    CK(cudaGetLastError());
-    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
-        (const double2*)mt, n_eig, (int)e_pad, n_vc, K, w.fweights, nb, S, w.rowmax, pb, eb,
-        (int)e_pad);
-    CK(cudaGetLastError());
-    if (launches) *launches += 3;
+    CK(cudaStreamWaitEvent(st, w.ev_sliced[buf], 0));
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap tb;
-    if (!make_map(&tb, w.planes, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S),
-                  err))
+    if (!make_map(&tb, pb, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S), err))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
@@ -1287,10 +1364,11 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
     a.ld_col = 1;
     a.conj = 0;
     w.hook(RPA_T_CHIS, 1);
-    rpa_status s = run_gemm(w, ta, tb, a, tiles_m, nb, true, a.out,
+    rpa_status r = run_gemm(w, ta, tb, a, tiles_m, nb, true, a.out,
                             sizeof(cplx) * (size_t)nb * n_eig * n_eig, st, err, launches);
     w.hook(RPA_T_CHIS, 0);
-    if (s != RPA_OK) return s;
+    if (r != RPA_OK) return r;
+    CK(cudaEventRecord(w.ev_gemm[buf], st));
   }
   return RPA_OK;
 }

@@ -48,10 +48,10 @@ struct Workspace {
   int4* work = nullptr;       // tile work list
   size_t work_count = 0;
   int* status = nullptr;      // device error word of the bounded waits
-  double* fweights = nullptr; // transition weights of one frequency group
+  float* fweights = nullptr;  // transition weights f(omega_k) rounded up to FP32, [n_freq][n_vc]
   size_t fweight_count = 0;
   Slices slices;
-  int freq_group = 8;
+  int freq_group = 4;         // frequencies per chi_s GEMM launch
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int debug_stall = 0;
   Hook hook;
@@ -92,9 +92,11 @@ rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int
                            cudaStream_t st, std::string& err, int* launches);
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
-rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* delta,
-                const double* ow, const double* omega, int n_freq, double scale, cplx* out,
-                cudaStream_t st, std::string& err, int* launches);
+// chi_s(i omega_k) for all k from M~ and the transition weights f[k][vc] of every
+// frequency (FP64, device).
+rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
+                int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
+                int* launches);
 
 }  // namespace tc
 }  // namespace rpa
