@@ -16,11 +16,15 @@
 //               rows, whose output columns land in the level accumulators
 //               L = s + t (levels sit BN columns apart in TMEM);
 //   BN/8 epilogue warps (4 lane quadrants x BN/32 column blocks): at the end
-//               of each drain interval, read the S level
-//               accumulators (exact integers) from TMEM, scale by 2^-8L and add
-//               them into per-thread double-float registers (one TMEM lane and
-//               32 columns per thread); finally apply the row scales and write
-//               complex FP64 results.
+//               of each drain interval, read the level accumulators from TMEM
+//               and add them into per-thread double-float accumulators (one
+//               TMEM lane and 32 columns per thread); finally apply the row
+//               scales and write complex FP64 results.
+// Digit planes are stored pre-scaled (plane s holds d_s 2^-8s), so level L
+// sums integers times 2^-8L.  Levels L < Le (p.nexact) have accumulators of
+// their own and stay exact (integer sums below 2^24 over a drain interval);
+// levels Le .. S-1, which weigh at most 2^-8Le of the leading one, share one
+// FP32 "tail" accumulator whose rounding stays far below the truncation.
 // Every mbarrier wait is bounded (about 2 s of SM clock): on expiry the CTA
 // raises a flag in the status word, stops issuing, frees TMEM and returns.
 #include <cuda.h>
@@ -29,6 +33,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -96,6 +101,7 @@ struct GemmArgs {
   int accumulate;     // add into the output with FP64 atomics, never zero it
   const double* rsa;  // optional FP64 factor per A row (NULL: 1)
   const double* rsb;  // optional FP64 factor per complex B column (NULL: 1)
+  int nexact;         // levels with exact accumulators (Le); the rest share a tail
   int stall;          // test hook: the producer issues nothing
   int* status;
 };
@@ -255,6 +261,8 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.S, NA = p.na, NB = p.nb, NACC = p.nacc;
+  const int Le = min(p.nexact, S);            // exact levels
+  const int NL = Le < S ? Le + 1 : S;         // accumulators: exact levels (+ tail)
   const int G = min(S, NA / 2);               // A slots per barrier group
   const int NG = NA / G;                      // barrier groups in the ring (>= 2)
   uint8_t* sA = smem;                         // NA x 16 KB
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
   const int nkt = (k_end - k_begin) / BK;
   const int kdt = p.kd_tiles;
   const int niv = (nkt + kdt - 1) / kdt;
-  const int used = NACC * S * TS + (BN == 128 ? BN : 0);  // + low halves for BN = 128
+  const int used = NACC * NL * TS + (BN == 128 ? BN : 0);  // + low halves for BN = 128
   const uint32_t ncols = used <= 32 ? 32 : (used <= 64 ? 64 : (used <= 128 ? 128 : (used <= 256 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
@@ -349,17 +357,19 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           if (!mbar_wait(&acc_empty[ab], accphase ^ 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
           tc_fence_after();
           first = 1;
-          acc_base = tmem + ab * S * TS;
+          acc_base = tmem + ab * NL * TS;
         }
         if (!mbar_wait(&full_b[bb], bphase, &abort_flag, p.status, ERR_WAIT_MMA)) break;
         tc_fence_after();
         bool ok = true;
         // The B planes of this stage are contiguous (plane t at rows t BN ..), so
-        // the rows of planes 0 .. S-1-s form one K-major operand; its output
-        // column t BN + j goes to TMEM column (s + t) BN + j = level s + t.
-        // The MMAs of plane s = 0 cover every level column: at the start of a
-        // drain interval they overwrite instead of accumulating.
+        // the rows of planes 0 .. Le-1-s form one K-major operand; its output
+        // column t BN + j goes to TMEM column (s + t) BN + j = exact level s + t.
+        // Pairs with s + t >= Le go one plane at a time into the tail.  The
+        // first MMAs of an interval into a column range overwrite it: plane
+        // s = 0 covers every exact level, and its first tail MMA the tail.
         const uint64_t bd0 = smem_desc(sB0 + bb * S * B_TILE);
+        bool tail_first = first;
         for (int s = 0; s < S; ++s, ++i) {
           if (pos == 0) {
             if (!mbar_wait(&full_a[h], aphase, &abort_flag, p.status, ERR_WAIT_MMA)) {
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             tc_fence_after();
           }
           const uint64_t ad = smem_desc(sA0 + (h * G + pos) * A_TILE);
-          const int rows = BN * (S - s);
+          const int rows = s < Le ? BN * (min(S, Le) - s) : 0;
           for (int c0 = 0; c0 < rows; c0 += MMA_N_MAX) {
             const int n = min(MMA_N_MAX, rows - c0);
             const uint32_t id = idesc_n(n);
@@ -378,6 +388,15 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             mma_bf16(d, ad, bd, id, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
             for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
+          }
+          for (int t = max(0, Le - s); t <= S - 1 - s; ++t) {
+            const uint32_t id = idesc_n(BN);
+            const uint64_t bd = bd0 + (uint64_t)((t * BN * BK * 2) >> 4);
+            const uint32_t d = acc_base + Le * TS;
+            mma_bf16(d, ad, bd, id, tail_first ? 0u : 1u);
+#pragma unroll
+            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
+            tail_first = false;
           }
           if (s == 0) first = 0;
           if (++pos == G || i == total - 1) {
@@ -416,7 +435,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
     const int q = warp & 3;              // TMEM lane quadrant of this warp
     const int h = (warp - 2) >> 2;       // which 32-column block of the BN columns
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    const uint32_t lo_base = lane_base + S * TS + CPT * h;  // used when kLoTmem
+    const uint32_t lo_base = lane_base + NACC * NL * TS + CPT * h;  // used when kLoTmem
     float hi[CPT], lo[NLO];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) hi[c] = 0.f;
@@ -444,15 +463,14 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           uint32_t lr[8];
           tmem_ld8(lo_base + c0, lr);
           tmem_wait_ld();
-          for (int L = 0; L < S; ++L) {
-            const float sc = __int_as_float((127 - 8 * L) << 23);  // 2^-8L, exact
+          for (int L = 0; L < NL; ++L) {
             uint32_t r[8];
-            tmem_ld8(lane_base + (ab * S + L) * TS + CPT * h + c0, r);
+            tmem_ld8(lane_base + (ab * NL + L) * TS + CPT * h + c0, r);
             tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               float l = __uint_as_float(lr[c]);
-              dfloat_add(hi[c0 + c], l, __uint_as_float(r[c]) * sc);
+              dfloat_add(hi[c0 + c], l, __uint_as_float(r[c]));
               lr[c] = __float_as_uint(l);
             }
           }
@@ -460,9 +478,8 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         }
         tmem_wait_st();
       } else {
-        for (int L = 0; L < S; ++L) {
-          const float sc = __int_as_float((127 - 8 * L) << 23);  // 2^-8L, exact
-          const uint32_t ta = lane_base + (ab * S + L) * TS + CPT * h;
+        for (int L = 0; L < NL; ++L) {
+          const uint32_t ta = lane_base + (ab * NL + L) * TS + CPT * h;
 #pragma unroll
           for (int c0 = 0; c0 < CPT; c0 += 8) {
             uint32_t r[8];
@@ -470,7 +487,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-              dfloat_add(hi[c0 + c], lo[(c0 + c) % NLO], __uint_as_float(r[c]) * sc);
+              dfloat_add(hi[c0 + c], lo[(c0 + c) % NLO], __uint_as_float(r[c]));
           }
         }
       }
@@ -529,12 +546,14 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 // digit slicing (HBM-bound)
 // ---------------------------------------------------------------------------
 
-// Signed base-256 digits d_0 .. d_{S-1} of the integer Y: Y = sum_s d_s 256^(S-1-s),
-// |d_s| <= 128 for s >= 1 (and for s = 0 when |Y| < 2^(7 + 8(S-1))).
+// Signed base-256 digits of the integer Y = sum_s d_s 256^(S-1-s), |d_s| <= 128
+// for s >= 1 (and for s = 0 when |Y| < 2^(7 + 8(S-1))), returned pre-scaled as
+// d[s] = d_s 2^-8s (exact in BF16): the product of digits s and t then carries
+// its level's weight 2^-8(s+t) by itself.
 __device__ __forceinline__ void split_digits(long long Y, int S, float* d) {
   for (int s = S - 1; s >= 1; --s) {
     const int dd = (int)((Y + 128) & 255) - 128;
-    d[s] = (float)dd;
+    d[s] = (float)dd * __int_as_float((127 - 8 * s) << 23);
     Y = (Y - dd) >> 8;
   }
   d[0] = (float)Y;
@@ -759,7 +778,7 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
 // each maximum bounds the FP64 one from above (a row exponent may come out one
 // larger, never smaller); a product above the FP32 range is taken in FP64.
 constexpr int MAX_GROUP = 8;   // frequencies per chis_b kernel launch (upper bound)
-constexpr int FREQ_GROUP = 4;  // frequencies per chi_s GEMM launch
+constexpr int CHIS_PLANE_GB = 64;  // default budget of the two chi_s B plane buffers
 __global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const float* f_up,
                                      const double* f, int nb, unsigned long long* rowmax,
                                      int stride) {
@@ -856,10 +875,29 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
 inline long rup(long a, long b) { return (a + b - 1) / b * b; }
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
-int drain_tiles(int S) {
-  // exact FP32 sums need K_d * (L+1) * 2^14 <= 2^24 for every level L <= S-1
-  int kd = (1024 / S) / BK * BK;
+int env_int(const char* name, int dflt);
+
+int drain_tiles(int Le) {
+  // exact FP32 sums need K_d * (L+1) * 2^14 <= 2^24 for every exact level L <= Le-1
+  int kd = (1024 / Le) / BK * BK;
   return std::max(1, kd / BK);
+}
+
+// Level accumulators for S slices of which Le are exact: Le, plus one tail.
+int n_levels(int S, int Le) { return Le < S ? Le + 1 : S; }
+
+// Exact levels per stage: chi~(0) and chi_s with S >= 3 slices keep their two
+// lowest-weight levels in the tail (weights 2^-8(S-2) and below relative to the
+// leading level; the FP32 rounding of their sum stays below the truncation of
+// the digit expansion); the projection, whose accuracy the whole subspace
+// rests on, keeps every level exact.  RPA_TC_LE_<STAGE> overrides (tuning).
+int clamp_levels(int Le, int S) { return std::max(1, std::min(S, Le)); }
+int exact_levels_chi0(int S) {
+  return clamp_levels(env_int("RPA_TC_LE_CHI0", S >= 3 ? S - 2 : S), S);
+}
+int exact_levels_proj(int S) { return clamp_levels(env_int("RPA_TC_LE_PROJ", S), S); }
+int exact_levels_chis(int S) {
+  return clamp_levels(env_int("RPA_TC_LE_CHIS", S >= 3 ? S - 2 : S), S);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -909,24 +947,24 @@ int env_int(const char* name, int dflt) {
   return v && *v ? atoi(v) : dflt;
 }
 
-// B rows per tile for S slices: 128 when the S level accumulators of 128
-// columns and the 128 columns of double-float low halves fit in TMEM (S <= 3),
+// B rows per tile: 128 when the level accumulators of 128 columns and the 128
+// columns of double-float low halves fit in TMEM (at most 3 accumulators),
 // else 64.  Level accumulators start at multiples of 64 TMEM columns.
-int pick_bn(int S) {
+int pick_bn(int S, int Le) {
   const int cap = env_int("RPA_TC_BN", 128);
-  if (cap >= 128 && (S + 1) * 128 <= 512) return 128;
+  if (cap >= 128 && (n_levels(S, Le) + 1) * 128 <= 512) return 128;
   return 64;
 }
 
 // Pipeline shape for S slices: the deepest A ring and B buffering that fit in
 // shared memory (up to the knobs), two TMEM accumulator sets when they fit.
-void gemm_shape(int S, int* na, int* nb, int* nacc) {
-  const int BN = pick_bn(S);
+void gemm_shape(int S, int Le, int* na, int* nb, int* nacc) {
+  const int BN = pick_bn(S, Le), NL = n_levels(S, Le);
   const size_t B_TILE = (size_t)BN * BK * 2;
   const int want_na = std::min(MAX_NA, std::max(2, env_int("RPA_TC_NA", MAX_NA)));
   const int want_nb = std::min(MAX_NB, std::max(2, env_int("RPA_TC_NB", 2)));
   const int want_acc = std::min(2, std::max(1, env_int("RPA_TC_NACC", 2)));
-  *nacc = (want_acc == 2 && BN == 64 && 2 * S * BN <= 512) ? 2 : 1;  // BN 128: one set
+  *nacc = (want_acc == 2 && BN == 64 && 2 * NL * BN <= 512) ? 2 : 1;  // BN 128: one set
   for (int b = want_nb; b >= 2; --b)
     for (int a = want_na; a >= 2; --a)
       if (1024 + (size_t)a * A_TILE + (size_t)b * S * B_TILE <= g_smem_limit) {
@@ -938,10 +976,10 @@ void gemm_shape(int S, int* na, int* nb, int* nacc) {
   *nb = 2;
 }
 
-size_t gemm_smem(int S) {
+size_t gemm_smem(int S, int Le) {
   int na, nb, nacc;
-  gemm_shape(S, &na, &nb, &nacc);
-  return 1024 + (size_t)na * A_TILE + (size_t)nb * S * ((size_t)pick_bn(S) * BK * 2);
+  gemm_shape(S, Le, &na, &nb, &nacc);
+  return 1024 + (size_t)na * A_TILE + (size_t)nb * S * ((size_t)pick_bn(S, Le) * BK * 2);
 }
 
 // Build the work list (upper block triangle when `upper`), choose split-K, launch.
@@ -949,9 +987,9 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
                     int tiles_m, int batches, bool upper, void* zero_ptr,
                     size_t zero_bytes, cudaStream_t st, std::string& err, int* launches) {
   std::vector<int4> work;
-  const int BN = pick_bn(a.S);
+  const int BN = pick_bn(a.S, a.nexact);
   const int tiles_n = cdiv(a.b_rows, BN);
-  const int kdt = drain_tiles(a.S);
+  const int kdt = drain_tiles(std::min(a.nexact, a.S));
   const int kd = kdt * BK;
   int tiles = 0;
   for (int b = 0; b < batches; ++b)
@@ -1025,8 +1063,8 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
     }
     g_smem_limit = lim;
   }
-  gemm_shape(a.S, &a.na, &a.nb, &a.nacc);
-  const size_t smem = gemm_smem(a.S);
+  gemm_shape(a.S, a.nexact, &a.na, &a.nb, &a.nacc);
+  const size_t smem = gemm_smem(a.S, a.nexact);
   if (smem > g_smem_limit) {
     err = "slice GEMM: shared memory of the pipeline exceeds the device limit";
     return RPA_EINVAL;
@@ -1061,9 +1099,15 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.slices = s;
   const long g_pad = rup(max_g, BM), e_pad = rup(max_eig, BM), vc_pad = rup(max_vc, BM);
   const long k_vc = rup(2 * max_vc, BK), k_g = rup(2 * max_g, BK);
-  // chi_s: two alternating buffers of the B planes of FREQ_GROUP frequencies
-  const int grp = (int)std::min<size_t>(FREQ_GROUP, max_freq);
+  // chi_s: two alternating buffers of the B planes of up to MAX_GROUP frequencies,
+  // as many as fit in a budget (RPA_TC_CHIS_GB, default 64 GB) for both buffers
+  const double per_freq = (double)s.chis * 2 * e_pad * k_vc * 2;
+  const long budget = (long)std::max(1, env_int("RPA_TC_CHIS_GB", CHIS_PLANE_GB)) << 30;
+  const int fit = (int)std::max(1.0, std::floor(budget / (2.0 * per_freq)));
+  const int grp = (int)std::min<size_t>(
+      std::max(1, std::min({MAX_GROUP, fit, env_int("RPA_TC_CHIS_GROUP", MAX_GROUP)})), max_freq);
   w.freq_group = grp;
+  w.chis_overlap = env_int("RPA_TC_CHIS_OVERLAP", 1) != 0;
   w.chi0_blocks = std::max(1, env_int("RPA_TC_CHI0_BLOCKS", 32));
   const long k_blk = rup(2 * rup(cdiv(max_vc, w.chi0_blocks), 32), BK);
   // chi~(0) double-buffers the planes of its K-blocks (one cut while the other multiplies)
@@ -1139,7 +1183,7 @@ static rpa_status side_fork(Workspace& w, cudaStream_t st, std::string& err) {
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
                 const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
                 std::string& err, int* launches) {
-  const int S = w.slices.chi0;
+  const int S = w.slices.chi0, Le = exact_levels_chi0(S);
   const long g_pad = rup(n_g, BM);
   // K-blocks of the transitions in `order` (sorted by sqrt f(0)): each block has
   // its own per-row digit exponents, so rows keep more significant bits where
@@ -1185,10 +1229,11 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
     const long plane_bytes = 2 * g_pad * K * 2;
     // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
     if (!make_map(&ta, planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
-    if (!make_map(&tb, planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S), err))
+    if (!make_map(&tb, planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S, Le), err))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
+    a.nexact = Le;
     a.K = (int)K;
     a.ea = exps;
     a.eb = exps;
@@ -1269,10 +1314,12 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta, tb;
   if (!make_map(&ta, w.planes, K, vc_pad, S, K * 2, vc_pad * K * 2, BM, err)) return RPA_ECUDA;
-  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S), err))
+  const int Le = exact_levels_proj(S);
+  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le), err))
     return RPA_ECUDA;
   GemmArgs a{};
   a.S = S;
+  a.nexact = Le;
   a.K = (int)K;
   a.ea = ea;
   a.eb = eb;
@@ -1297,7 +1344,7 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
                 int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
                 int* launches) {
-  const int S = w.slices.chis;
+  const int S = w.slices.chis, Le = exact_levels_chis(S);
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_vc, BK);
   const int grp = w.freq_group;
   __nv_bfloat162* pa = (__nv_bfloat162*)w.planes2;
@@ -1324,33 +1371,37 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   // on the side stream while group g is multiplied on `st`.
   const size_t buf_pairs = (size_t)grp * S * 2 * e_pad * (K / 2);  // BF16 pairs per buffer
   if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
+  cudaStream_t cut = w.chis_overlap ? w.side : st;
   int g = 0;
   for (int k0 = 0; k0 < n_freq; k0 += grp, ++g) {
     const int nb = std::min(grp, n_freq - k0), buf = g & 1;
     __nv_bfloat162* pb = (__nv_bfloat162*)w.planes + buf * buf_pairs;
     int* eb = w.exps + e_pad + (size_t)buf * grp * e_pad;
     unsigned long long* rowmax = w.rowmax + (size_t)buf * grp * e_pad;
-    if (g >= 2) CK(cudaStreamWaitEvent(w.side, w.ev_gemm[buf], 0));
-    CK(cudaMemsetAsync(rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), w.side));
-    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, w.side>>>(
+    if (g >= 2) CK(cudaStreamWaitEvent(cut, w.ev_gemm[buf], 0));
+    if (cut == st) w.hook(RPA_T_SLICE, 1);
+    CK(cudaMemsetAsync(rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), cut));
+    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, n_vc, w.fweights + (size_t)k0 * n_vc, f + (size_t)k0 * n_vc,
         nb, rowmax, (int)e_pad);
     CK(cudaGetLastError());
-    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, w.side>>>(
+    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, (int)e_pad, n_vc, K, f + (size_t)k0 * n_vc, nb, S, rowmax, pb,
         eb, (int)e_pad);
     CK(cudaGetLastError());
-    CK(cudaEventRecord(w.ev_sliced[buf], w.side));
-    CK(cudaEventRecord(w.ev_side_last, w.side));
+    CK(cudaEventRecord(w.ev_sliced[buf], cut));
+    CK(cudaEventRecord(w.ev_side_last, cut));
     if (launches) *launches += 2;
-    w.hook(RPA_T_SLICE, 1);
+    if (cut != st) w.hook(RPA_T_SLICE, 1);
     CK(cudaStreamWaitEvent(st, w.ev_sliced[buf], 0));
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap tb;
-    if (!make_map(&tb, pb, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S), err))
+    if (!make_map(&tb, pb, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le),
+                  err))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
+    a.nexact = Le;
     a.K = (int)K;
     a.ea = ea;
     a.eb = eb;

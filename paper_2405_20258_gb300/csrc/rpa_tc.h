@@ -51,7 +51,8 @@ struct Workspace {
   float* fweights = nullptr;  // transition weights f(omega_k) rounded up to FP32, [n_freq][n_vc]
   size_t fweight_count = 0;
   Slices slices;
-  int freq_group = 4;         // frequencies per chi_s GEMM launch
+  int freq_group = 8;         // frequencies per chi_s GEMM launch
+  bool chis_overlap = true;   // cut the chi_s B planes on the side stream
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int debug_stall = 0;
   Hook hook;
