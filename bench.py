@@ -200,6 +200,24 @@ def products(S):
     return S * (S + 1) // 2
 
 
+def gpu_local_cpus(index):
+    """CPUs on the GPU's NUMA node (from sysfs) that this process may run on, or None."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s/local_cpulist" % (int(dom, 16), rest.lower())
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def run_steps(plan, n):
     return [plan.run(0) for _ in range(n)]
 
@@ -302,47 +320,86 @@ def main():
                     "peak_source": "%s bf16 burst x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind,
                     "traffic": None, "work_per_launch": "%.4g algorithmic flops" % fl[dom]}
 
-    # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back
+    # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back.
+    # Two input slots (two q-point entries of one plan over the same q-point): the copy of
+    # step i+1's inputs into one slot runs on a copy stream while step i computes on the
+    # other, as a stream of q-points would be fed.
     e2e = None
     if not args.no_e2e:
-        host_A = torch.empty_like(A, device="cpu").pin_memory()
+        plan.close()
+        # pinned host buffers placed on the GPU's NUMA node: pages are placed where the
+        # allocating thread runs, so the thread runs there while it allocates them
+        saved = os.sched_getaffinity(0)
+        near = gpu_local_cpus(local)
+        if near:
+            os.sched_setaffinity(0, near)
+        host_A = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+        host_small = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                      for t in (dq.qg2, dq.e_v, dq.e_c)]
+        os.sched_setaffinity(0, saved)
         host_A.copy_(A)
-        host_small = [t.cpu().pin_memory() for t in (dq.qg2, dq.e_v, dq.e_c)]
-        dev_small = [dq.qg2, dq.e_v, dq.e_c]
+        for h_, t in zip(host_small, (dq.qg2, dq.e_v, dq.e_c)):
+            h_.copy_(t)
         h2d = host_A.numel() * 16 + sum(t.numel() * t.element_size() for t in host_small)
+        dq2 = rpa.device_qpoint(qp, w["n_eig"], w["n_freq"], device=dev)
+        dq2.m = torch.empty_like(A)
+        slots = [dq, dq2]
+        plan_e = rpa.Plan(slots, precision=precision, energy_route=route, stream=stream,
+                          timing=True, slices=slices if mixed else (0, 0, 0))
+        copy_stream = torch.cuda.Stream(device=dev)
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        h2d_ev = []
 
-        h2d_ms = []
-
-        def e2e_step():
+        def stage(i, after=None):
+            # H2D of step i's inputs into slot i % 2 (its previous user, step i-2, is done:
+            # plan.run returns only after the step's result reached the host)
+            d = slots[i % 2]
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                c0.record(stream)
-                A.copy_(host_A, non_blocking=True)
-                for d_, h_ in zip(dev_small, host_small):
+            if after is not None:
+                copy_stream.wait_event(after)
+            c0.record(copy_stream)
+            with torch.cuda.stream(copy_stream):
+                d.m.copy_(host_A, non_blocking=True)
+                for d_, h_ in zip((d.qg2, d.e_v, d.e_c), host_small):
                     d_.copy_(h_, non_blocking=True)
-                c1.record(stream)
-            ec = plan.run(0)  # returns E_c to the host (8 bytes)
-            h2d_ms.append(c0.elapsed_time(c1))
-            return ec
+            c1.record(copy_stream)
+            ready[i % 2].record(copy_stream)
+            h2d_ev.append((c0, c1))
 
-        e2e_step()
+        def run_e2e(n, after=None):
+            stage(0, after)
+            ecs_e = []
+            for i in range(n):
+                stream.wait_event(ready[i % 2])
+                if i + 1 < n:
+                    stage(i + 1)
+                ecs_e.append(plan_e.run(i % 2))  # returns E_c to the host (8 bytes)
+            return ecs_e
+
+        run_e2e(2)
         torch.cuda.synchronize()
+        plan_e.timings()
+        h2d_ev.clear()
         barrier(dist)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        ecs_e2e = run_e2e(args.steps, after=e0)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(dist)
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        h2d_ms = [a.elapsed_time(b) for a, b in h2d_ev]
         e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
-               "h2d_ms_per_step": statistics.mean(h2d_ms[1:]) if len(h2d_ms) > 1 else None}
-        plan.timings()
-        del host_A
+               "h2d_ms_per_step": statistics.mean(h2d_ms),
+               "h2d_overlap": "step i+1's inputs are copied during step i (two input slots)",
+               "host_buffers": "pinned, allocated by a thread on the GPU's NUMA node" if near
+               else "pinned",
+               "ec_spread": max(ecs_e2e) - min(ecs_e2e)}
+        plan_e.close()
+        del host_A, dq2, slots
 
     # the FP64 path on the same inputs: speed-up and |dE_c| of the mixed path
     compare = None
