@@ -195,6 +195,13 @@ def reference_arm(args, w, rank, dist):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+# DRAM traffic (read + write) of one chi~(0) slice_gemm launch at N_G = 4000 with K-blocks
+# of 8,000 transitions and S = 4, from the ncu capture summarised in
+# profiles/slice_gemm_chi0_ng4000.md (a K = 32,000 launch scaled to K = 16,000). Valid for
+# the GEMM kernel as captured; set to None when the kernel changes until it is re-captured.
+CHI0_GEMM_TRAFFIC = {"workload": "qpoint-4000", "slices": 4, "bytes_per_launch": 3.49e9}
+
+
 def products(S):
     """BF16 digit-product contractions per algorithmic one: pairs (s, t), s + t <= S - 1."""
     return S * (S + 1) // 2
@@ -306,11 +313,17 @@ def main():
         nprod = products(dict(chi0=slices[0], proj=slices[1], chis=slices[2])[dom])
         peak = pk["bf16_tflops_sustained"]
         achieved = fl[dom] * nprod / dom_s / 1e12
+        traffic = None
+        if (dom == "chi0" and CHI0_GEMM_TRAFFIC and args.workload == CHI0_GEMM_TRAFFIC["workload"]
+                and slices[0] == CHI0_GEMM_TRAFFIC["slices"]):
+            traffic = CHI0_GEMM_TRAFFIC["bytes_per_launch"]
         roofline = {"bound": "tensor", "kernel": "slice_gemm (%s)" % dom, "achieved": achieved,
                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "peak_source": "%s bf16 sustained (MEASURED_PEAKS.json)" % pk_kind,
-                    "traffic": None, "work_per_launch": "%d digit-product contractions x %.4g "
-                    "algorithmic flops" % (nprod, fl[dom]),
+                    "traffic": traffic,
+                    "traffic_unit": "bytes per launch (ncu dram read + write)",
+                    "work_per_step": "%d digit-product contractions x %.4g algorithmic flops, "
+                    "all launches of the stage" % (nprod, fl[dom]),
                     "fp64_equivalent_tflops": fl[dom] / dom_s / 1e12}
     else:
         peak = pk["bf16_tflops"] * FP64_OVER_BF16

@@ -546,23 +546,10 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 // digit slicing (HBM-bound)
 // ---------------------------------------------------------------------------
 
-// Signed base-256 digits of the integer Y = sum_s d_s 256^(S-1-s), |d_s| <= 128
-// for s >= 1 (and for s = 0 when |Y| < 2^(7 + 8(S-1))), returned pre-scaled as
-// d[s] = d_s 2^-8s (exact in BF16): the product of digits s and t then carries
-// its level's weight 2^-8(s+t) by itself.
-__device__ __forceinline__ void split_digits(long long Y, int S, float* d) {
-  for (int s = S - 1; s >= 1; --s) {
-    const int dd = (int)((Y + 128) & 255) - 128;
-    d[s] = (float)dd * __int_as_float((127 - 8 * s) << 23);
-    Y = (Y - dd) >> 8;
-  }
-  d[0] = (float)Y;
-}
-
-// Signed base-256 digits of Y = round(x 2^(7 + 8(S-1) - e)) for |x| < 2^e:
-// x ~= 2^(e-7) sum_s d_s 2^(-8s), integer |d_s| <= 128 (exact in BF16).
+// Y = round(x 2^(7 + 8(S-1) - e)) for |x| < 2^e, whose signed base-256 digits
+// give x ~= 2^(e-7) sum_s d_s 2^(-8s), integer |d_s| <= 128 (exact in BF16).
 // Pure integer arithmetic on the IEEE fields (GB300's FP64 pipe is narrow).
-__device__ __forceinline__ void cut_digits(double x, int e, int S, float* d) {
+__device__ __forceinline__ long long digits_y(double x, int e, int S) {
   const long long bits = __double_as_longlong(x);
   const int bexp = (int)((bits >> 52) & 0x7FF);
   const int F = 7 + 8 * (S - 1);
@@ -576,16 +563,40 @@ __device__ __forceinline__ void cut_digits(double x, int e, int S, float* d) {
       Y = (mant + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) Y = -Y;
   }
-  split_digits(Y, S, d);
+  return Y;
 }
 
-// Digits of Y = round(x f 2^(7 + 8(S-1) - e)) for |x f| < 2^e and S <= 3
-// without an FP64 multiply: the product of the leading 31 bits of both
+// The signed base-256 digits of Y = sum_s d_s 256^(S-1-s) for a complex value
+// (yr, yi), |d_s| <= 128 for s >= 1 (and for s = 0 when |Y| < 2^(7 + 8(S-1))),
+// least significant first, handed to put(s, d_s^r 2^-8s, d_s^i 2^-8s) one plane at
+// a time.  The pre-scaled digit d_s 2^-8s is exact in BF16, and the product of
+// digits s and t then carries its level's weight 2^-8(s+t) by itself.
+template <class Put>
+__device__ __forceinline__ void emit_digits(long long yr, long long yi, int S, Put put) {
+#pragma unroll 1
+  for (int s = S - 1; s >= 0; --s) {
+    int dr, di;
+    if (s > 0) {
+      dr = (int)((yr + 128) & 255) - 128;
+      di = (int)((yi + 128) & 255) - 128;
+      yr = (yr - dr) >> 8;
+      yi = (yi - di) >> 8;
+    } else {
+      dr = (int)yr;
+      di = (int)yi;
+    }
+    const float sc = __int_as_float((127 - 8 * s) << 23);
+    put(s, (float)dr * sc, (float)di * sc);
+  }
+}
+
+// Y = round(x f 2^(7 + 8(S-1) - e)) for |x f| < 2^e and S <= 3 without an FP64
+// multiply: the product of the leading 31 bits of both
 // significands (relative error below 2^-29) is rounded to the at most 23-bit Y,
 // so Y can differ from the digits of the FP64 product only where x f 2^(F-e)
 // lies within 2^-6 of a rounding tie, by one unit of the last digit.
 constexpr int PROD_DIGITS_MAX_S = 3;
-__device__ __forceinline__ void cut_digits_prod(double x, double f, int e, int S, float* d) {
+__device__ __forceinline__ long long digits_y_prod(double x, double f, int e, int S) {
   const long long bx = __double_as_longlong(x), bf = __double_as_longlong(f);
   const int ex = (int)((bx >> 52) & 0x7FF), ef = (int)((bf >> 52) & 0x7FF);
   long long Y = 0;
@@ -597,7 +608,7 @@ __device__ __forceinline__ void cut_digits_prod(double x, double f, int e, int S
     if (sh > -63) Y = (long long)((m + (1ULL << (-sh - 1))) >> (-sh));
     if ((bx ^ bf) < 0) Y = -Y;
   }
-  split_digits(Y, S, d);
+  return Y;
 }
 
 // e with m < 2^e (frexp exponent) for m > 0; 0 for m == 0.
@@ -675,14 +686,13 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, in
     const int vc = vc0 + tx;  // K pair index
     if ((long)2 * vc >= K) continue;
     double2 x = t[tx][r];
-    float dr[MAX_SLICES], di[MAX_SLICES];
-    cut_digits(x.x, es[r], S, dr);
-    cut_digits(x.y, es[r], S, di);
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat162* p0 = planes + s * plane + (long)(2 * g) * (K / 2) + vc;
-      p0[0] = __floats2bfloat162_rn(dr[s], di[s]);
-      p0[K / 2] = __floats2bfloat162_rn(di[s], -dr[s]);
-    }
+    __nv_bfloat162* p = planes + (long)(2 * g) * (K / 2) + vc;
+    emit_digits(digits_y(x.x, es[r], S), digits_y(x.y, es[r], S), S,
+                [&](int s, float fr, float fi) {
+                  __nv_bfloat162* p0 = p + s * plane;
+                  p0[0] = __floats2bfloat162_rn(fr, fi);
+                  p0[K / 2] = __floats2bfloat162_rn(fi, -fr);
+                });
   }
 }
 
@@ -725,11 +735,9 @@ __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_row
   for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
     if (r < n_rows && k < n_cplx) x = load_any(src, dtype, (long)r * ld + k);
-    float dr[MAX_SLICES], di[MAX_SLICES];
-    cut_digits(x.x, e, S, dr);
-    cut_digits(x.y, e, S, di);
-    for (int s = 0; s < S; ++s)
-      planes[s * plane + (long)r * (K / 2) + k] = __floats2bfloat162_rn(dr[s], di[s]);
+    __nv_bfloat162* p = planes + (long)r * (K / 2) + k;
+    emit_digits(digits_y(x.x, e, S), digits_y(x.y, e, S), S,
+                [&](int s, float fr, float fi) { p[s * plane] = __floats2bfloat162_rn(fr, fi); });
   }
 }
 
@@ -760,14 +768,12 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
   for (long g = threadIdx.x; g < K / 2; g += blockDim.x) {
     double2 b = make_double2(0.0, 0.0);
     if (i < n_eig && g < n_g) b = B[g * n_eig + i];
-    float dr[MAX_SLICES], di[MAX_SLICES];
-    cut_digits(b.x, e, S, dr);
-    cut_digits(b.y, e, S, di);
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat162* p0 = planes + s * plane + (long)(2 * i) * (K / 2) + g;
-      p0[0] = __floats2bfloat162_rn(dr[s], -di[s]);
-      p0[K / 2] = __floats2bfloat162_rn(di[s], dr[s]);
-    }
+    __nv_bfloat162* p = planes + (long)(2 * i) * (K / 2) + g;
+    emit_digits(digits_y(b.x, e, S), digits_y(b.y, e, S), S, [&](int s, float fr, float fi) {
+      __nv_bfloat162* p0 = p + s * plane;
+      p0[0] = __floats2bfloat162_rn(fr, -fi);
+      p0[K / 2] = __floats2bfloat162_rn(fi, fr);
+    });
   }
 }
 
@@ -833,37 +839,38 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
                                     const unsigned long long* rowmax, __nv_bfloat162* planes,
                                     int* exps, int eb_stride) {
   const int j = blockIdx.x;
-  int e[MAX_GROUP];
-#pragma unroll
-  for (int b = 0; b < MAX_GROUP; ++b) {
+  __shared__ int e[MAX_GROUP];
+  if (threadIdx.x < MAX_GROUP) {
+    const int b = threadIdx.x;
     e[b] = (b < nb && j < n_eig)
                ? row_exponent(__longlong_as_double((long long)rowmax[(long)b * eb_stride + j]))
                : 0;
-    if (blockIdx.y == 0 && threadIdx.x == 0 && b < nb) exps[b * eb_stride + j] = e[b];
+    if (blockIdx.y == 0 && b < nb) exps[b * eb_stride + j] = e[b];
   }
+  __syncthreads();
   const long plane = (long)2 * n_eig_pad * (K / 2);
   const long v0 = (long)blockIdx.y * CHUNK, v1 = min(K / 2, v0 + CHUNK);
   for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
     const bool in = j < n_eig && vc < n_vc;
     if (in) x = mt[(long)j * n_vc + vc];
-#pragma unroll
-    for (int b = 0; b < MAX_GROUP; ++b) {
-      if (b >= nb) break;
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
       const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
-      float dr[MAX_SLICES], di[MAX_SLICES];
+      long long yr, yi;
       if (S <= PROD_DIGITS_MAX_S) {
-        cut_digits_prod(x.x, fv, e[b], S, dr);
-        cut_digits_prod(x.y, fv, e[b], S, di);
+        yr = digits_y_prod(x.x, fv, e[b], S);
+        yi = digits_y_prod(x.y, fv, e[b], S);
       } else {
-        cut_digits(fv * x.x, e[b], S, dr);
-        cut_digits(fv * x.y, e[b], S, di);
+        yr = digits_y(fv * x.x, e[b], S);
+        yi = digits_y(fv * x.y, e[b], S);
       }
-      for (int s = 0; s < S; ++s) {
-        __nv_bfloat162* p0 = planes + (long)(b * S + s) * plane + (long)(2 * j) * (K / 2) + vc;
-        p0[0] = __floats2bfloat162_rn(dr[s], di[s]);
-        p0[K / 2] = __floats2bfloat162_rn(-di[s], dr[s]);
-      }
+      __nv_bfloat162* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
+      emit_digits(yr, yi, S, [&](int s, float fr, float fi) {
+        __nv_bfloat162* p0 = p + s * plane;
+        p0[0] = __floats2bfloat162_rn(fr, fi);
+        p0[K / 2] = __floats2bfloat162_rn(-fi, fr);
+      });
     }
   }
 }
