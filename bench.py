@@ -373,7 +373,11 @@ def main():
                 copy_stream.wait_event(after)
             c0.record(copy_stream)
             with torch.cuda.stream(copy_stream):
-                d.m.copy_(host_A, non_blocking=True)
+                # in chunks of ~256 MB, so that the small transfers of the running step
+                # (its eigensolver's and its result's) are not queued behind one 16 GB copy
+                rows = max(1, (256 << 20) // (host_A.shape[1] * 16))
+                for r0 in range(0, host_A.shape[0], rows):
+                    d.m[r0:r0 + rows].copy_(host_A[r0:r0 + rows], non_blocking=True)
                 for d_, h_ in zip((d.qg2, d.e_v, d.e_c), host_small):
                     d_.copy_(h_, non_blocking=True)
             c1.record(copy_stream)

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "rpa_internal.h"
 
@@ -45,8 +47,9 @@ struct Workspace {
   size_t exp_count = 0;
   unsigned long long* rowmax = nullptr;  // per-row max |x| (double bits)
   size_t rowmax_count = 0;
-  int4* work = nullptr;       // tile work list
-  size_t work_count = 0;
+  int4* work = nullptr;       // tile work lists (each distinct list uploaded once)
+  size_t work_count = 0, work_used = 0;
+  std::vector<std::pair<std::vector<int4>, size_t>> work_cache;  // list, offset in `work`
   int* status = nullptr;      // device error word of the bounded waits
   float* fweights = nullptr;  // transition weights f(omega_k) rounded up to FP32, [n_freq][n_vc]
   size_t fweight_count = 0;

@@ -103,3 +103,23 @@ def test_bounded_wait_reports_timeout():
     with rpa.Plan([rpa.device_qpoint(qp, 8, 2, A=A)], precision=rpa.RPA_MIXED,
                   slices=(7, 7, 7)) as plan:
         assert abs(plan.run(0) - ref) < 1e-11 * abs(ref)
+
+
+@pytest.mark.parametrize("env", [
+    {"RPA_TC_LE_CHI0": "5", "RPA_TC_LE_CHIS": "4"},   # every level exact, no tail
+    {"RPA_TC_CHIS_OVERLAP": "0"},                      # chi_s planes cut on the plan stream
+    {"RPA_TC_CHIS_GROUP": "1"},                        # one frequency per group: buffer reuse
+    {"RPA_TC_BN": "64"},                               # narrow tiles everywhere
+    {"RPA_TC_NA": "3", "RPA_TC_NB": "3", "RPA_TC_NACC": "1"},  # other pipeline depths
+])
+def test_gemm_variants_agree(env, monkeypatch):
+    """Tail accumulator, side-stream cutting, tile width and pipeline depth are
+    implementation choices: every variant gives the default's E_c and chi~ to
+    within the digit truncation of (5, 6, 4) slices."""
+    qp, A = problem(200, 4, 50)
+    base = run_gpu(qp, A, 40, 6, precision=1, slices=(5, 6, 4))
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    got = run_gpu(qp, A, 40, 6, precision=1, slices=(5, 6, 4))
+    assert rel_fro(got["chit"], base["chit"]) < 1e-10
+    assert abs(got["ec"] - base["ec"]) < 1e-10 * abs(base["ec"])
