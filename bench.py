@@ -31,6 +31,8 @@ WORKLOADS = {
     "qpoint-400": dict(n_g=400, n_v=16, n_c=200, n_eig=40, n_freq=16),
     # small case for ncu captures (A is 0.5 GB, larger than L2)
     "qpoint-1024": dict(n_g=1024, n_v=32, n_c=1000, n_eig=128, n_freq=16),
+    # the interface-sized q-point with complex64 matrix elements drawn on the device (50 GB)
+    "qpoint-12000": dict(n_g=12000, n_v=256, n_c=2048, n_eig=1200, n_freq=48, m_dtype="c64"),
 }
 # FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
@@ -270,7 +272,11 @@ def main():
                             q_twentieths=(1, 0, 0) if iq == 0 else inputs.qgrid_4x4x4()[iq])
     n_vc = w["n_v"] * w["n_c"]
     dq = rpa.device_qpoint(qp, w["n_eig"], w["n_freq"], device=dev)
-    A = torch.empty((n_vc, w["n_g"]), dtype=torch.complex128, device=dev)
+    c64 = w.get("m_dtype") == "c64"
+    A = torch.empty((n_vc, w["n_g"]), dtype=torch.complex64 if c64 else torch.complex128,
+                    device=dev)
+    if c64:
+        dq.m_dtype = rpa.RPA_C64
     with torch.cuda.stream(stream):
         rpa.rpa_generate_m(dq, 0, w["n_v"], 0, w["n_c"], A, stream=stream)
     stream.synchronize()
@@ -353,7 +359,8 @@ def main():
         host_A.copy_(A)
         for h_, t in zip(host_small, (dq.qg2, dq.e_v, dq.e_c)):
             h_.copy_(t)
-        h2d = host_A.numel() * 16 + sum(t.numel() * t.element_size() for t in host_small)
+        h2d = host_A.numel() * host_A.element_size() + sum(t.numel() * t.element_size()
+                                                          for t in host_small)
         dq2 = rpa.device_qpoint(qp, w["n_eig"], w["n_freq"], device=dev)
         dq2.m = torch.empty_like(A)
         slots = [dq, dq2]
@@ -455,7 +462,7 @@ def main():
         "data": "synthetic (splitmix64 matrix elements drawn on the device)",
         "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
                    "slices": list(slices) if mixed else None, "energy_route": args.route,
-                   "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * 16 / 1e9),
+                   "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
         "contraction_tflops": contraction_tflops,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},

@@ -785,6 +785,7 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
 // larger, never smaller); a product above the FP32 range is taken in FP64.
 constexpr int MAX_GROUP = 8;   // frequencies per chis_b kernel launch (upper bound)
 constexpr int CHIS_PLANE_GB = 64;  // default budget of the two chi_s B plane buffers
+constexpr int PROJ_PLANE_GB = 48;  // default budget of the projection's A planes
 __global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const float* f_up,
                                      const double* f, int nb, unsigned long long* rowmax,
                                      int stride) {
@@ -1140,8 +1141,16 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.chis_overlap = env_int("RPA_TC_CHIS_OVERLAP", 1) != 0;
   w.chi0_blocks = std::max(1, env_int("RPA_TC_CHI0_BLOCKS", 32));
   const long k_blk = rup(2 * rup(cdiv(max_vc, w.chi0_blocks), 32), BK);
+  // projection: the A planes of all rows if they fit in the budget (RPA_TC_PROJ_GB,
+  // default 48 GB), else chunks of rows (tile-height multiples) one after another
+  const long proj_budget = (long)std::max(1, env_int("RPA_TC_PROJ_GB", PROJ_PLANE_GB)) << 30;
+  const long proj_row_bytes = (long)s.proj * k_g * 2;
+  w.proj_chunk = std::max<long>(BM, std::min<long>(vc_pad, proj_budget / proj_row_bytes / BM * BM));
+  if (env_int("RPA_TC_PROJ_CHUNK", 0) > 0)  // test hook: force small chunks
+    w.proj_chunk = std::max<long>(BM, rup(env_int("RPA_TC_PROJ_CHUNK", 0), BM));
   // chi~(0) double-buffers the planes of its K-blocks (one cut while the other multiplies)
-  size_t p1 = std::max({(size_t)2 * s.chi0 * 2 * g_pad * k_blk, (size_t)s.proj * vc_pad * k_g,
+  size_t p1 = std::max({(size_t)2 * s.chi0 * 2 * g_pad * k_blk,
+                        (size_t)s.proj * std::min<long>(vc_pad, w.proj_chunk) * k_g,
                         (size_t)2 * grp * s.chis * 2 * e_pad * k_vc});
   size_t p2 = std::max((size_t)s.proj * 2 * e_pad * k_g, (size_t)s.chis * e_pad * k_vc);
   w.plane_bytes = p1 * 2;
@@ -1290,16 +1299,29 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
 }
 
 // rows of A -> S digit planes of the projection's A operand and exponents ea
-static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+// Rows of A per projection chunk: all of them when their digit planes fit in the
+// plane budget, else a multiple of the tile height (the planes of one chunk at a time).
+static long proj_chunk_rows(const Workspace& w, int n_vc) {
+  return std::min<long>(rup(n_vc, BM), w.proj_chunk);
+}
+
+// A byte offset of `rows` rows of A (n_g complex elements each, complex128 or complex64).
+static const void* a_rows_at(const void* A, int dtype, long row, int n_g) {
+  return (const char*)A + row * n_g * (dtype == RPA_C64 ? 8 : 16);
+}
+
+// rows [r0, r0 + nr) of A -> S digit planes of the projection's A operand and exponents ea
+static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, long r0, int nr, int n_g,
                                cudaStream_t s, std::string& err, int* launches) {
   const int S = w.slices.proj;
-  const long vc_pad = rup(n_vc, BM), K = rup(2L * n_g, BK);
-  CK(cudaMemsetAsync(w.rowmax, 0, vc_pad * sizeof(unsigned long long), s));
-  row_max_kernel<<<dim3((unsigned)n_vc, cdiv(n_g, CHUNK)), 256, 0, s>>>(A, dtype, n_g, n_vc, n_g,
-                                                                         w.rowmax);
+  const long rpad = rup(nr, BM), K = rup(2L * n_g, BK);
+  const void* a0 = a_rows_at(A, dtype, r0, n_g);
+  CK(cudaMemsetAsync(w.rowmax, 0, rpad * sizeof(unsigned long long), s));
+  row_max_kernel<<<dim3((unsigned)nr, cdiv(n_g, CHUNK)), 256, 0, s>>>(a0, dtype, n_g, nr, n_g,
+                                                                      w.rowmax);
   CK(cudaGetLastError());
-  slice_rows_kernel<<<dim3((unsigned)vc_pad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
-      A, dtype, n_g, n_vc, n_g, (int)vc_pad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps);
+  slice_rows_kernel<<<dim3((unsigned)rpad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
+      a0, dtype, n_g, nr, n_g, (int)rpad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps);
   CK(cudaGetLastError());
   if (launches) *launches += 2;
   return RPA_OK;
@@ -1309,7 +1331,8 @@ rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int
                            cudaStream_t st, std::string& err, int* launches) {
   w.proj_a.valid = false;
   if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
-  rpa_status r = slice_proj_a(w, A, dtype, n_vc, n_g, w.side, err, launches);
+  const int nr = (int)std::min<long>(n_vc, proj_chunk_rows(w, n_vc));  // the first chunk
+  rpa_status r = slice_proj_a(w, A, dtype, 0, nr, n_g, w.side, err, launches);
   if (r != RPA_OK) return r;
   CK(cudaEventRecord(w.ev_side_last, w.side));
   w.proj_a.valid = true;
@@ -1324,51 +1347,63 @@ rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches) {
   const int S = w.slices.proj;
-  const long vc_pad = rup(n_vc, BM), e_pad = rup(n_eig, BM), K = rup(2L * n_g, BK);
+  const long chunk = proj_chunk_rows(w, n_vc);
+  const long e_pad = rup(n_eig, BM), K = rup(2L * n_g, BK);
+  const bool chunked = chunk < n_vc;
   __nv_bfloat162* pb = (__nv_bfloat162*)w.planes2;
   int* ea = w.exps;
-  int* eb = w.exps + std::max({rup(n_g, BM), vc_pad, e_pad});
+  int* eb = w.exps + std::max({rup(n_g, BM), rup(std::min<long>(chunk, n_vc), BM), e_pad});
   const bool ready = w.proj_a.valid && w.proj_a.a == A && w.proj_a.dtype == dtype &&
                      w.proj_a.n_vc == n_vc && w.proj_a.n_g == n_g && w.proj_a.S == S;
   w.proj_a.valid = false;  // the chi_s stage reuses the planes next
   w.hook(RPA_T_SLICE, 1);
   if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
-  if (!ready) {
-    rpa_status r = slice_proj_a(w, A, dtype, n_vc, n_g, st, err, launches);
-    if (r != RPA_OK) return r;
-  }
   proj_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
                                                        K, S, pb, eb);
   CK(cudaGetLastError());
   if (launches) *launches += 1;
+  // chunks of the output's columns are added with FP64 atomics into a zeroed M~
+  if (chunked) CK(cudaMemsetAsync(mt, 0, sizeof(cplx) * (size_t)n_eig * n_vc, st));
   w.hook(RPA_T_SLICE, 0);
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, w.planes, K, vc_pad, S, K * 2, vc_pad * K * 2, BM, err)) return RPA_ECUDA;
   const int Le = exact_levels_proj(S);
+  CUtensorMap tb;
   if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le), err))
     return RPA_ECUDA;
-  GemmArgs a{};
-  a.S = S;
-  a.nexact = Le;
-  a.K = (int)K;
-  a.ea = ea;
-  a.eb = eb;
-  a.eb_stride = 0;
-  a.a_rows = n_vc;
-  a.b_rows = 2 * n_eig;
-  a.alpha = 1.0;
-  a.out = (double2*)mt;
-  a.out_bstride = 0;
-  a.ld_row = 1;
-  a.ld_col = n_vc;
-  a.conj = 1;
-  a.atomic = 0;
-  const int tiles_m = cdiv(n_vc, BM);
-  w.hook(RPA_T_PROJ, 1);
-  rpa_status r = run_gemm(w, ta, tb, a, tiles_m, 1, false, mt,
-                          sizeof(cplx) * (size_t)n_eig * n_vc, st, err, launches);
-  w.hook(RPA_T_PROJ, 0);
-  return r;
+  for (long r0 = 0; r0 < n_vc; r0 += chunk) {
+    const int nr = (int)std::min<long>(chunk, n_vc - r0);
+    const long rpad = rup(nr, BM);
+    if (r0 > 0 || !ready) {
+      w.hook(RPA_T_SLICE, 1);
+      rpa_status r = slice_proj_a(w, A, dtype, r0, nr, n_g, st, err, launches);
+      w.hook(RPA_T_SLICE, 0);
+      if (r != RPA_OK) return r;
+    }
+    CUtensorMap ta;
+    if (!make_map(&ta, w.planes, K, rpad, S, K * 2, rpad * K * 2, BM, err)) return RPA_ECUDA;
+    GemmArgs a{};
+    a.S = S;
+    a.nexact = Le;
+    a.K = (int)K;
+    a.ea = ea;
+    a.eb = eb;
+    a.eb_stride = 0;
+    a.a_rows = nr;
+    a.b_rows = 2 * n_eig;
+    a.alpha = 1.0;
+    a.out = (double2*)(mt + r0);
+    a.out_bstride = 0;
+    a.ld_row = 1;
+    a.ld_col = n_vc;
+    a.conj = 1;
+    a.atomic = 0;
+    a.accumulate = chunked ? 1 : 0;
+    w.hook(RPA_T_PROJ, 1);
+    rpa_status r = run_gemm(w, ta, tb, a, cdiv(nr, BM), 1, false, mt,
+                            sizeof(cplx) * (size_t)n_eig * n_vc, st, err, launches);
+    w.hook(RPA_T_PROJ, 0);
+    if (r != RPA_OK) return r;
+  }
+  return RPA_OK;
 }
 
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,

@@ -55,6 +55,7 @@ struct Workspace {
   size_t fweight_count = 0;
   Slices slices;
   int freq_group = 8;         // frequencies per chi_s GEMM launch
+  long proj_chunk = 0;        // rows of A whose projection planes are cut at a time
   bool chis_overlap = true;   // cut the chi_s B planes on the side stream
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int debug_stall = 0;

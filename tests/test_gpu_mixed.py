@@ -111,11 +111,12 @@ def test_bounded_wait_reports_timeout():
     {"RPA_TC_CHIS_GROUP": "1"},                        # one frequency per group: buffer reuse
     {"RPA_TC_BN": "64"},                               # narrow tiles everywhere
     {"RPA_TC_NA": "3", "RPA_TC_NB": "3", "RPA_TC_NACC": "1"},  # other pipeline depths
+    {"RPA_TC_PROJ_CHUNK": "128"},                      # projection in chunks of 128 rows of A
 ])
 def test_gemm_variants_agree(env, monkeypatch):
-    """Tail accumulator, side-stream cutting, tile width and pipeline depth are
-    implementation choices: every variant gives the default's E_c and chi~ to
-    within the digit truncation of (5, 6, 4) slices."""
+    """Tail accumulator, side-stream cutting, tile width, pipeline depth and the
+    projection's row chunks are implementation choices: every variant gives the
+    default's E_c and chi~ to within the digit truncation of (5, 6, 4) slices."""
     qp, A = problem(200, 4, 50)
     base = run_gpu(qp, A, 40, 6, precision=1, slices=(5, 6, 4))
     for k, v in env.items():
