@@ -51,6 +51,7 @@ constexpr int BK = 64;   // K elements per tile: 128 bytes of BF16, one 128B swi
 constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA), in groups of G slots
 constexpr int MAX_NB = 3;   // B buffers (runtime, <= MAX_NB)
 size_t g_smem_limit = 0;    // dynamic shared memory a CTA of the GEMM may use (set at first use)
+int g_num_sms = 0;          // streaming multiprocessors of the device (set at first use)
 // producer warp, MMA warp, and 4 x BN/32 epilogue warps (4 lane quadrants x
 // BN/32 column blocks of 32 accumulator columns)
 template <int BN>
@@ -90,6 +91,7 @@ struct GemmArgs {
   int kd_tiles;       // K-tiles per drain interval
   int k_per_split;    // K elements per split (multiple of BK)
   const int4* work;   // (tile_m, tile_n, batch, k_split)
+  int n_work;         // tiles in the list; CTA b takes tiles b, b + gridDim.x, ...
   const int* ea;      // exponent per A row
   const int* eb;      // exponent per complex B row pair, [batch][eb_stride]
   int eb_stride;
@@ -268,13 +270,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
   uint8_t* sA = smem;                         // NA x 16 KB
   uint8_t* sB = smem + NA * A_TILE;           // NB x S x 8 KB
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 wk = p.work[blockIdx.x];
-  const int tm = wk.x, tn = wk.y, batch = wk.z, ks = wk.w;
-  const int k_begin = ks * p.k_per_split;
-  const int k_end = min(p.K, k_begin + p.k_per_split);
-  const int nkt = (k_end - k_begin) / BK;
   const int kdt = p.kd_tiles;
-  const int niv = (nkt + kdt - 1) / kdt;
   const int used = NACC * NL * TS + (BN == 128 ? BN : 0);  // + low halves for BN = 128
   const uint32_t ncols = used <= 32 ? 32 : (used <= 64 ? 64 : (used <= 128 ? 128 : (used <= 256 ? 256 : 512)));
 
@@ -310,12 +306,23 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !p.stall) {
-      // A planes in K order i = kt S + s fill group h = (i / G) % NG of the ring
+      // A planes of a tile in K order i = kt S + s fill groups of G slots of the
+      // ring; a group ends after G planes or at the tile's last plane
+      int pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0;
+      bool ok = true;
+      for (int wi = blockIdx.x; wi < p.n_work && ok; wi += gridDim.x) {
+      const int4 wk = p.work[wi];
+      const int tm = wk.x, tn = wk.y, batch = wk.z;
+      const int k_begin = wk.w * p.k_per_split;
+      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
       const int total = nkt * S;
-      int i = 0, pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0;
+      int i = 0;
       for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
         const int k0 = k_begin + kt * BK;
-        if (!mbar_wait(&empty_b[bb], bphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) break;
+        if (!mbar_wait(&empty_b[bb], bphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
+          ok = false;
+          break;
+        }
         mbar_expect_tx(&full_b[bb], S * B_TILE);
         for (int t = 0; t < S; ++t)
           tma_load_3d(sB + (bb * S + t) * B_TILE, &tmB, &full_b[bb], k0, tn * BN, batch * S + t);
@@ -323,7 +330,6 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           bb = 0;
           bphase ^= 1;
         }
-        bool ok = true;
         for (int s = 0; s < S; ++s, ++i) {
           if (pos == 0) {
             if (!mbar_wait(&empty_a[h], aphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             mbar_expect_tx(&full_a[h], (uint32_t)min(G, total - i) * A_TILE);
           }
           tma_load_3d(sA + (h * G + pos) * A_TILE, &tmA, &full_a[h], k0, tm * BM, s);
-          if (++pos == G) {
+          if (++pos == G || i == total - 1) {
             pos = 0;
             if (++h == NG) {
               h = 0;
@@ -343,15 +349,22 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         }
         if (!ok) break;
       }
+      }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       unsigned first = 0;
-      const int total = nkt * S;
-      int i = 0, pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0, ab = 0, accphase = 0, kin = 0;
+      int pos = 0, h = 0, aphase = 0, bb = 0, bphase = 0, ab = 0, accphase = 0;
       uint32_t acc_base = tmem;
       const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+      bool alive = true;
+      for (int wi = blockIdx.x; wi < p.n_work && alive; wi += gridDim.x) {
+      const int k_begin = p.work[wi].w * p.k_per_split;
+      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
+      const int total = nkt * S;
+      int i = 0, kin = 0;
+      alive = false;
       for (int kt = 0; kt < nkt; ++kt) {
         if (kin == 0) {
           if (!mbar_wait(&acc_empty[ab], accphase ^ 1, &abort_flag, p.status, ERR_WAIT_MMA)) break;
@@ -422,6 +435,9 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             accphase ^= 1;
           }
         }
+        if (kt == nkt - 1) alive = true;  // the tile completed
+      }
+      if (nkt == 0) alive = true;
       }
     }
   } else {
@@ -436,6 +452,14 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
     const int h = (warp - 2) >> 2;       // which 32-column block of the BN columns
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t lo_base = lane_base + NACC * NL * TS + CPT * h;  // used when kLoTmem
+    int ivg = 0;  // drain intervals consumed so far (all tiles of this CTA)
+    bool ok = true;
+    for (int wi = blockIdx.x; wi < p.n_work && ok; wi += gridDim.x) {
+    const int4 wk = p.work[wi];
+    const int tm = wk.x, tn = wk.y, batch = wk.z;
+    const int k_begin = wk.w * p.k_per_split;
+    const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
+    const int niv = (nkt + kdt - 1) / kdt;
     float hi[CPT], lo[NLO];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) hi[c] = 0.f;
@@ -447,10 +471,9 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
       for (int c0 = 0; c0 < CPT; c0 += 8) tmem_st8(lo_base + c0, z);
       tmem_wait_st();
     }
-    bool ok = true;
-    for (int iv = 0; iv < niv; ++iv) {
-      const int ab = iv % NACC;
-      const bool got = mbar_wait_sleep(&acc_full[ab], (iv / NACC) & 1, &abort_flag, p.status,
+    for (int iv = 0; iv < niv; ++iv, ++ivg) {
+      const int ab = ivg % NACC;
+      const bool got = mbar_wait_sleep(&acc_full[ab], (ivg / NACC) & 1, &abort_flag, p.status,
                                        ERR_WAIT_EPILOGUE);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
@@ -532,6 +555,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           }
         }
       }
+    }
     }
   }
   tc_fence_before();
@@ -1093,6 +1117,11 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
       return RPA_ECUDA;
     }
     g_smem_limit = lim;
+    if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
+        cudaSuccess) {
+      err = std::string("querying the SM count: ") + cudaGetErrorString(e);
+      return RPA_ECUDA;
+    }
   }
   gemm_shape(a.S, a.nexact, &a.na, &a.nb, &a.nacc);
   const size_t smem = gemm_smem(a.S, a.nexact);
@@ -1100,10 +1129,15 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
     err = "slice GEMM: shared memory of the pipeline exceeds the device limit";
     return RPA_EINVAL;
   }
+  // persistent: one CTA per SM (the pipeline fills the shared memory), each taking every
+  // grid-th tile of the rasterised list, so a tile's epilogue overlaps the next tile's MMAs
+  a.n_work = (int)work.size();
+  const unsigned grid = (unsigned)std::min<long>(
+      a.n_work, std::max(1, env_int("RPA_TC_GRID", g_num_sms > 0 ? g_num_sms : a.n_work)));
   if (BN == 128)
-    slice_gemm_kernel<128><<<(unsigned)work.size(), threads_for<128>(), smem, st>>>(ta, tb, a);
+    slice_gemm_kernel<128><<<grid, threads_for<128>(), smem, st>>>(ta, tb, a);
   else
-    slice_gemm_kernel<64><<<(unsigned)work.size(), threads_for<64>(), smem, st>>>(ta, tb, a);
+    slice_gemm_kernel<64><<<grid, threads_for<64>(), smem, st>>>(ta, tb, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("slice GEMM launch: ") + cudaGetErrorString(e);
