@@ -22,8 +22,16 @@
  *  - Complex arrays are interleaved (re, im) pairs, row-major, in DEVICE memory
  *    unless the argument says "host".  The caller owns every array it passes;
  *    the plan owns its workspace and frees it in rpa_plan_destroy.
- *  - All work is enqueued on the plan's CUDA stream.  Only rpa_ecorr (which
- *    returns energies to the host) and rpa_plan_create synchronise.
+ *  - All work is enqueued on the plan's CUDA stream.  rpa_plan_create,
+ *    rpa_subspace_basis (it reads the eigensolver's status), rpa_plan_frequencies
+ *    and rpa_ecorr (both return values to the host) synchronise it.  The mixed
+ *    path also cuts digit planes on an internal stream of its own, which every
+ *    entry point joins into the plan's stream before it returns, so a caller
+ *    sees all of a call's work ordered on the plan's stream.
+ *  - Memory: the mixed path's digit planes are sized for the largest q-point
+ *    within budgets (about 64 GB for the chi_s planes, 48 GB for the
+ *    projection's, which then runs in row chunks); the rest is a few arrays of
+ *    the problem's own sizes.
  *  - Errors are returned, never aborted on.  After RPA_EINVAL or RPA_ESTATE the
  *    plan is unchanged and stays usable.  rpa_last_error() gives a message.
  *  - Stages of one q-point must run in order chi0 -> basis -> freq -> ecorr;
