@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -201,7 +202,7 @@ def reference_arm(args, w, rank, dist):
 # of 8,000 transitions and S = 4, from the ncu capture summarised in
 # profiles/slice_gemm_chi0_ng4000.md (a K = 32,000 launch scaled to K = 16,000). Valid for
 # the GEMM kernel as captured; set to None when the kernel changes until it is re-captured.
-CHI0_GEMM_TRAFFIC = None
+CHI0_GEMM_TRAFFIC = {"workload": "qpoint-4000", "slices": 4, "bytes_per_launch": 3.61e9}
 
 
 def products(S):
@@ -372,23 +373,30 @@ def main():
 
         def stage(i, after=None):
             # H2D of step i's inputs into slot i % 2 (its previous user, step i-2, is done:
-            # plan.run returns only after the step's result reached the host)
+            # plan.run returns only after the step's result reached the host).  Runs in a
+            # thread that keeps at most two 256 MB pieces queued on the copy engine, so that
+            # the small transfers of the running step (its eigensolver's) are not queued
+            # behind the whole 16 GB.
             d = slots[i % 2]
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
-            if after is not None:
-                copy_stream.wait_event(after)
-            c0.record(copy_stream)
-            with torch.cuda.stream(copy_stream):
-                # in chunks of ~256 MB, so that the small transfers of the running step
-                # (its eigensolver's and its result's) are not queued behind one 16 GB copy
-                rows = max(1, (256 << 20) // (host_A.shape[1] * 16))
+            rows = max(1, (256 << 20) // (host_A.shape[1] * host_A.element_size()))
+            with torch.cuda.device(dev), torch.cuda.stream(copy_stream):
+                if after is not None:
+                    copy_stream.wait_event(after)
+                c0.record(copy_stream)
+                inflight = []
                 for r0 in range(0, host_A.shape[0], rows):
                     d.m[r0:r0 + rows].copy_(host_A[r0:r0 + rows], non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                    inflight.append(ev)
+                    if len(inflight) > 2:
+                        inflight.pop(0).synchronize()
                 for d_, h_ in zip((d.qg2, d.e_v, d.e_c), host_small):
                     d_.copy_(h_, non_blocking=True)
-            c1.record(copy_stream)
-            ready[i % 2].record(copy_stream)
+                c1.record(copy_stream)
+                ready[i % 2].record(copy_stream)
             h2d_ev.append((c0, c1))
 
         def run_e2e(n, after=None):
@@ -396,9 +404,13 @@ def main():
             ecs_e = []
             for i in range(n):
                 stream.wait_event(ready[i % 2])
+                t = None
                 if i + 1 < n:
-                    stage(i + 1)
+                    t = threading.Thread(target=stage, args=(i + 1,))
+                    t.start()
                 ecs_e.append(plan_e.run(i % 2))  # returns E_c to the host (8 bytes)
+                if t is not None:
+                    t.join()
             return ecs_e
 
         run_e2e(2)
