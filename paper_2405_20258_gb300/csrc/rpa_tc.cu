@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -50,8 +51,15 @@ constexpr int BK = 64;   // K elements per tile: 128 bytes of BF16, one 128B swi
 // accumulators of 128 columns fit in TMEM (S <= 4), else 64.
 constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA), in groups of G slots
 constexpr int MAX_NB = 3;   // B buffers (runtime, <= MAX_NB)
-size_t g_smem_limit = 0;    // dynamic shared memory a CTA of the GEMM may use (set at first use)
-int g_num_sms = 0;          // streaming multiprocessors of the device (set at first use)
+// Per-device launch limits of the GEMM, set up once per device (the dynamic
+// shared-memory attribute of a kernel is a per-device setting).
+struct DeviceLimits {
+  size_t smem = 0;  // dynamic shared memory a CTA of the GEMM may use
+  int sms = 0;      // streaming multiprocessors
+};
+constexpr int kMaxDevices = 64;
+DeviceLimits g_limits[kMaxDevices];
+std::mutex g_limits_mutex;
 // producer warp, MMA warp, and 4 x BN/32 epilogue warps (4 lane quadrants x
 // BN/32 column blocks of 32 accumulator columns)
 template <int BN>
@@ -990,7 +998,7 @@ int pick_bn(int S, int Le) {
 
 // Pipeline shape for S slices: the deepest A ring and B buffering that fit in
 // shared memory (up to the knobs), two TMEM accumulator sets when they fit.
-void gemm_shape(int S, int Le, int* na, int* nb, int* nacc) {
+void gemm_shape(int S, int Le, size_t smem_limit, int* na, int* nb, int* nacc) {
   const int BN = pick_bn(S, Le), NL = n_levels(S, Le);
   const size_t B_TILE = (size_t)BN * BK * 2;
   const int want_na = std::min(MAX_NA, std::max(2, env_int("RPA_TC_NA", MAX_NA)));
@@ -999,7 +1007,7 @@ void gemm_shape(int S, int Le, int* na, int* nb, int* nacc) {
   *nacc = (want_acc == 2 && BN == 64 && 2 * NL * BN <= 512) ? 2 : 1;  // BN 128: one set
   for (int b = want_nb; b >= 2; --b)
     for (int a = want_na; a >= 2; --a)
-      if (1024 + (size_t)a * A_TILE + (size_t)b * S * B_TILE <= g_smem_limit) {
+      if (1024 + (size_t)a * A_TILE + (size_t)b * S * B_TILE <= smem_limit) {
         *na = a;
         *nb = b;
         return;
@@ -1008,9 +1016,9 @@ void gemm_shape(int S, int Le, int* na, int* nb, int* nacc) {
   *nb = 2;
 }
 
-size_t gemm_smem(int S, int Le) {
+size_t gemm_smem(int S, int Le, size_t smem_limit) {
   int na, nb, nacc;
-  gemm_shape(S, Le, &na, &nb, &nacc);
+  gemm_shape(S, Le, smem_limit, &na, &nb, &nacc);
   return 1024 + (size_t)na * A_TILE + (size_t)nb * S * ((size_t)pick_bn(S, Le) * BK * 2);
 }
 
@@ -1094,12 +1102,18 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   a.work = w.work + at;
   a.status = w.status;
   a.stall = w.debug_stall;
-  if (!g_smem_limit) {
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    err = std::string("slice GEMM: no usable current device: ") + cudaGetErrorString(e);
+    return RPA_ECUDA;
+  }
+  std::unique_lock<std::mutex> lock(g_limits_mutex);
+  DeviceLimits& lim_dev = g_limits[dev];
+  if (!lim_dev.smem) {
     // opt-in shared memory per block minus the kernels' static shared memory
-    int dev = 0, optin = 0;
+    int optin = 0, sms = 0;
     cudaFuncAttributes fa64{}, fa128{};
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
             cudaSuccess ||
         (e = cudaFuncGetAttributes(&fa64, slice_gemm_kernel<64>)) != cudaSuccess ||
         (e = cudaFuncGetAttributes(&fa128, slice_gemm_kernel<128>)) != cudaSuccess) {
@@ -1116,16 +1130,18 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
       err = std::string("cudaFuncSetAttribute(max dynamic smem): ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
-    g_smem_limit = lim;
-    if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
-        cudaSuccess) {
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
       err = std::string("querying the SM count: ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
+    lim_dev.sms = sms;
+    lim_dev.smem = lim;
   }
-  gemm_shape(a.S, a.nexact, &a.na, &a.nb, &a.nacc);
-  const size_t smem = gemm_smem(a.S, a.nexact);
-  if (smem > g_smem_limit) {
+  const DeviceLimits limits = lim_dev;
+  lock.unlock();
+  gemm_shape(a.S, a.nexact, limits.smem, &a.na, &a.nb, &a.nacc);
+  const size_t smem = gemm_smem(a.S, a.nexact, limits.smem);
+  if (smem > limits.smem) {
     err = "slice GEMM: shared memory of the pipeline exceeds the device limit";
     return RPA_EINVAL;
   }
@@ -1133,7 +1149,7 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   // grid-th tile of the rasterised list, so a tile's epilogue overlaps the next tile's MMAs
   a.n_work = (int)work.size();
   const unsigned grid = (unsigned)std::min<long>(
-      a.n_work, std::max(1, env_int("RPA_TC_GRID", g_num_sms > 0 ? g_num_sms : a.n_work)));
+      a.n_work, std::max(1, env_int("RPA_TC_GRID", limits.sms > 0 ? limits.sms : a.n_work)));
   if (BN == 128)
     slice_gemm_kernel<128><<<grid, threads_for<128>(), smem, st>>>(ta, tb, a);
   else
