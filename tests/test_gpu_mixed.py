@@ -124,3 +124,26 @@ def test_gemm_variants_agree(env, monkeypatch):
     got = run_gpu(qp, A, 40, 6, precision=1, slices=(5, 6, 4))
     assert rel_fro(got["chit"], base["chit"]) < 1e-10
     assert abs(got["ec"] - base["ec"]) < 1e-10 * abs(base["ec"])
+
+
+def test_interleaved_stages_of_two_qpoints():
+    """Stages of two q-points interleaved in one plan (the projection planes cut
+    during one q-point's eigensolve are overwritten by the other's) give the
+    energies of the two q-points run one after the other."""
+    import torch
+    from paper_2405_20258_gb300 import rpa
+    qa = inputs.make_qpoint(160, 3, 40, iq=0)
+    qb = inputs.make_qpoint(130, 4, 30, iq=1, seed=inputs.DEFAULT_SEED + 7)
+    dqs = [rpa.device_qpoint(q, 30, 6, A=inputs.matrix_elements(q)) for q in (qa, qb)]
+    with rpa.Plan(dqs, precision=rpa.RPA_MIXED) as p:
+        seq = [p.run(0), p.run(1)]
+        p.chi0_static(0)
+        p.chi0_static(1)
+        p.subspace_basis(0)
+        p.subspace_basis(1)
+        p.chi_freq(1)
+        p.chi_freq(0)
+        mixed = [p.ecorr(0), p.ecorr(1)]
+        torch.cuda.synchronize()
+    for a, b in zip(seq, mixed):
+        assert abs(a - b) <= 1e-12 * abs(a), (seq, mixed)
