@@ -228,6 +228,41 @@ def gpu_local_cpus(index):
         return None
 
 
+# Small cases for ncu captures of one kernel (a few GB on the device, inputs above L2):
+#   chi0: the chi~(0) GEMM of a 4000-plane-wave q-point with 16,000 transitions (run with
+#         RPA_TC_CHI0_BLOCKS=1 for one K-block of K = 32,000); chi0_static three times.
+#   chis: the chi_s stage of a 1000-plane-wave q-point with 32,000 transitions, N_eig 400
+#         and 4 frequencies; the whole chain twice.
+PROFILE_CASES = {
+    "chi0": dict(n_g=4000, n_v=16, n_c=1000, n_eig=400, n_freq=8),
+    "chis": dict(n_g=1000, n_v=16, n_c=2000, n_eig=400, n_freq=4),
+}
+
+
+def profile_case(name, slices):
+    import torch
+    from paper_2405_20258_gb300 import inputs, rpa
+    w = PROFILE_CASES[name]
+    qp = inputs.make_qpoint(w["n_g"], w["n_v"], w["n_c"])
+    dq = rpa.device_qpoint(qp, w["n_eig"], w["n_freq"])
+    A = torch.empty((w["n_v"] * w["n_c"], w["n_g"]), dtype=torch.complex128, device="cuda")
+    rpa.rpa_generate_m(dq, 0, w["n_v"], 0, w["n_c"], A)
+    torch.cuda.synchronize()
+    dq.m = A
+    sl = tuple(int(x) for x in slices.split(","))
+    with rpa.Plan([dq], precision=rpa.RPA_MIXED, slices=sl, timing=True) as p:
+        reps = 3 if name == "chi0" else 2
+        for _ in range(reps):
+            p.chi0_static(0)
+            if name == "chis":
+                p.subspace_basis(0)
+                p.chi_freq(0)
+        torch.cuda.synchronize()
+        st, _ = p.timings()
+    print(json.dumps({"profile": name, "case": w, "reps": reps,
+                      "stage_ms": {k: v / reps for k, v in st.items() if v}}))
+
+
 def run_steps(plan, n):
     return [plan.run(0) for _ in range(n)]
 
@@ -245,7 +280,12 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one stage of a small case three times (for ncu captures) and exit")
     args = ap.parse_args()
+    if args.profile:
+        profile_case(args.profile, args.slices)
+        return
     w = WORKLOADS[args.workload]
     rank, world, local, dist = setup_dist(args)
     if args.impl == "reference":
