@@ -34,8 +34,12 @@
  *    the problem's own sizes.
  *  - Errors are returned, never aborted on.  After RPA_EINVAL or RPA_ESTATE the
  *    plan is unchanged and stays usable.  rpa_last_error() gives a message.
- *  - Stages of one q-point must run in order chi0 -> basis -> freq -> ecorr;
- *    calling a stage early returns RPA_ESTATE.
+ *  - Stages of one q-point must run in order chi0 -> basis -> freq -> ecorr.
+ *    The plan holds one q-point's outputs per stage (chi~, the basis, M~ and
+ *    chi_s): stages of different q-points may interleave as long as each stage
+ *    finds its predecessor's outputs for its own q-point; otherwise (called
+ *    early, or after another q-point's stage replaced them) it returns
+ *    RPA_ESTATE.
  *  - Output pointers marked "may be NULL" are optional copies of intermediates.
  *  - Not thread-safe per plan: one host thread drives one plan at a time.
  */

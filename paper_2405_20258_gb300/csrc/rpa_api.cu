@@ -19,7 +19,6 @@ using rpa::cplx;
 
 namespace {
 
-enum Stage { ST_NONE = 0, ST_CHI0 = 1, ST_BASIS = 2, ST_FREQ = 3 };
 
 thread_local std::string g_create_error;
 
@@ -41,7 +40,11 @@ struct rpa_plan_s {
   cudaStream_t st = nullptr;
   cusolverDnHandle_t sol = nullptr;
   cusolverDnParams_t params = nullptr;
-  std::vector<int> stage;
+  // The plan holds one q-point's intermediates per stage: the q-point whose
+  // scalars (v^1/2, Delta, pair weights), chi~(0), basis (C, B) and chi_s stage
+  // outputs (M~, chi_s, traces) are resident (-1: none).  A stage checks that the
+  // previous stage's outputs are those of its own q-point.
+  int scalars_iq = -1, chi_iq = -1, basis_iq = -1, freq_iq = -1;
   std::string err;
   int max_g = 0, max_eig = 0, max_freq = 0;
   long max_vc = 0;
@@ -300,6 +303,7 @@ rpa_status transition_order(rpa_plan_t p, int iq) {
 
 rpa_status prepare(rpa_plan_t p, int iq) {
   const rpa_qpoint& q = p->q[iq];
+  p->scalars_iq = -1;
   CU(p, cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), p->st));
   {
     StageTimer t(p, RPA_T_OTHER);
@@ -317,7 +321,13 @@ rpa_status prepare(rpa_plan_t p, int iq) {
                 "e_c - e_v, and zero where e_c = e_v",
                 iq);
   if (h & 8) return fail(p, RPA_EINVAL, "q-point %d: slab Coulomb kernel not positive", iq);
+  p->scalars_iq = iq;
   return RPA_OK;
+}
+
+// The per-q-point scalars of iq, recomputed if another q-point's replaced them.
+rpa_status ensure_scalars(rpa_plan_t p, int iq) {
+  return p->scalars_iq == iq ? RPA_OK : prepare(p, iq);
 }
 
 }  // namespace
@@ -369,7 +379,6 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   p->q.assign(q, q + n_q);
   p->opt = o;
   p->st = (cudaStream_t)stream;
-  p->stage.assign(n_q, ST_NONE);
   bool need_gen = false;
   size_t gen_bytes = 0;
   for (int i = 0; i < n_q; ++i) {
@@ -541,6 +550,7 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   rpa_status s = check_iq(p, iq);
   if (s != RPA_OK) return s;
   const rpa_qpoint& q = *qp(p, iq);
+  p->chi_iq = -1;
   s = prepare(p, iq);
   if (s != RPA_OK) return s;
   const void* A;
@@ -569,14 +579,18 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   if (chi_out)
     CU(p, cudaMemcpyAsync(chi_out, p->chi, sizeof(cplx) * (size_t)q.n_g * q.n_g,
                           cudaMemcpyDeviceToDevice, p->st));
-  p->stage[iq] = ST_CHI0;
+  p->chi_iq = iq;
   return RPA_OK;
 }
 
 rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_out) {
   rpa_status s = check_iq(p, iq);
   if (s != RPA_OK) return s;
-  if (p->stage[iq] < ST_CHI0) return fail(p, RPA_ESTATE, "rpa_chi0_static(%d) must come first", iq);
+  if (p->chi_iq != iq)
+    return fail(p, RPA_ESTATE, "rpa_chi0_static(%d) must come first (chi~ held: q-point %d)", iq,
+                p->chi_iq);
+  if ((s = ensure_scalars(p, iq)) != RPA_OK) return s;
+  p->basis_iq = -1;
   const rpa_qpoint& q = *qp(p, iq);
   const int n = q.n_g;
   if (p->opt.precision == RPA_MIXED) {
@@ -619,15 +633,18 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   if (c_out)
     CU(p, cudaMemcpyAsync(c_out, p->C, sizeof(cplx) * (size_t)n * q.n_eig,
                           cudaMemcpyDeviceToDevice, p->st));
-  p->stage[iq] = ST_BASIS;
+  p->basis_iq = iq;
   return RPA_OK;
 }
 
 rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, double* trace_out) {
   rpa_status s = check_iq(p, iq);
   if (s != RPA_OK) return s;
-  if (p->stage[iq] < ST_BASIS)
-    return fail(p, RPA_ESTATE, "rpa_subspace_basis(%d) must come first", iq);
+  if (p->basis_iq != iq)
+    return fail(p, RPA_ESTATE, "rpa_subspace_basis(%d) must come first (basis held: q-point %d)",
+                iq, p->basis_iq);
+  if ((s = ensure_scalars(p, iq)) != RPA_OK) return s;
+  p->freq_iq = -1;
   const rpa_qpoint& q = *qp(p, iq);
   const void* A;
   int dt;
@@ -686,7 +703,7 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   if (trace_out)
     CU(p, cudaMemcpyAsync(trace_out, p->trace, sizeof(double) * F, cudaMemcpyDeviceToDevice,
                           p->st));
-  p->stage[iq] = ST_FREQ;
+  p->freq_iq = iq;
   return RPA_OK;
 }
 
@@ -777,7 +794,9 @@ rpa_status rpa_ecorr(rpa_plan_t p, int iq, double* ec_host, double* lam_out) {
   }
   rpa_status s = check_iq(p, iq);
   if (s != RPA_OK) return s;
-  if (p->stage[iq] < ST_FREQ) return fail(p, RPA_ESTATE, "rpa_chi_freq(%d) must come first", iq);
+  if (p->freq_iq != iq)
+    return fail(p, RPA_ESTATE, "rpa_chi_freq(%d) must come first (chi_s held: q-point %d)", iq,
+                p->freq_iq);
   return energy_one(p, iq, ec_host, lam_out);
 }
 

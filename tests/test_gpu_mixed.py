@@ -127,9 +127,11 @@ def test_gemm_variants_agree(env, monkeypatch):
 
 
 def test_interleaved_stages_of_two_qpoints():
-    """Stages of two q-points interleaved in one plan (the projection planes cut
-    during one q-point's eigensolve are overwritten by the other's) give the
-    energies of the two q-points run one after the other."""
+    """The plan holds one q-point's intermediates per stage.  Interleaving the
+    stages of two q-points gives their one-after-the-other energies while each
+    stage still finds its predecessor's outputs (the projection planes cut during
+    one q-point's eigensolve being replaced by the other's chi~ blocks on the way);
+    a stage whose inputs another q-point has replaced returns RPA_ESTATE."""
     import torch
     from paper_2405_20258_gb300 import rpa
     qa = inputs.make_qpoint(160, 3, 40, iq=0)
@@ -138,12 +140,24 @@ def test_interleaved_stages_of_two_qpoints():
     with rpa.Plan(dqs, precision=rpa.RPA_MIXED) as p:
         seq = [p.run(0), p.run(1)]
         p.chi0_static(0)
-        p.chi0_static(1)
-        p.subspace_basis(0)
+        p.subspace_basis(0)      # cuts q-point 0's projection planes on the side stream
+        p.chi0_static(1)         # chi~ of q-point 1 (its K-blocks replace those planes)
+        p.chi_freq(0)            # q-point 0's basis is still held
+        e0 = p.ecorr(0)
         p.subspace_basis(1)
         p.chi_freq(1)
-        p.chi_freq(0)
-        mixed = [p.ecorr(0), p.ecorr(1)]
+        e1 = p.ecorr(1)
         torch.cuda.synchronize()
-    for a, b in zip(seq, mixed):
-        assert abs(a - b) <= 1e-12 * abs(a), (seq, mixed)
+        for a, b in zip(seq, (e0, e1)):
+            assert abs(a - b) <= 1e-12 * abs(a), (seq, (e0, e1))
+        p.chi0_static(0)
+        p.chi0_static(1)         # replaces q-point 0's chi~
+        with pytest.raises(rpa.RPAError) as e:
+            p.subspace_basis(0)
+        assert e.value.status == rpa.RPA_ESTATE
+        with pytest.raises(rpa.RPAError) as e:
+            p.ecorr(0)           # chi_s held is q-point 1's
+        assert e.value.status == rpa.RPA_ESTATE
+        p.subspace_basis(1)
+        p.chi_freq(1)
+        assert abs(p.ecorr(1) - seq[1]) <= 1e-12 * abs(seq[1])
