@@ -2,7 +2,8 @@
 // digit-sliced BF16 GEMM with TMEM accumulation and a double-float epilogue,
 // plus the HBM-bound kernels that cut FP64 operands into digit planes.
 //
-// GEMM kernel roles (one output tile of 128 x BN per CTA, BN = 64 or 128):
+// GEMM kernel: persistent, one CTA per SM walking every grid-th output tile of
+// 128 x BN (BN = 64 or 128) of a rasterised work list; its roles:
 //   warp 0      TMA producer: per 64-wide K-tile, all S digit planes of the B
 //               tile (double- or triple-buffered) and the S digit planes of the
 //               A tile through a ring of slots in groups of G = min(S, NA/2);
@@ -12,14 +13,16 @@
 //               always cover, so the producer can fill it);
 //   warp 1      TMEM allocation and the single MMA-issuing thread: per A digit
 //               plane s, kind::f16 MMAs (K = 16 each) against the B planes
-//               t = 0 .. S-1-s taken together as one operand of BN (S - s)
-//               rows, whose output columns land in the level accumulators
-//               L = s + t (levels sit BN columns apart in TMEM);
+//               t = 0 .. Le-1-s taken together as one operand of BN (Le - s)
+//               rows, whose output columns land in the exact level accumulators
+//               L = s + t (levels sit BN columns apart in TMEM), and one MMA per
+//               remaining pair (s, t) into the tail accumulator;
 //   BN/8 epilogue warps (4 lane quadrants x BN/32 column blocks): at the end
 //               of each drain interval, read the level accumulators from TMEM
 //               and add them into per-thread double-float accumulators (one
-//               TMEM lane and 32 columns per thread); finally apply the row
-//               scales and write complex FP64 results.
+//               TMEM lane and 32 columns per thread); at the end of a tile apply
+//               the row scales and write complex FP64 results while the MMA
+//               thread already works on the next tile.
 // Digit planes are stored pre-scaled (plane s holds d_s 2^-8s), so level L
 // sums integers times 2^-8L.  Levels L < Le (p.nexact) have accumulators of
 // their own and stay exact (integer sums below 2^24 over a drain interval);
@@ -34,9 +37,9 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "rpa_tc.h"
@@ -47,8 +50,8 @@ namespace {
 
 constexpr int BM = 128;  // A rows per tile = TMEM lanes = MMA M
 constexpr int BK = 64;   // K elements per tile: 128 bytes of BF16, one 128B swizzle row
-// B rows per tile (= MMA N) is a template parameter: 128 when the S level
-// accumulators of 128 columns fit in TMEM (S <= 4), else 64.
+// B rows per tile (= MMA N) is a template parameter: 128 when the level
+// accumulators (at most 3) and the low halves fit in TMEM, else 64 (pick_bn).
 constexpr int MAX_NA = 8;   // A ring depth (runtime, <= MAX_NA), in groups of G slots
 constexpr int MAX_NB = 3;   // B buffers (runtime, <= MAX_NB)
 // Per-device launch limits of the GEMM, set up once per device (the dynamic

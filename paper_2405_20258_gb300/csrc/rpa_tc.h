@@ -4,11 +4,13 @@
 // digit slices: each operand row r is scaled by 2^-e_r (e_r from the row's
 // largest magnitude) and cut into S signed 8-bit integer digits, so
 //   x = 2^(e_r - 7) * sum_s d_s 2^(-8 s),   |d_s| <= 128  (exact in BF16).
-// Digit products are exact, and their FP32 sums over a drain interval of K
-// are exact integers below 2^24; the epilogue folds each interval into a
-// double-float accumulator.  The only approximation is the truncation of the
-// digit expansion and of the product triangle (s + t <= S - 1): about
-// 2^-(7 + 8(S-1)) relative to the row scales.
+// Digit products are exact; the FP32 sums of the leading levels s + t < Le over
+// a drain interval of K are exact (integers below 2^24 times the level weight),
+// the lower levels share one FP32 accumulator, and the epilogue folds each
+// interval into a double-float accumulator.  The approximations are the
+// truncation of the digit expansion and of the product triangle
+// (s + t <= S - 1), about 2^-(7 + 8(S-1)) relative to the row scales, and the
+// rounding of the low-level accumulator below it.
 #pragma once
 
 #include <cuda_runtime.h>
