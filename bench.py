@@ -32,6 +32,9 @@ WORKLOADS = {
     "qpoint-400": dict(n_g=400, n_v=16, n_c=200, n_eig=40, n_freq=16),
     # small case for ncu captures (A is 0.5 GB, larger than L2)
     "qpoint-1024": dict(n_g=1024, n_v=32, n_c=1000, n_eig=128, n_freq=16),
+    # the 4000-plane-wave q-point at the other subspace sizes of the mixed-precision study
+    "qpoint-4000-neig200": dict(n_g=4000, n_v=128, n_c=2000, n_eig=200, n_freq=32),
+    "qpoint-4000-neig800": dict(n_g=4000, n_v=128, n_c=2000, n_eig=800, n_freq=32),
     # the interface-sized q-point with complex64 matrix elements drawn on the device (50 GB)
     "qpoint-12000": dict(n_g=12000, n_v=256, n_c=2048, n_eig=1200, n_freq=48, m_dtype="c64"),
 }
