@@ -67,6 +67,8 @@ struct rpa_plan_s {
   bool batched_eig = false;   // cusolverDnXsyevBatched usable for the chi_s eigenvalues
   int* infos = nullptr;       // [max_freq] solver info of the batched solve
   rpa::tc::Workspace tcw;     // tensor-core path workspace
+  rpa::eig::Refine refine;    // mixed path: FP32 subspace of chi~ refined in FP64
+  bool refine_ready = false;
   // stage timers (CUDA events on the plan stream) and the library's launch count
   struct Pending {
     int id;
@@ -138,6 +140,7 @@ void free_plan(rpa_plan_t p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
+  p->refine.release();
   if (p->sol_host) free(p->sol_host);
   if (p->params) cusolverDnDestroyParams(p->params);
   if (p->sol) cusolverDnDestroy(p->sol);
@@ -510,6 +513,23 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     return fail(nullptr, RPA_ENOMEM, "solver workspace of %zu bytes", dmax);
   }
   p->sol_host = malloc(p->sol_host_bytes);
+  if (o.precision == RPA_MIXED) {
+    int n_max = 0, mp_max = 0;
+    for (int i = 0; i < n_q; ++i)
+      if (rpa::eig::applies(q[i].n_g, q[i].n_eig)) {
+        n_max = std::max(n_max, q[i].n_g);
+        mp_max = std::max(mp_max, q[i].n_eig + rpa::eig::extra_vectors(q[i].n_eig));
+      }
+    if (n_max > 0) {
+      std::string e;
+      rpa_status rs = p->refine.alloc(p->sol, p->params, n_max, mp_max, e);
+      if (rs != RPA_OK) {
+        free_plan(p);
+        return fail(nullptr, rs, "%s", e.c_str());
+      }
+      p->refine_ready = true;
+    }
+  }
   // quadrature of every q-point
   for (int i = 0; i < n_q; ++i) {
     if (rpa::launch_freq_grid(q[i].n_freq, o.omega_scale, p->omega + (size_t)i * F,
@@ -604,27 +624,44 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
     if (s != RPA_OK) return s;
   }
   StageTimer timer(p, RPA_T_EIG0);
-  CU(p, cudaMemcpyAsync(p->chi_work, p->chi, sizeof(cplx) * (size_t)n * n,
-                        cudaMemcpyDeviceToDevice, p->st));
-  double vl = 0.0, vu = 0.0;
-  int64_t meig = 0;
-  CU(p, cudaMemsetAsync(p->flags + 2, 0, sizeof(int), p->st));
-  // The row-major Hermitian chi~ read column-major is conj(chi~): same eigenvalues,
-  // conjugated eigenvectors, undone by the gauge kernel.
-  CS(p, cusolverDnXsyevdx(p->sol, p->params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                          CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, p->chi_work, n, &vl, &vu, 1,
-                          q.n_eig, &meig, CUDA_R_64F, p->lam_all, CUDA_C_64F, p->sol_dev,
-                          p->sol_dev_bytes, p->sol_host, p->sol_host_bytes, p->flags + 2));
-  int info = 0;
-  CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
-  if (p->opt.precision == RPA_MIXED &&
-      (s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK)
-    return s;
-  CU(p, cudaStreamSynchronize(p->st));
-  if ((s = tc_status(p)) != RPA_OK) return s;
-  if (info != 0) return fail(p, RPA_EEIG, "Xsyevdx info = %d", info);
-  if (meig != q.n_eig) return fail(p, RPA_EEIG, "Xsyevdx returned %lld of %d eigenpairs",
-                                   (long long)meig, q.n_eig);
+  bool refined = false;
+  if (p->opt.precision == RPA_MIXED && p->refine_ready && rpa::eig::applies(n, q.n_eig)) {
+    // FP32 solve refined by a filtered Rayleigh-Ritz step in FP64 (rpa_eig.cu);
+    // the eigenvectors land where the FP64 solver leaves them, for the gauge kernel
+    int nl = 0;
+    s = p->refine.subspace(p->sol, p->params, p->chi, n, q.n_eig, p->lam_all, p->chi_work, p->st,
+                           p->err, &nl);
+    p->launches += nl;
+    if (s != RPA_OK && s != RPA_ENUMERIC) return s;
+    refined = s == RPA_OK;  // RPA_ENUMERIC: no spectral interval to filter, use FP64
+  }
+  if (refined) {
+    if ((s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK) return s;
+    CU(p, cudaStreamSynchronize(p->st));
+    if ((s = tc_status(p)) != RPA_OK) return s;
+  } else {
+    CU(p, cudaMemcpyAsync(p->chi_work, p->chi, sizeof(cplx) * (size_t)n * n,
+                          cudaMemcpyDeviceToDevice, p->st));
+    double vl = 0.0, vu = 0.0;
+    int64_t meig = 0;
+    CU(p, cudaMemsetAsync(p->flags + 2, 0, sizeof(int), p->st));
+    // The row-major Hermitian chi~ read column-major is conj(chi~): same eigenvalues,
+    // conjugated eigenvectors, undone by the gauge kernel.
+    CS(p, cusolverDnXsyevdx(p->sol, p->params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                            CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, p->chi_work, n, &vl, &vu, 1,
+                            q.n_eig, &meig, CUDA_R_64F, p->lam_all, CUDA_C_64F, p->sol_dev,
+                            p->sol_dev_bytes, p->sol_host, p->sol_host_bytes, p->flags + 2));
+    int info = 0;
+    CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    if (p->opt.precision == RPA_MIXED &&
+        (s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK)
+      return s;
+    CU(p, cudaStreamSynchronize(p->st));
+    if ((s = tc_status(p)) != RPA_OK) return s;
+    if (info != 0) return fail(p, RPA_EEIG, "Xsyevdx info = %d", info);
+    if (meig != q.n_eig) return fail(p, RPA_EEIG, "Xsyevdx returned %lld of %d eigenpairs",
+                                     (long long)meig, q.n_eig);
+  }
   CU(p, rpa::launch_gauge(p->chi_work, n, n, q.n_eig, p->sv, p->C, p->B, p->st));
   p->launches += 1;
   if (lambda_out)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/rpa.h"
 
 namespace rpa {
@@ -19,6 +21,39 @@ struct cplx {
 inline long n_transitions(const rpa_qpoint& q) {
   return (long)(q.n_k > 1 ? q.n_k : 1) * q.n_v * q.n_c;
 }
+
+// ---- mixed-precision subspace of chi~(0) (rpa_eig.cu) ---------------------
+
+namespace eig {
+// Extra vectors carried beyond N_eig through the FP32 solve and the FP64 step.
+int extra_vectors(int n_eig);
+// Whether the mixed path takes the subspace this way (opt-in with RPA_EIG_MIXED=1;
+// N_G >= 1024 and room for the extra vectors).
+bool applies(int n, int n_eig);
+struct Refine {
+  void* blas = nullptr;               // cublasHandle_t
+  float2* h32 = nullptr;              // chi~ / max|chi~| in complex64, n x n
+  float* w32 = nullptr;               // FP32 eigenvalues
+  cplx *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;  // n x m' blocks (column-major)
+  cplx* tau = nullptr;                // Householder scalars
+  cplx* g = nullptr;                  // m' x m' Rayleigh quotient
+  double* theta = nullptr;            // its eigenvalues
+  unsigned long long* absmax = nullptr;
+  int* info = nullptr;
+  void* dwork = nullptr;
+  size_t dbytes = 0;
+  void* hwork = nullptr;
+  size_t hbytes = 0;
+  int max_n = 0, max_mp = 0;
+  rpa_status alloc(void* sol, void* params, int n_max, int mp_max, std::string& err);
+  void release();
+  // lam_out[0 .. n_eig) and the column-major n x n_eig vec_out: the N_eig most
+  // negative eigenpairs of the column-major view hc (n x n, Hermitian, not modified).
+  rpa_status subspace(void* sol, void* params, const cplx* hc, int n, int n_eig,
+                      double* lam_out, cplx* vec_out, cudaStream_t st, std::string& err,
+                      int* launches);
+};
+}  // namespace eig
 
 // ---- FP64 SIMT contractions (rpa_fp64.cu) ---------------------------------
 
