@@ -66,3 +66,20 @@ def test_batched_workload_ranges():
     assert len(w) == 64
     assert all(1500 <= x["n_g"] <= 6000 and 800 <= x["n_c"] <= 2400 for x in w)
     assert len({x["q_twentieths"] for x in w}) == 64
+
+
+def test_qg_vectors_match_qg2_and_grid_offsets():
+    qp = inputs.make_qpoint(120, 2, 5, q_twentieths=(6, 5, 0))
+    v = inputs.qg_vectors(qp)
+    assert np.allclose(np.sum(v ** 2, axis=1), qp.qg2, rtol=1e-14, atol=0)
+    grid = inputs.qgrid_4x4x4()
+    assert len(grid) == 64 and len(set(grid)) == 64
+    # every q of the grid keeps q + G away from zero (the 0.05 offset along x)
+    assert all(t[0] % 5 == 1 for t in grid)
+
+
+def test_fermi_occupations_bounds_and_monotone():
+    e = np.linspace(-1.0, 1.0, 101)
+    f = inputs.fermi_occupations(e, 0.0, 0.05)
+    assert np.all((f >= 0) & (f <= 1)) and np.all(np.diff(f) <= 0)
+    assert abs(f[50] - 0.5) < 1e-15 and f[0] > 1 - 1e-8 and f[-1] < 1e-8
