@@ -2,18 +2,25 @@
 // chi~(0) with the most negative eigenvalues).
 //
 // GB300's FP64 rate makes a dense FP64 eigensolve of chi~ the largest part of a
-// q-point, while an FP32 one costs about a tenth.  FP32 alone is not enough: the
-// spectrum of chi~ is graded (the cut eigenvalue is ~1e-5 of the largest and the
-// gap at the cut ~1e-8 of it, below FP32's resolution), so FP32 eigenvectors near
-// the cut mix with their neighbours.  The subspace is therefore taken from FP32
-// and made FP64-accurate by one filtered subspace step in FP64:
-//   1. the m' = N_eig + p most negative eigenpairs of chi~ / max|chi~| in FP32
-//      (cuSOLVER range solve; p extra vectors absorb the mixing at the cut);
-//   2. a degree-3 Chebyshev polynomial of chi~ that damps the interval of the
+// q-point.  Its O(n^3) part, the Householder reduction to a real tridiagonal T, is
+// done here in FP32; everything after it in FP64:
+//   1. chi~ / max|chi~| in complex64, reduced to T = Q^H (chi~/max) Q (cuSOLVER
+//      FP32 hetrd).  The reduction keeps the graded structure of chi~ (the cut
+//      eigenvalue is ~1e-5 of the largest), so the m' = N_eig + p eigenvectors of T
+//      back-transformed by Q span chi~'s leading subspace to ~1e-5 -- provided T's
+//      own eigenpairs are FP64: an FP32 solve of T resolves eigenvalues only to
+//      ~1e-7 of the largest, which near the cut mixes the subspace to ~0.1;
+//   2. the m' + 1 most negative eigenvalues of T by Sturm bisection and their
+//      eigenvectors by inverse iteration, in FP64 (rpa_tridiag.h), one thread per
+//      eigenvalue or cluster; Q applied to them in FP32 (cuSOLVER unmtr);
+//   3. a degree-3 Chebyshev polynomial of chi~ that damps the interval of the
 //      unwanted eigenvalues [lambda_{m'+1}, 0] (scaled at lambda_1, after Zhou and
 //      Saad 2007), applied to those m' vectors with FP64 products;
-//   3. an orthonormal basis (Householder QR) and a Rayleigh-Ritz step in FP64:
+//   4. an orthonormal basis (Householder QR) and a Rayleigh-Ritz step in FP64:
 //      the eigenpairs of Q^H chi~ Q give the N_eig Ritz vectors and values.
+// p = max(32, N_eig/4) extra vectors keep the unwanted eigenvalues that the filter
+// must damp at |lambda| <= ~0.55 |lambda_{N_eig}| on these spectra, so one step
+// gains ~200x.
 // The matrix is used as the column-major view of the row-major chi~ buffer, i.e.
 // conj(chi~): same eigenvalues, conjugated eigenvectors (undone by the gauge
 // kernel, as for the FP64 solver).
@@ -29,6 +36,7 @@
 #include <vector>
 
 #include "rpa_internal.h"
+#include "rpa_tridiag.h"
 
 namespace rpa {
 namespace eig {
@@ -66,6 +74,61 @@ __global__ void to_c128_kernel(const float2* v32, long n, int cols, cplx* x) {
     x[i] = cplx{(double)v32[i].x, (double)v32[i].y};
 }
 
+// T in FP64 (an exact promotion of the FP32 reduction) and its squared off-diagonal
+__global__ void promote_tri_kernel(const float* d32, const float* e32, int n, double* d,
+                                   double* e, double* e2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    d[i] = (double)d32[i];
+    if (i + 1 < n) {
+      const double x = (double)e32[i];
+      e[i] = x;
+      e2[i] = x * x;
+    }
+  }
+}
+
+// w[j] for j < k: eigenvalue j (ascending) of T by Sturm bisection, a thread each
+__global__ void bisect_kernel(const double* d, const double* e, const double* e2, int n, int k,
+                              double* w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double lo, hi, pivmin;
+  tri::bounds(d, e, n, &lo, &hi, &pivmin);
+  const double abstol = 1e-8 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
+  w[j] = tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
+}
+
+// Eigenvectors of T for the clusters c < nc of w (cluster c = w[first[c] ..
+// first[c+1])), a thread each; z is n x ldz row-major; lanes holds 6 n nc doubles,
+// element i of a thread's lane q at q n nc + i nc + c.
+__global__ void invit_kernel(const double* d, const double* e, int n, const double* w,
+                             const int* first, int nc, double* z, int ldz, double* lanes) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double lo, hi, pivmin;
+  tri::bounds(d, e, n, &lo, &hi, &pivmin);
+  const double tiny = DBL_EPSILON * fmax(fabs(lo), fabs(hi));
+  const long plane = (long)n * nc;
+  double* b = lanes + c;
+  tri::cluster_vectors(d, e, n, w, first[c], first[c + 1], tiny, z, ldz,
+                       tri::Lane{b, nc}, tri::Lane{b + plane, nc}, tri::Lane{b + 2 * plane, nc},
+                       tri::Lane{b + 3 * plane, nc}, tri::Lane{b + 4 * plane, nc},
+                       tri::Lane{b + 5 * plane, nc});
+}
+
+// c[i + n j] = z[i k + j] as complex64 (column-major n x k from row-major FP64)
+__global__ void z_to_c64_kernel(const double* z, int n, int k, float2* c) {
+  const long tot = (long)n * k;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < tot;
+       o += (long)gridDim.x * blockDim.x) {
+    const long i = o % n, j = o / n;
+    c[o] = make_float2((float)z[i * k + j], 0.f);
+  }
+}
+
+// widest cluster of T's eigenvalues re-orthogonalised by one thread
+constexpr int kMaxCluster = 64;
+
 int grid_for(long n, int block) { return (int)std::min<long>((n + block - 1) / block, 4096); }
 
 cuDoubleComplex z(double re, double im = 0.0) { return make_cuDoubleComplex(re, im); }
@@ -75,8 +138,8 @@ cuDoubleComplex z(double re, double im = 0.0) { return make_cuDoubleComplex(re, 
 int extra_vectors(int n_eig) { return std::max(32, n_eig / 4); }
 
 bool applies(int n, int n_eig) {
-  // opt-in (RPA_EIG_MIXED=1) until it passes the subspace-size parity cases: one
-  // filtered step left |dE_c| = 4.9e-4 Ha at N_G = 4000, N_eig = 200
+  // opt-in (RPA_EIG_MIXED=1) until it passes the subspace-size parity cases on the
+  // device (its tridiagonal solver is tested on the host against LAPACK)
   const char* e = getenv("RPA_EIG_MIXED");
   if (!e || e[0] != '1') return false;
   return n >= 1024 && n_eig + extra_vectors(n_eig) + 1 < n;
@@ -103,29 +166,41 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
     return true;
   };
   const size_t n = (size_t)n_max, mp = (size_t)mp_max;
-  if (!al((void**)&h32, n * n * sizeof(float2)) || !al((void**)&w32, (n + 1) * sizeof(float)) ||
+  if (!al((void**)&h32, n * n * sizeof(float2)) || !al((void**)&d32, n * sizeof(float)) ||
+      !al((void**)&e32, n * sizeof(float)) || !al((void**)&tau32, n * sizeof(float2)) ||
+      !al((void**)&d64, n * sizeof(double)) || !al((void**)&e64, n * sizeof(double)) ||
+      !al((void**)&e2, n * sizeof(double)) || !al((void**)&wt, (mp + 1) * sizeof(double)) ||
+      !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
+      !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
+      !al((void**)&c32, n * mp * sizeof(float2)) ||
       !al((void**)&x0, n * mp * sizeof(cplx)) || !al((void**)&x1, n * mp * sizeof(cplx)) ||
       !al((void**)&x2, n * mp * sizeof(cplx)) || !al((void**)&tau, mp * sizeof(cplx)) ||
       !al((void**)&g, mp * mp * sizeof(cplx)) || !al((void**)&theta, mp * sizeof(double)) ||
-      !al((void**)&absmax, sizeof(unsigned long long)) || !al((void**)&info, sizeof(int))) {
+      !al((void**)&absmax, sizeof(unsigned long long)) || !al((void**)&info, 4 * sizeof(int))) {
     release();
     return RPA_ENOMEM;
   }
-  // solver workspace for the largest shapes (the FP32 range solve, QR, and Q^H chi~ Q)
+  // solver workspace for the largest shapes (the FP32 reduction and back-transform,
+  // QR, and Q^H chi~ Q)
   size_t db = 0, hb = 0, d1 = 0, h1 = 0;
-  float vl = 0, vu = 0;
-  int64_t meig = 0;
   int lw = 0;
-  if (cusolverDnXsyevdx_bufferSize(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                   CUBLAS_FILL_MODE_LOWER, n_max, CUDA_C_32F, h32, n_max, &vl,
-                                   &vu, 1, mp_max + 1, &meig, CUDA_R_32F, w32, CUDA_C_32F, &d1,
-                                   &h1) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnXsyevdx_bufferSize (FP32) failed";
+  if (cusolverDnChetrd_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, n_max, (const cuComplex*)h32,
+                                  n_max, d32, e32, (const cuComplex*)tau32,
+                                  &lw) != CUSOLVER_STATUS_SUCCESS) {
+    err = "cusolverDnChetrd_bufferSize failed";
     release();
     return RPA_EEIG;
   }
-  db = std::max(db, d1);
-  hb = std::max(hb, h1);
+  db = std::max(db, (size_t)lw * sizeof(cuComplex));
+  if (cusolverDnCunmtr_bufferSize(sol, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                                  n_max, mp_max, (const cuComplex*)h32, n_max,
+                                  (const cuComplex*)tau32, (const cuComplex*)c32, n_max,
+                                  &lw) != CUSOLVER_STATUS_SUCCESS) {
+    err = "cusolverDnCunmtr_bufferSize failed";
+    release();
+    return RPA_EEIG;
+  }
+  db = std::max(db, (size_t)lw * sizeof(cuComplex));
   if (cusolverDnXgeqrf_bufferSize(sol, params, n_max, mp_max, CUDA_C_64F, x1, n_max, CUDA_C_64F,
                                   tau, CUDA_C_64F, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
     err = "cusolverDnXgeqrf_bufferSize failed";
@@ -161,7 +236,8 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
 }
 
 void Refine::release() {
-  void* b[] = {h32, w32, x0, x1, x2, tau, g, theta, absmax, info, dwork};
+  void* b[] = {h32, d32, e32, tau32, d64, e64, e2, wt, first, zt, lanes, c32,
+               x0, x1, x2, tau, g, theta, absmax, info, dwork};
   for (void* p : b)
     if (p) cudaFree(p);
   if (hwork) free(hwork);
@@ -207,41 +283,66 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   }
   const long n2 = (long)n * n;
   CB_E(cublasSetStream(bh, st));
-  // 1. FP32 range solve of chi~ / max|chi~|
+  // 1. chi~ / max|chi~| in complex64, reduced to a real tridiagonal T in FP32
   CU_E(cudaMemsetAsync(absmax, 0, sizeof(unsigned long long), st));
   absmax_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax);
   CU_E(cudaGetLastError());
   to_c64_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax, h32);
   CU_E(cudaGetLastError());
-  float vl = 0.f, vu = 0.f;
-  int64_t meig = 0;
-  CU_E(cudaMemsetAsync(info, 0, sizeof(int), st));
-  CS_E(cusolverDnXsyevdx(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                         CUBLAS_FILL_MODE_LOWER, n, CUDA_C_32F, h32, n, &vl, &vu, 1, mp + 1,
-                         &meig, CUDA_R_32F, w32, CUDA_C_32F, dwork, dbytes, hwork, hbytes,
-                         info));
-  std::vector<float> w(mp + 1);
+  CU_E(cudaMemsetAsync(info, 0, 4 * sizeof(int), st));
+  const int lwc = (int)std::min<size_t>(dbytes / sizeof(cuComplex), (size_t)0x7fffffff);
+  CS_E(cusolverDnChetrd(sol, CUBLAS_FILL_MODE_LOWER, n, (cuComplex*)h32, n, d32, e32,
+                        (cuComplex*)tau32, (cuComplex*)dwork, lwc, info + 1));
+  // 2. the m' + 1 most negative eigenvalues of T in FP64
+  promote_tri_kernel<<<grid_for(n, 256), 256, 0, st>>>(d32, e32, n, d64, e64, e2);
+  CU_E(cudaGetLastError());
+  bisect_kernel<<<(mp + 1 + 31) / 32, 32, 0, st>>>(d64, e64, e2, n, mp + 1, wt);
+  CU_E(cudaGetLastError());
+  std::vector<double> w(mp + 1);
   unsigned long long mx_bits = 0;
   int inf = 0;
-  CU_E(cudaMemcpyAsync(w.data(), w32, (mp + 1) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CU_E(cudaMemcpyAsync(w.data(), wt, (mp + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU_E(cudaMemcpyAsync(&mx_bits, absmax, sizeof mx_bits, cudaMemcpyDeviceToHost, st));
-  CU_E(cudaMemcpyAsync(&inf, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU_E(cudaMemcpyAsync(&inf, info + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_E(cudaStreamSynchronize(st));
-  if (inf != 0 || meig != mp + 1) {
-    err = "mixed eigensolver: FP32 range solve info " + std::to_string(inf) + ", " +
-          std::to_string((long long)meig) + " pairs";
+  if (inf != 0) {
+    err = "mixed eigensolver: FP32 tridiagonal reduction info " + std::to_string(inf);
     return RPA_EEIG;
   }
   double mx = 0.0;
   memcpy(&mx, &mx_bits, sizeof mx);
   if (!(mx > 0.0)) mx = 1.0;
-  to_c128_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(h32, n, mp, x0);
+  // 3. T's eigenvectors for the first m' (inverse iteration, re-orthogonalised within
+  //    clusters of eigenvalues closer than 1e-10 of the largest), then Q applied
+  const double tnorm = std::max(std::fabs(w[0]), std::fabs(w[mp]));
+  if (!(tnorm > 0.0) || !std::isfinite(tnorm)) {
+    err = "mixed eigensolver: degenerate tridiagonal spectrum";
+    return RPA_ENUMERIC;
+  }
+  std::vector<int> fh(mp + 1);
+  const int nc = tri::clusters(w.data(), mp, 1e-10 * tnorm, fh.data());
+  int widest = 0;
+  for (int c = 0; c < nc; ++c) widest = std::max(widest, fh[c + 1] - fh[c]);
+  if (widest > kMaxCluster) {
+    // one thread would re-orthogonalise the whole cluster: the FP64 solver is faster
+    err = "mixed eigensolver: a cluster of " + std::to_string(widest) + " eigenvalues";
+    return RPA_ENUMERIC;
+  }
+  CU_E(cudaMemcpyAsync(first, fh.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  invit_kernel<<<(nc + 31) / 32, 32, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
   CU_E(cudaGetLastError());
-  if (launches) *launches += 3;
+  z_to_c64_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, c32);
+  CU_E(cudaGetLastError());
+  CS_E(cusolverDnCunmtr(sol, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, n, mp,
+                        (cuComplex*)h32, n, (cuComplex*)tau32, (cuComplex*)c32, n,
+                        (cuComplex*)dwork, lwc, info + 2));
+  to_c128_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(c32, n, mp, x0);
+  CU_E(cudaGetLastError());
+  if (launches) *launches += 7;
 
-  // 2. Chebyshev filter of degree 3 damping [a, b] = [lambda_{m'+1}, 0], scaled at
-  //    lambda_1 (FP32 estimates, FP64 products)
-  const double a = (double)w[mp] * mx, b = 0.0, lo = (double)w[0] * mx;
+  // 4. Chebyshev filter of degree 3 damping [a, b] = [lambda_{m'+1}, 0], scaled at
+  //    lambda_1 (the eigenvalues of T, FP64 products)
+  const double a = w[mp] * mx, b = 0.0, lo = w[0] * mx;
   if (!(a < 0.0) || !(lo < a)) {
     // no unwanted interval to damp (the (m'+1)-th eigenvalue not below zero, or no
     // spread): the caller takes the FP64 solver
@@ -276,8 +377,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
     std::swap(xk, xn);  // X_k <- X_{k+1}; xn now holds the oldest block (free)
     sigma = s1;
   }
-  // 3. orthonormal basis Q of the filtered block (Householder QR, FP64)
-  CU_E(cudaMemsetAsync(info, 0, sizeof(int), st));
+  // 5. orthonormal basis Q of the filtered block (Householder QR, FP64)
   CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F, dwork,
                         dbytes, hwork, hbytes, info));
   CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
@@ -293,10 +393,12 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, n_eig, mp, &one, (const cuDoubleComplex*)xk,
                    n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)vec_out, n));
   CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
-  CU_E(cudaMemcpyAsync(&inf, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int infs[3] = {0, 0, 0};
+  CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
   CU_E(cudaStreamSynchronize(st));
-  if (inf != 0) {
-    err = "mixed eigensolver: QR or Rayleigh-Ritz info " + std::to_string(inf);
+  if (infs[0] != 0 || infs[2] != 0) {
+    err = "mixed eigensolver: back-transform info " + std::to_string(infs[2]) +
+          ", QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
     return RPA_EEIG;
   }
   return RPA_OK;

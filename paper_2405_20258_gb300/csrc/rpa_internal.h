@@ -25,15 +25,22 @@ inline long n_transitions(const rpa_qpoint& q) {
 // ---- mixed-precision subspace of chi~(0) (rpa_eig.cu) ---------------------
 
 namespace eig {
-// Extra vectors carried beyond N_eig through the FP32 solve and the FP64 step.
+// Extra vectors carried beyond N_eig through the start and the FP64 step.
 int extra_vectors(int n_eig);
 // Whether the mixed path takes the subspace this way (opt-in with RPA_EIG_MIXED=1;
 // N_G >= 1024 and room for the extra vectors).
 bool applies(int n, int n_eig);
 struct Refine {
   void* blas = nullptr;               // cublasHandle_t
-  float2* h32 = nullptr;              // chi~ / max|chi~| in complex64, n x n
-  float* w32 = nullptr;               // FP32 eigenvalues
+  float2* h32 = nullptr;              // chi~ / max|chi~| in complex64, n x n (then reflectors)
+  float *d32 = nullptr, *e32 = nullptr;  // FP32 tridiagonal T: diagonal, off-diagonal
+  float2* tau32 = nullptr;            // its Householder scalars
+  double *d64 = nullptr, *e64 = nullptr, *e2 = nullptr;  // T in FP64, e^2
+  double* wt = nullptr;               // m' + 1 smallest eigenvalues of T
+  int* first = nullptr;               // cluster starts of those eigenvalues
+  double* zt = nullptr;               // eigenvectors of T, n x m' row-major
+  double* lanes = nullptr;            // inverse-iteration scratch, 6 n x m'
+  float2* c32 = nullptr;              // T's eigenvectors, then chi~'s, n x m' complex64
   cplx *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;  // n x m' blocks (column-major)
   cplx* tau = nullptr;                // Householder scalars
   cplx* g = nullptr;                  // m' x m' Rayleigh quotient

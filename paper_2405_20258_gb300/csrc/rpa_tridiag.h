@@ -1,0 +1,231 @@
+// FP64 eigenpairs of a real symmetric tridiagonal matrix T (diagonal d[0..n-1],
+// off-diagonal e[0..n-2]): the start of the mixed-precision subspace of chi~(0).
+//
+// The FP32 Householder reduction of chi~ to T keeps the graded structure of chi~
+// (large entries first) well enough for an N_eig + p subspace accurate to ~1e-5,
+// but an FP32 solve of T itself resolves eigenvalues only to ~1e-7 of the largest,
+// which near the cut (~1e-5 of the largest) mixes the subspace to ~0.1.  So T's
+// eigenpairs are computed in FP64:
+//   * eigenvalue j (ascending) by bisection on the Sturm count of T - x I (the
+//     number of negative pivots of its LDL^T factorisation, Sylvester's law of
+//     inertia), each eigenvalue independently;
+//   * its eigenvector by inverse iteration with T - lambda_j I factored by
+//     Gaussian elimination with partial pivoting (three iterations from a fixed
+//     pseudo-random start), re-orthogonalised (modified Gram-Schmidt) against the
+//     earlier vectors of its cluster: consecutive eigenvalues closer than
+//     cluster_tol apart, whose inverse-iteration vectors are not reliably
+//     orthogonal by themselves.
+// Every routine here is plain scalar code, compiled both for the device (one
+// thread per eigenvalue or per cluster) and for the host (tests).
+#pragma once
+
+#include <math.h>
+#include <float.h>
+#include <stdint.h>
+
+#ifndef RPA_HD
+#ifdef __CUDACC__
+#define RPA_HD __host__ __device__ __forceinline__
+#else
+#define RPA_HD inline
+#endif
+#endif
+
+namespace rpa {
+namespace tri {
+
+// Gershgorin interval [*lo, *hi] of T and a pivot floor (the smallest magnitude a
+// Sturm pivot may take before it is replaced, to keep the recurrence finite).
+RPA_HD void bounds(const double* d, const double* e, int n, double* lo, double* hi,
+                   double* pivmin) {
+  double l = d[0], h = d[0], emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    l = fmin(l, d[i] - r);
+    h = fmax(h, d[i] + r);
+    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double w = fmax(h - l, DBL_MIN);
+  // widen by a little more than the rounding of the Gershgorin sums
+  *lo = l - 2.0 * DBL_EPSILON * w * n - DBL_MIN;
+  *hi = h + 2.0 * DBL_EPSILON * w * n + DBL_MIN;
+  *pivmin = DBL_MIN * fmax(1.0, emax2);
+}
+
+// Number of eigenvalues of T below x: the negative pivots q_i of T - x I = L D L^T,
+// q_0 = d_0 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}.  A pivot at or below pivmin
+// counts as negative and is clamped to -pivmin (the standard safeguard; the count
+// stays that of a matrix within a few ulps of T).
+RPA_HD int sturm_count(const double* d, const double* e2, int n, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (q <= pivmin) {
+    ++c;
+    q = fmin(q, -pivmin);
+  }
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (q <= pivmin) {
+      ++c;
+      q = fmin(q, -pivmin);
+    }
+  }
+  return c;
+}
+
+// Eigenvalue j (0-based, ascending) of T by bisection of [lo, hi] (the Gershgorin
+// interval), to the larger of 2 ulps of the eigenvalue and abstol.  At most 160
+// halvings: from any finite interval this reaches the tolerance.
+RPA_HD double bisect(const double* d, const double* e2, int n, int j, double lo, double hi,
+                     double pivmin, double abstol) {
+  for (int it = 0; it < 160; ++it) {
+    const double tol = fmax(abstol, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)));
+    if (hi - lo <= tol) break;
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e2, n, mid, pivmin) <= j)
+      lo = mid;  // at most j eigenvalues below mid: lambda_j >= mid
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Cluster starts of the ascending eigenvalues w[0..k-1]: a new cluster begins at j
+// when w[j] - w[j-1] > cluster_tol.  first[c] is the first index of cluster c,
+// first[n_clusters] = k.  Returns the number of clusters.
+inline int clusters(const double* w, int k, double cluster_tol, int* first) {
+  int nc = 0;
+  for (int j = 0; j < k; ++j)
+    if (j == 0 || w[j] - w[j - 1] > cluster_tol) first[nc++] = j;
+  first[nc] = k;
+  return nc;
+}
+
+// Strided view of one thread's scratch: element i lives at p[i * stride], so that
+// the threads of a warp, each at the same i, touch consecutive addresses.
+struct Lane {
+  double* p;
+  long stride;
+  RPA_HD double& operator[](long i) const { return p[i * stride]; }
+};
+
+// Gaussian elimination with partial pivoting of M = T - lambda I.  U (upper, two
+// super-diagonals) in u0 (diagonal), u1, u2; multipliers in l; piv[i] = 1 when
+// rows i and i+1 were exchanged at step i.  Pivots smaller than tiny are replaced
+// by +-tiny, so that the solve stays finite at an exact eigenvalue.
+RPA_HD void lu_factor(const double* d, const double* e, int n, double lambda, double tiny,
+                      Lane u0, Lane u1, Lane u2, Lane l, Lane piv) {
+  // current row k: a at column k, b at column k+1
+  double a = d[0] - lambda, b = n > 1 ? e[0] : 0.0;
+  for (int k = 0; k + 1 < n; ++k) {
+    const double g = e[k];                      // M[k+1][k]
+    const double al = d[k + 1] - lambda;        // M[k+1][k+1]
+    const double be = k + 2 < n ? e[k + 1] : 0.0;  // M[k+1][k+2]
+    if (fabs(a) >= fabs(g)) {
+      if (fabs(a) < tiny) a = a < 0.0 ? -tiny : tiny;
+      const double m = g / a;
+      u0[k] = a;
+      u1[k] = b;
+      u2[k] = 0.0;
+      l[k] = m;
+      piv[k] = 0.0;
+      a = al - m * b;
+      b = be;
+    } else {
+      const double m = a / g;
+      u0[k] = g;
+      u1[k] = al;
+      u2[k] = be;
+      l[k] = m;
+      piv[k] = 1.0;
+      a = b - m * al;
+      b = -m * be;
+    }
+  }
+  if (fabs(a) < tiny) a = a < 0.0 ? -tiny : tiny;
+  u0[n - 1] = a;
+}
+
+// Solve M x = y in place (y becomes x) with the factors of lu_factor.  Returns the
+// factor by which the result was scaled down to stay finite (1 if none).
+RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane y) {
+  for (int k = 0; k + 1 < n; ++k) {
+    if (piv[k] != 0.0) {
+      const double yk = y[k], yk1 = y[k + 1];
+      y[k] = yk1;
+      y[k + 1] = yk - l[k] * yk1;
+    } else {
+      y[k + 1] -= l[k] * y[k];
+    }
+  }
+  double scale = 1.0;
+  const double big = 1e150;
+  for (int k = n - 1; k >= 0; --k) {
+    double s = y[k];
+    if (k + 1 < n) s -= u1[k] * y[k + 1];
+    if (k + 2 < n) s -= u2[k] * y[k + 2];
+    s /= u0[k];
+    if (fabs(s) > big) {
+      // rescale the solved tail (and the rest of the right-hand side) by 1/big
+      for (int i = 0; i < n; ++i) y[i] *= 1.0 / big;
+      s *= 1.0 / big;
+      scale *= 1.0 / big;
+    }
+    y[k] = s;
+  }
+  return scale;
+}
+
+// A fixed pseudo-random start in [-1, 1) for component i of vector j (splitmix64 of
+// the pair; any start with a component along the eigenvector serves).
+RPA_HD double start_component(int j, long i) {
+  uint64_t x = ((uint64_t)(uint32_t)j << 32) ^ (uint64_t)i;
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Eigenvectors of the cluster w[j0..j1-1] by inverse iteration.  Column j of Z is
+// z[i * ldz + j] (row-major, i the row).  The scratch lanes hold n elements each.
+RPA_HD void cluster_vectors(const double* d, const double* e, int n, const double* w, int j0,
+                            int j1, double tiny, double* z, long ldz, Lane u0, Lane u1,
+                            Lane u2, Lane l, Lane piv, Lane y) {
+  for (int j = j0; j < j1; ++j) {
+    lu_factor(d, e, n, w[j], tiny, u0, u1, u2, l, piv);
+    double nrm2 = 0.0;
+    for (long i = 0; i < n; ++i) {
+      y[i] = start_component(j, i);
+      nrm2 += y[i] * y[i];
+    }
+    for (int it = 0; it < 3; ++it) {
+      const double s = 1.0 / sqrt(nrm2);
+      for (long i = 0; i < n; ++i) y[i] *= s;
+      lu_solve(n, u0, u1, u2, l, piv, y);
+      // modified Gram-Schmidt against the cluster's earlier (unit) vectors
+      for (int jj = j0; jj < j; ++jj) {
+        double dot = 0.0;
+        for (long i = 0; i < n; ++i) dot += z[i * ldz + jj] * y[i];
+        for (long i = 0; i < n; ++i) y[i] -= dot * z[i * ldz + jj];
+      }
+      nrm2 = 0.0;
+      for (long i = 0; i < n; ++i) nrm2 += y[i] * y[i];
+      if (!(nrm2 > 0.0)) {
+        // the solve returned nothing outside the earlier vectors: restart from a
+        // different pseudo-random vector
+        nrm2 = 0.0;
+        for (long i = 0; i < n; ++i) {
+          y[i] = start_component(j + 7919 * (it + 1), i);
+          nrm2 += y[i] * y[i];
+        }
+      }
+    }
+    const double s = 1.0 / sqrt(nrm2);
+    for (long i = 0; i < n; ++i) z[i * ldz + j] = y[i] * s;
+  }
+}
+
+}  // namespace tri
+}  // namespace rpa

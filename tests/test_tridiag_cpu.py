@@ -1,0 +1,170 @@
+"""CPU tests of the FP64 tridiagonal eigensolver that starts the mixed-precision
+subspace of chi~(0) (csrc/rpa_tridiag.h, built here for the host through
+tests/tridiag_shim.cpp): eigenvalues by Sturm bisection, eigenvectors by inverse
+iteration with cluster re-orthogonalisation, against LAPACK's FP64 tridiagonal
+solvers; and the FP32-reduction + FP64-tridiagonal start on a small chi~."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2405_20258_gb300", "csrc")
+
+DP = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+IP = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("tri") / "libtri.so")
+    subprocess.run([cxx, "-O2", "-shared", "-fPIC", "-I", CSRC, os.path.join(HERE, "tridiag_shim.cpp"),
+                    "-o", out], check=True)
+    so = ctypes.CDLL(out)
+    so.tri_eigvals.argtypes = [DP, DP, ctypes.c_int, ctypes.c_int, DP]
+    so.tri_clusters.argtypes = [DP, ctypes.c_int, ctypes.c_double, IP]
+    so.tri_vectors.argtypes = [DP, DP, ctypes.c_int, DP, ctypes.c_int, ctypes.c_double, DP]
+    return so
+
+
+def eigvals(lib, d, e, k):
+    w = np.zeros(k)
+    assert lib.tri_eigvals(np.ascontiguousarray(d, float), np.ascontiguousarray(e, float),
+                           len(d), k, w) == 0
+    return w
+
+
+def vectors(lib, d, e, w, tol):
+    n, k = len(d), len(w)
+    z = np.zeros((n, k))
+    lib.tri_vectors(np.ascontiguousarray(d, float), np.ascontiguousarray(e, float), n,
+                    np.ascontiguousarray(w, float), k, tol, z)
+    return z
+
+
+def sin_angle(U, V):
+    """Largest principal-angle sine between the column spans of U and V."""
+    Qu, _ = np.linalg.qr(U)
+    Qv, _ = np.linalg.qr(V)
+    return np.linalg.norm(Qv - Qu @ (Qu.conj().T @ Qv), 2)
+
+
+def test_random_tridiagonal_all_pairs(lib):
+    rng = np.random.default_rng(1)
+    n = 200
+    d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+    ref = sla.eigh_tridiagonal(d, e, eigvals_only=True)
+    w = eigvals(lib, d, e, n)
+    nrm = np.max(np.abs(ref))
+    assert np.max(np.abs(w - ref)) <= 1e-13 * nrm
+    z = vectors(lib, d, e, w, 1e-10 * nrm)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.max(np.abs(z.T @ z - np.eye(n))) < 1e-10
+    assert np.max(np.linalg.norm(T @ z - z * w, axis=0)) < 1e-12 * nrm
+
+
+def test_graded_tridiagonal_smallest_pairs_relative(lib):
+    # a graded negative definite T (entries from 1 down to 1e-8, as chi~ reduces to),
+    # its 60 most negative eigenvalues to high relative accuracy
+    rng = np.random.default_rng(2)
+    n, k = 300, 60
+    g = 10.0 ** (-8.0 * np.arange(n) / n)
+    d = -g * (1.0 + 0.1 * rng.random(n))
+    e = 0.2 * np.sqrt(g[:-1] * g[1:]) * np.sign(rng.standard_normal(n - 1))
+    ref_w, ref_z = sla.eigh_tridiagonal(d, e, select="i", select_range=(0, k - 1),
+                                        lapack_driver="stemr")
+    w = eigvals(lib, d, e, k)
+    assert np.max(np.abs(w - ref_w) / np.abs(ref_w)) < 1e-12
+    z = vectors(lib, d, e, w, 1e-10 * abs(w[0]))
+    assert sin_angle(z, ref_z) < 1e-9
+    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-9
+
+
+def test_tight_cluster_is_reorthogonalised(lib):
+    # two copies of one tridiagonal coupled by 1e-13: eigenvalues in pairs 1e-13 apart
+    rng = np.random.default_rng(3)
+    m = 40
+    d0, e0 = rng.standard_normal(m), rng.standard_normal(m - 1)
+    d = np.concatenate([d0, d0])
+    e = np.concatenate([e0, [1e-13], e0])
+    k = 20
+    w = eigvals(lib, d, e, k)
+    first = np.zeros(k + 1, np.int32)
+    nc = lib.tri_clusters(w, k, 1e-10, first)
+    assert nc == k // 2 and np.all(np.diff(first[:nc + 1]) == 2)
+    z = vectors(lib, d, e, w, 1e-10)
+    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-12
+    ref_w, ref_z = sla.eigh_tridiagonal(d, e, select="i", select_range=(0, k - 1))
+    assert np.max(np.abs(w - ref_w)) < 1e-13 * np.max(np.abs(d))
+    for c in range(nc):
+        j0, j1 = first[c], first[c + 1]
+        assert sin_angle(z[:, j0:j1], ref_z[:, j0:j1]) < 1e-9
+
+
+def test_clusters_split_on_gaps(lib):
+    w = np.array([0.0, 1e-12, 1.0, 2.0, 2.0 + 1e-12, 2.0 + 2e-12])
+    first = np.zeros(len(w) + 1, np.int32)
+    nc = lib.tri_clusters(w, len(w), 1e-10, first)
+    assert nc == 3 and list(first[:4]) == [0, 2, 3, 6]
+
+
+def test_split_matrix_and_size_one(lib):
+    # a zero off-diagonal splits T; n = 1 is its own eigenvalue
+    d = np.array([3.0, -1.0, 2.0, 0.5])
+    e = np.array([0.5, 0.0, 0.25])
+    w = eigvals(lib, d, e, 4)
+    assert np.allclose(w, np.sort(sla.eigh_tridiagonal(d, e, eigvals_only=True)), atol=1e-14)
+    z = vectors(lib, d, e, w, 1e-10)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.max(np.abs(T @ z - z * w)) < 1e-13
+    assert abs(eigvals(lib, [2.5], np.zeros(0), 1)[0] - 2.5) < 1e-15
+
+
+def householder_apply_lower(a, tau, Z):
+    """Q Z for the Q of a lower-triangle Hermitian tridiagonal reduction (reflectors
+    H(i) = I - tau_i v v^H, v[i+1] = 1, v[i+2:] = a[i+2:, i], Q = H(0) ... H(n-2))."""
+    n = a.shape[0]
+    Z = Z.astype(np.complex128)
+    for i in range(n - 2, -1, -1):
+        v = np.empty(n - i - 1, np.complex128)
+        v[0] = 1.0
+        v[1:] = a[i + 2:, i]
+        Z[i + 1:] -= tau[i] * np.outer(v, v.conj() @ Z[i + 1:])
+    return Z
+
+
+def test_fp32_reduction_fp64_tridiagonal_start_on_chi_tilde(lib):
+    # the start of the mixed-precision subspace on a 400-plane-wave chi~: the FP32
+    # reduction with this FP64 tridiagonal solve contains the FP64 subspace as well
+    # as with LAPACK's FP64 tridiagonal solver (an all-FP32 solve is printed beside;
+    # it falls behind on the graded spectra of larger N_G)
+    import oracle.rpa_oracle as orc
+    from paper_2405_20258_gb300 import inputs
+    qp = inputs.make_qpoint(400, 16, 200)
+    A = inputs.matrix_elements(qp)
+    H = orc.chi_tilde(A, qp.qg2, orc.transition_energies(qp.e_v, qp.e_c), 0.0, qp.omega_cell)
+    lam, V = np.linalg.eigh(H)
+    n_eig, k = 40, 72
+    mx = np.max(np.abs(np.concatenate([H.real.ravel(), H.imag.ravel()])))
+    c, d32, e32, tau, info = sla.lapack.chetrd((H / mx).astype(np.complex64), lower=1)
+    assert info == 0
+    d, e = d32.astype(np.float64), e32.astype(np.float64)
+    w = eigvals(lib, d, e, k + 1)
+    z = vectors(lib, d, e, w[:k], 1e-10 * abs(w[0]))
+    ours = sin_angle(householder_apply_lower(c, tau, z), V[:, :n_eig])
+    _, zl = sla.eigh_tridiagonal(d, e, select="i", select_range=(0, k - 1), lapack_driver="stemr")
+    lapack = sin_angle(householder_apply_lower(c, tau, zl), V[:, :n_eig])
+    _, z32 = sla.eigh_tridiagonal(d32, e32, lapack_driver="stev")
+    fp32 = sin_angle(householder_apply_lower(c, tau, z32[:, :k].astype(np.float64)), V[:, :n_eig])
+    assert ours <= 1.5 * lapack + 1e-12, (ours, lapack)
+    assert ours < 1e-3, ours
+    # the eigenvalue bounds the Chebyshev filter uses: T's (k+1)-th eigenvalue
+    assert abs(w[k] * mx - lam[k]) < 1e-4 * abs(lam[0])
+    print("containment: FP64 tridiagonal %.2e, LAPACK %.2e, all FP32 %.2e" % (ours, lapack, fp32))
