@@ -18,9 +18,10 @@
 //      Saad 2007), applied to those m' vectors with FP64 products;
 //   4. an orthonormal basis (Householder QR) and a Rayleigh-Ritz step in FP64:
 //      the eigenpairs of Q^H chi~ Q give the N_eig Ritz vectors and values.
-// p = max(32, N_eig/4) extra vectors keep the unwanted eigenvalues that the filter
-// must damp at |lambda| <= ~0.55 |lambda_{N_eig}| on these spectra, so one step
-// gains ~200x.
+// p = max(64, N_eig/4) extra vectors put the unwanted eigenvalues that the filter
+// must damp well below |lambda_{N_eig}| on these spectra (0.55 of it at N_eig =
+// 400), so one step gains ~10-200x; with p = 32 one step only just reached 1e-6 Ha
+// at N_G = 4000, N_eig = 400.
 // The matrix is used as the column-major view of the row-major chi~ buffer, i.e.
 // conj(chi~): same eigenvalues, conjugated eigenvectors (undone by the gauge
 // kernel, as for the FP64 solver).
@@ -135,7 +136,7 @@ cuDoubleComplex z(double re, double im = 0.0) { return make_cuDoubleComplex(re, 
 
 }  // namespace
 
-int extra_vectors(int n_eig) { return std::max(32, n_eig / 4); }
+int extra_vectors(int n_eig) { return std::max(64, n_eig / 4); }
 
 bool applies(int n, int n_eig) {
   // opt-in (RPA_EIG_MIXED=1) until it passes the subspace-size parity cases on the
