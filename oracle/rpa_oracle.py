@@ -38,8 +38,10 @@ Parity pins (tests/test_oracle_pins.py): Hermitian and negative semidefinite
 chi0; closed-form rank-1 energy; full-basis equivalence against an LU
 log-determinant of the full matrix; chi_s(0) = diag(lambda); Sylvester
 log-determinant identity; polynomial exactness of the quadrature; brute-force
-loops on tiny inputs.  The truncation error at N_eig < N_G has no closed form:
-parity unpinned beyond this oracle for that quantity.
+loops on tiny inputs; Cauchy interlacing of chi_s(iw) = C^H chi~(iw) C against
+chi~(iw) at every node, with E_c non-increasing in N_eig towards the full-basis
+value.  Those bound the truncation error at N_eig < N_G, but its size has no
+closed form: parity unpinned beyond this oracle for that quantity.
 """
 from __future__ import annotations
 

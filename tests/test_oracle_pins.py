@@ -202,6 +202,33 @@ def test_energy_negative_and_terms_nonpositive():
     assert np.all(out["e_k"] <= 0)
 
 
+def test_subspace_interlacing_bounds_and_monotone_energy():
+    # chi_s(iw) = C^H chi~(iw) C is a compression of chi~(iw) = v^1/2 chi0(iw) v^1/2
+    # onto orthonormal columns (Method: M_s = M C_s), so Cauchy interlacing holds:
+    # lambda_i <= mu_i <= lambda_{i + N_G - N_eig} (ascending).  f(l) = ln(1-l) + l is
+    # increasing and <= 0 for l <= 0, so every node's term, and E_c, can only rise
+    # (towards 0) when the subspace shrinks, and equal the full-basis value at N_G.
+    # This bounds the truncation error; its size has no closed form.
+    qp, A = tiny_problem(24, 2, 5, seed=17)
+    nf = 6
+    delta = orc.transition_energies(qp.e_v, qp.e_c)
+    prev = None
+    for n_eig in (1, 3, 8, 15, 24):
+        out = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, n_eig, nf, keep=True)
+        for k in range(nf):
+            lam = np.linalg.eigvalsh(orc.chi_tilde(A, qp.qg2, delta, out["omega"][k], qp.omega_cell))
+            mu = np.sort(out["lam_k"][k])
+            tol = 1e-12 * abs(lam).max()
+            assert np.all(mu >= lam[:n_eig] - tol)
+            assert np.all(mu <= lam[qp.n_g - n_eig:] + tol)
+        if prev is not None:
+            assert np.all(out["e_k"] <= prev["e_k"] + 1e-12 * abs(out["e_k"]).max())
+            assert out["ec"] <= prev["ec"] + 1e-12 * abs(out["ec"])
+        prev = out
+    full = orc.ecorr_full_basis(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, nf)
+    assert abs(prev["ec"] - full) < 1e-11 * abs(full)
+
+
 # --- mutation tests: a planted mistake must be caught by the pins -------------
 
 def _run_pins():
@@ -209,6 +236,7 @@ def _run_pins():
     for fn in (test_chi0_bruteforce_loops, test_rank1_eigenvalue_per_node,
                test_full_basis_equivalence_lu, test_chis_static_is_diagonal_lambda,
                test_projection_bruteforce, test_quadrature_integrates_lorentzian,
+               test_subspace_interlacing_bounds_and_monotone_energy,
                lambda: test_quadrature_exact_for_polynomials(8)):
         try:
             fn()
@@ -222,7 +250,7 @@ def test_pins_pass_unmutated():
 
 
 @pytest.mark.parametrize("mutation", ["transpose_chi0", "drop_antiresonant", "wrong_weight_jacobian",
-                                      "project_no_conj", "sign_trace"])
+                                      "project_no_conj", "sign_trace", "chi_s_static_weights"])
 def test_planted_mistake_is_caught(monkeypatch, mutation):
     if mutation == "transpose_chi0":
         orig = orc.chi0
@@ -242,4 +270,9 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
     elif mutation == "sign_trace":
         orig = orc.trace_term
         monkeypatch.setattr(orc, "trace_term", lambda *a, **k: -orig(*a, **k))
+    elif mutation == "chi_s_static_weights":
+        # chi_s(iw_k) built with the omega = 0 weights at every node
+        orig = orc.chi_s
+        monkeypatch.setattr(orc, "chi_s",
+                            lambda Mt, d, o, oc, ow=None: orig(Mt, d, 0.0, oc, ow))
     assert _run_pins() > 0
