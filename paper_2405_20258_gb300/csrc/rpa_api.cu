@@ -67,7 +67,7 @@ struct rpa_plan_s {
   bool batched_eig = false;   // cusolverDnXsyevBatched usable for the chi_s eigenvalues
   int* infos = nullptr;       // [max_freq] solver info of the batched solve
   rpa::tc::Workspace tcw;     // tensor-core path workspace
-  rpa::eig::Refine refine;    // mixed path: FP32 subspace of chi~ refined in FP64
+  rpa::eig::Refine refine;    // opt-in mixed eigensolver of chi~ (rpa_eig.cu)
   bool refine_ready = false;
   // stage timers (CUDA events on the plan stream) and the library's launch count
   struct Pending {
@@ -441,7 +441,13 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     if (o.slices_proj > 0) sl.proj = o.slices_proj;
     if (o.slices_chis > 0) sl.chis = o.slices_chis;
     std::string e;
-    s = rpa::tc::alloc_workspace(p->tcw, G, E, V, F, sl, e);
+    // the opt-in mixed eigensolver multiplies chi~ by N_eig + p columns on the
+    // projection GEMM: size its B operand for them
+    size_t E_tc = E;
+    for (int i = 0; i < n_q; ++i)
+      if (rpa::eig::applies(q[i].n_g, q[i].n_eig))
+        E_tc = std::max(E_tc, (size_t)(q[i].n_eig + rpa::eig::extra_vectors(q[i].n_eig)));
+    s = rpa::tc::alloc_workspace(p->tcw, G, E_tc, V, F, sl, e);
     if (s != RPA_OK) {
       free_plan(p);
       return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
@@ -626,11 +632,11 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   StageTimer timer(p, RPA_T_EIG0);
   bool refined = false;
   if (p->opt.precision == RPA_MIXED && p->refine_ready && rpa::eig::applies(n, q.n_eig)) {
-    // FP32 solve refined by a filtered Rayleigh-Ritz step in FP64 (rpa_eig.cu);
+    // FP32 reduction, FP64 tridiagonal solve, one filtered Rayleigh-Ritz step (rpa_eig.cu);
     // the eigenvectors land where the FP64 solver leaves them, for the gauge kernel
     int nl = 0;
-    s = p->refine.subspace(p->sol, p->params, p->chi, n, q.n_eig, p->lam_all, p->chi_work, p->st,
-                           p->err, &nl);
+    s = p->refine.subspace(p->sol, p->params, p->chi, n, q.n_eig, p->lam_all, p->chi_work,
+                           &p->tcw, p->st, p->err, &nl);
     p->launches += nl;
     if (s != RPA_OK && s != RPA_ENUMERIC) return s;
     refined = s == RPA_OK;  // RPA_ENUMERIC: no spectral interval to filter, use FP64

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "rpa_internal.h"
+#include "rpa_tc.h"
 #include "rpa_tridiag.h"
 
 namespace rpa {
@@ -173,7 +174,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
       !al((void**)&e2, n * sizeof(double)) || !al((void**)&wt, (mp + 1) * sizeof(double)) ||
       !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
       !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
-      !al((void**)&c32, n * mp * sizeof(float2)) ||
+      !al((void**)&c32, n * mp * sizeof(float2)) || !al((void**)&bt, n * mp * sizeof(cplx)) ||
       !al((void**)&x0, n * mp * sizeof(cplx)) || !al((void**)&x1, n * mp * sizeof(cplx)) ||
       !al((void**)&x2, n * mp * sizeof(cplx)) || !al((void**)&tau, mp * sizeof(cplx)) ||
       !al((void**)&g, mp * mp * sizeof(cplx)) || !al((void**)&theta, mp * sizeof(double)) ||
@@ -238,7 +239,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
 
 void Refine::release() {
   void* b[] = {h32, d32, e32, tau32, d64, e64, e2, wt, first, zt, lanes, c32,
-               x0, x1, x2, tau, g, theta, absmax, info, dwork};
+               bt, x0, x1, x2, tau, g, theta, absmax, info, dwork};
   for (void* p : b)
     if (p) cudaFree(p);
   if (hwork) free(hwork);
@@ -272,8 +273,8 @@ void Refine::release() {
   } while (0)
 
 rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, int n_eig,
-                            double* lam_out, cplx* vec_out, cudaStream_t st, std::string& err,
-                            int* launches) {
+                            double* lam_out, cplx* vec_out, tc::Workspace* tcw, cudaStream_t st,
+                            std::string& err, int* launches) {
   cusolverDnHandle_t sol = (cusolverDnHandle_t)sol_;
   cusolverDnParams_t params = (cusolverDnParams_t)params_;
   cublasHandle_t bh = (cublasHandle_t)blas;
@@ -341,8 +342,34 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   CU_E(cudaGetLastError());
   if (launches) *launches += 7;
 
+  // Y = H X for an n x m' block.  On the tensor cores (unless RPA_EIG_TC=0): the
+  // projection GEMM with the chi~ buffer as its A operand returns
+  // conj(sum_g chi~[g'][g] B[g][i]); with B = X^H (B[g][i] = conj(X(g, i))) that is
+  // sum_g conj(chi~[g'][g]) X(g, i) = (H X)(g', i), laid out column-major.  Its
+  // digit slices are the projection's (6 by default: products exact to ~2^-47 of
+  // the row and column scales); the stage timers leave them in this stage.
+  const char* tc_env = getenv("RPA_EIG_TC");
+  const bool on_tc = tcw != nullptr && !(tc_env && tc_env[0] == '0');
+  const cuDoubleComplex one = z(1.0), zero = z(0.0);
+  auto hx = [&](const cplx* X, cplx* Y) -> rpa_status {
+    if (!on_tc) {
+      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc,
+                       n, (const cuDoubleComplex*)X, n, &zero, (cuDoubleComplex*)Y, n));
+      return RPA_OK;
+    }
+    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)X, n,
+                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
+    const tc::Hook saved = tcw->hook;
+    tcw->hook = tc::Hook{};
+    int nl = 0;
+    const rpa_status r = tc::project(*tcw, hc, RPA_C128, n, n, bt, mp, Y, st, err, &nl);
+    tcw->hook = saved;
+    if (launches) *launches += nl;
+    return r;
+  };
+
   // 4. Chebyshev filter of degree 3 damping [a, b] = [lambda_{m'+1}, 0], scaled at
-  //    lambda_1 (the eigenvalues of T, FP64 products)
+  //    lambda_1 (the eigenvalues of T)
   const double a = w[mp] * mx, b = 0.0, lo = w[0] * mx;
   if (!(a < 0.0) || !(lo < a)) {
     // no unwanted interval to damp (the (m'+1)-th eigenvalue not below zero, or no
@@ -353,11 +380,10 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   double sigma = e / (lo - c);
   const double tau2 = 2.0 / sigma;
-  const cuDoubleComplex one = z(1.0), zero = z(0.0);
   cplx *xm = x0, *xk = x1, *xn = x2;  // X_{k-1}, X_k, X_{k+1}
+  rpa_status r = RPA_OK;
   // X_1 = (sigma / e) (H - c) X_0
-  CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc, n,
-                   (const cuDoubleComplex*)xm, n, &zero, (cuDoubleComplex*)xk, n));
+  if ((r = hx(xm, xk)) != RPA_OK) return r;
   {
     const cuDoubleComplex al = z(sigma / e), be = z(-c * sigma / e);
     CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xk, n,
@@ -366,8 +392,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   for (int k = 2; k <= 3; ++k) {
     const double s1 = 1.0 / (tau2 - sigma);
     // X_{k+1} = (2 s1 / e) (H - c) X_k - sigma s1 X_{k-1}
-    CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc,
-                     n, (const cuDoubleComplex*)xk, n, &zero, (cuDoubleComplex*)xn, n));
+    if ((r = hx(xk, xn)) != RPA_OK) return r;
     const cuDoubleComplex al = z(2.0 * s1 / e), be = z(-2.0 * s1 * c / e);
     CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xn, n,
                      &be, (const cuDoubleComplex*)xk, n, (cuDoubleComplex*)xn, n));
@@ -384,8 +409,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
                         (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)), info));
   // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H, U = Q Y
-  CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc, n,
-                   (const cuDoubleComplex*)xk, n, &zero, (cuDoubleComplex*)xn, n));
+  if ((r = hx(xk, xn)) != RPA_OK) return r;
   CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)xk, n,
                    (const cuDoubleComplex*)xn, n, &zero, (cuDoubleComplex*)g, mp));
   CS_E(cusolverDnXsyevd(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mp,

@@ -24,6 +24,10 @@ inline long n_transitions(const rpa_qpoint& q) {
 
 // ---- mixed-precision subspace of chi~(0) (rpa_eig.cu) ---------------------
 
+namespace tc {
+struct Workspace;
+}
+
 namespace eig {
 // Extra vectors carried beyond N_eig through the start and the FP64 step.
 int extra_vectors(int n_eig);
@@ -41,6 +45,7 @@ struct Refine {
   double* zt = nullptr;               // eigenvectors of T, n x m' row-major
   double* lanes = nullptr;            // inverse-iteration scratch, 6 n x m'
   float2* c32 = nullptr;              // T's eigenvectors, then chi~'s, n x m' complex64
+  cplx* bt = nullptr;                 // X^H of a block, the tensor-core product's B operand
   cplx *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;  // n x m' blocks (column-major)
   cplx* tau = nullptr;                // Householder scalars
   cplx* g = nullptr;                  // m' x m' Rayleigh quotient
@@ -56,9 +61,11 @@ struct Refine {
   void release();
   // lam_out[0 .. n_eig) and the column-major n x n_eig vec_out: the N_eig most
   // negative eigenpairs of the column-major view hc (n x n, Hermitian, not modified).
+  // With a tensor-core workspace the chi~ X products run on its digit-sliced
+  // projection GEMM (sized for N_eig + extra_vectors columns), else in cuBLAS FP64.
   rpa_status subspace(void* sol, void* params, const cplx* hc, int n, int n_eig,
-                      double* lam_out, cplx* vec_out, cudaStream_t st, std::string& err,
-                      int* launches);
+                      double* lam_out, cplx* vec_out, tc::Workspace* tcw, cudaStream_t st,
+                      std::string& err, int* launches);
 };
 }  // namespace eig
 
