@@ -280,6 +280,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
     ap.add_argument("--slices", default="4,6,3", help="digit slices of chi0, projection, chi_s")
+    ap.add_argument("--eig", default="fp64", choices=["fp64", "mixed"],
+                    help="eigensolver of chi~(0) on the mixed path: cuSOLVER FP64, or the opt-in "
+                         "FP32-reduction / FP64-tridiagonal solver with one filtered step")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -290,6 +293,8 @@ def main():
         profile_case(args.profile, args.slices)
         return
     w = WORKLOADS[args.workload]
+    if args.eig == "mixed":
+        os.environ["RPA_EIG_MIXED"] = "1"  # read by the library when a plan is created
     rank, world, local, dist = setup_dist(args)
     if args.impl == "reference":
         reference_arm(args, w, rank, dist)
@@ -517,6 +522,7 @@ def main():
         "data": "synthetic (splitmix64 matrix elements drawn on the device)",
         "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
                    "slices": list(slices) if mixed else None, "energy_route": args.route,
+                   "eigensolver": args.eig if mixed else "fp64",
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
         "contraction_tflops": contraction_tflops,
