@@ -368,63 +368,93 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
     return r;
   };
 
-  // 4. Chebyshev filter of degree 3 damping [a, b] = [lambda_{m'+1}, 0], scaled at
-  //    lambda_1 (the eigenvalues of T)
-  const double a = w[mp] * mx, b = 0.0, lo = w[0] * mx;
-  if (!(a < 0.0) || !(lo < a)) {
-    // no unwanted interval to damp (the (m'+1)-th eigenvalue not below zero, or no
-    // spread): the caller takes the FP64 solver
-    err = "mixed eigensolver: degenerate spectrum bounds";
-    return RPA_ENUMERIC;
-  }
-  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-  double sigma = e / (lo - c);
-  const double tau2 = 2.0 / sigma;
-  cplx *xm = x0, *xk = x1, *xn = x2;  // X_{k-1}, X_k, X_{k+1}
+  // 4.-5. RPA_EIG_STEPS (default 1, at most 8) filtered Rayleigh-Ritz steps.  Each
+  //    applies a degree-3 Chebyshev filter damping [a, 0] -- a = lambda_{m'+1} of T
+  //    first, the largest Ritz value of the block after that -- scaled at lambda_1,
+  //    takes an orthonormal basis Q of the filtered block (Householder QR, FP64)
+  //    and the eigenpairs of Q^H H Q (FP64); a further step starts from all m'
+  //    Ritz vectors.
+  const char* steps_env = getenv("RPA_EIG_STEPS");
+  const int steps = std::max(1, std::min(8, steps_env ? atoi(steps_env) : 1));
+  double a = w[mp] * mx, lo = w[0] * mx;
+  const double b = 0.0;
+  cplx* xs = x0;  // the block the next filter starts from
   rpa_status r = RPA_OK;
-  // X_1 = (sigma / e) (H - c) X_0
-  if ((r = hx(xm, xk)) != RPA_OK) return r;
-  {
-    const cuDoubleComplex al = z(sigma / e), be = z(-c * sigma / e);
-    CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xk, n,
-                     &be, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xk, n));
-  }
-  for (int k = 2; k <= 3; ++k) {
-    const double s1 = 1.0 / (tau2 - sigma);
-    // X_{k+1} = (2 s1 / e) (H - c) X_k - sigma s1 X_{k-1}
+  for (int step = 0; step < steps; ++step) {
+    if (!(a < 0.0) || !(lo < a)) {
+      // no unwanted interval to damp (the bound not below zero, or no spread): the
+      // caller takes the FP64 solver
+      err = "mixed eigensolver: degenerate spectrum bounds";
+      return RPA_ENUMERIC;
+    }
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    double sigma = e / (lo - c);
+    const double tau2 = 2.0 / sigma;
+    // X_{k-1}, X_k, X_{k+1}: the start block and the two other buffers
+    cplx *xm = xs, *xk = xs == x0 ? x1 : x0, *xn = xs == x2 ? x1 : x2;
+    // X_1 = (sigma / e) (H - c) X_0
+    if ((r = hx(xm, xk)) != RPA_OK) return r;
+    {
+      const cuDoubleComplex al = z(sigma / e), be = z(-c * sigma / e);
+      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xk, n,
+                       &be, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xk, n));
+    }
+    for (int k = 2; k <= 3; ++k) {
+      const double s1 = 1.0 / (tau2 - sigma);
+      // X_{k+1} = (2 s1 / e) (H - c) X_k - sigma s1 X_{k-1}
+      if ((r = hx(xk, xn)) != RPA_OK) return r;
+      const cuDoubleComplex al = z(2.0 * s1 / e), be = z(-2.0 * s1 * c / e);
+      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xn, n,
+                       &be, (const cuDoubleComplex*)xk, n, (cuDoubleComplex*)xn, n));
+      const cuDoubleComplex be2 = z(-sigma * s1);
+      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &one, (const cuDoubleComplex*)xn, n,
+                       &be2, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xn, n));
+      std::swap(xm, xk);  // X_{k-1} <- X_k
+      std::swap(xk, xn);  // X_k <- X_{k+1}; xn now holds the oldest block (free)
+      sigma = s1;
+    }
+    // orthonormal basis Q of the filtered block
+    CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F,
+                          dwork, dbytes, hwork, hbytes, info));
+    CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
+                          (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)), info));
+    // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H
     if ((r = hx(xk, xn)) != RPA_OK) return r;
-    const cuDoubleComplex al = z(2.0 * s1 / e), be = z(-2.0 * s1 * c / e);
-    CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xn, n,
-                     &be, (const cuDoubleComplex*)xk, n, (cuDoubleComplex*)xn, n));
-    const cuDoubleComplex be2 = z(-sigma * s1);
-    CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &one, (const cuDoubleComplex*)xn, n,
-                     &be2, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xn, n));
-    std::swap(xm, xk);  // X_{k-1} <- X_k
-    std::swap(xk, xn);  // X_k <- X_{k+1}; xn now holds the oldest block (free)
-    sigma = s1;
-  }
-  // 5. orthonormal basis Q of the filtered block (Householder QR, FP64)
-  CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F, dwork,
-                        dbytes, hwork, hbytes, info));
-  CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
-                        (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)), info));
-  // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H, U = Q Y
-  if ((r = hx(xk, xn)) != RPA_OK) return r;
-  CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)xk, n,
-                   (const cuDoubleComplex*)xn, n, &zero, (cuDoubleComplex*)g, mp));
-  CS_E(cusolverDnXsyevd(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mp,
-                        CUDA_C_64F, g, mp, CUDA_R_64F, theta, CUDA_C_64F, dwork, dbytes, hwork,
-                        hbytes, info));
-  CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, n_eig, mp, &one, (const cuDoubleComplex*)xk,
-                   n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)vec_out, n));
-  CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
-  int infs[3] = {0, 0, 0};
-  CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
-  CU_E(cudaStreamSynchronize(st));
-  if (infs[0] != 0 || infs[2] != 0) {
-    err = "mixed eigensolver: back-transform info " + std::to_string(infs[2]) +
-          ", QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
-    return RPA_EEIG;
+    CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)xk,
+                     n, (const cuDoubleComplex*)xn, n, &zero, (cuDoubleComplex*)g, mp));
+    CS_E(cusolverDnXsyevd(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mp,
+                          CUDA_C_64F, g, mp, CUDA_R_64F, theta, CUDA_C_64F, dwork, dbytes, hwork,
+                          hbytes, info));
+    int infs[3] = {0, 0, 0};
+    if (step + 1 < steps) {
+      // U = Q Y (all m' Ritz vectors, into the buffer H Q occupied) starts the next
+      // step; its filter damps beyond the largest Ritz value
+      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, mp, &one, (const cuDoubleComplex*)xk,
+                       n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)xn, n));
+      std::vector<double> th(mp);
+      CU_E(cudaMemcpyAsync(th.data(), theta, sizeof(double) * mp, cudaMemcpyDeviceToHost, st));
+      CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
+      CU_E(cudaStreamSynchronize(st));
+      if (infs[0] != 0) {
+        err = "mixed eigensolver: QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
+        return RPA_EEIG;
+      }
+      a = th[mp - 1];
+      lo = th[0];
+      xs = xn;
+      continue;
+    }
+    // the N_eig Ritz pairs: U = Q Y[:, 0:N_eig]
+    CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, n_eig, mp, &one, (const cuDoubleComplex*)xk,
+                     n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)vec_out, n));
+    CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
+    CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
+    CU_E(cudaStreamSynchronize(st));
+    if (infs[0] != 0 || infs[2] != 0) {
+      err = "mixed eigensolver: back-transform info " + std::to_string(infs[2]) +
+            ", QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
+      return RPA_EEIG;
+    }
   }
   return RPA_OK;
 }
