@@ -10,9 +10,10 @@
 //      back-transformed by Q span chi~'s leading subspace to ~1e-5 -- provided T's
 //      own eigenpairs are FP64: an FP32 solve of T resolves eigenvalues only to
 //      ~1e-7 of the largest, which near the cut mixes the subspace to ~0.1;
-//   2. the m' + 1 most negative eigenvalues of T by Sturm bisection and their
-//      eigenvectors by inverse iteration, in FP64 (rpa_tridiag.h), one thread per
-//      eigenvalue or cluster; Q applied to them in FP32 (cuSOLVER unmtr);
+//   2. the m' + 1 most negative eigenvalues of T by Sturm bisection (an FP32
+//      phase, then FP64 from the FP32 bracket once FP64 counts confirm it) and
+//      their eigenvectors by inverse iteration in FP64 (rpa_tridiag.h), one thread
+//      per eigenvalue or cluster; Q applied to them in FP32 (cuSOLVER unmtr);
 //   3. a degree-3 Chebyshev polynomial of chi~ that damps the interval of the
 //      unwanted eigenvalues [lambda_{m'+1}, 0] (scaled at lambda_1, after Zhou and
 //      Saad 2007), applied to those m' vectors with FP64 products;
@@ -76,28 +77,32 @@ __global__ void to_c128_kernel(const float2* v32, long n, int cols, cplx* x) {
     x[i] = cplx{(double)v32[i].x, (double)v32[i].y};
 }
 
-// T in FP64 (an exact promotion of the FP32 reduction) and its squared off-diagonal
+// T in FP64 (an exact promotion of the FP32 reduction) and its squared
+// off-diagonal in FP64 and in FP32
 __global__ void promote_tri_kernel(const float* d32, const float* e32, int n, double* d,
-                                   double* e, double* e2) {
+                                   double* e, double* e2, float* e2f) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     d[i] = (double)d32[i];
     if (i + 1 < n) {
       const double x = (double)e32[i];
       e[i] = x;
       e2[i] = x * x;
+      e2f[i] = e32[i] * e32[i];
     }
   }
 }
 
-// w[j] for j < k: eigenvalue j (ascending) of T by Sturm bisection, a thread each
-__global__ void bisect_kernel(const double* d, const double* e, const double* e2, int n, int k,
-                              double* w) {
+// w[j] for j < k: eigenvalue j (ascending) of T by Sturm bisection, a thread each;
+// FP32 bisection finished in FP64 (use32) or FP64 throughout
+__global__ void bisect_kernel(const double* d, const double* e, const double* e2, const float* d32,
+                              const float* e2f, int n, int k, int use32, double* w) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
   double lo, hi, pivmin;
   tri::bounds(d, e, n, &lo, &hi, &pivmin);
   const double abstol = 1e-8 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
-  w[j] = tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
+  w[j] = use32 ? tri::bisect_mixed(d, e2, d32, e2f, n, j, lo, hi, pivmin, abstol)
+               : tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
 }
 
 // Eigenvectors of T for the clusters c < nc of w (cluster c = w[first[c] ..
@@ -171,7 +176,8 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
   if (!al((void**)&h32, n * n * sizeof(float2)) || !al((void**)&d32, n * sizeof(float)) ||
       !al((void**)&e32, n * sizeof(float)) || !al((void**)&tau32, n * sizeof(float2)) ||
       !al((void**)&d64, n * sizeof(double)) || !al((void**)&e64, n * sizeof(double)) ||
-      !al((void**)&e2, n * sizeof(double)) || !al((void**)&wt, (mp + 1) * sizeof(double)) ||
+      !al((void**)&e2, n * sizeof(double)) || !al((void**)&e2f, n * sizeof(float)) ||
+      !al((void**)&wt, (mp + 1) * sizeof(double)) ||
       !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
       !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
       !al((void**)&c32, n * mp * sizeof(float2)) || !al((void**)&bt, n * mp * sizeof(cplx)) ||
@@ -238,7 +244,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
 }
 
 void Refine::release() {
-  void* b[] = {h32, d32, e32, tau32, d64, e64, e2, wt, first, zt, lanes, c32,
+  void* b[] = {h32, d32, e32, tau32, d64, e64, e2, e2f, wt, first, zt, lanes, c32,
                bt, x0, x1, x2, tau, g, theta, absmax, info, dwork};
   for (void* p : b)
     if (p) cudaFree(p);
@@ -296,9 +302,16 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   CS_E(cusolverDnChetrd(sol, CUBLAS_FILL_MODE_LOWER, n, (cuComplex*)h32, n, d32, e32,
                         (cuComplex*)tau32, (cuComplex*)dwork, lwc, info + 1));
   // 2. the m' + 1 most negative eigenvalues of T in FP64
-  promote_tri_kernel<<<grid_for(n, 256), 256, 0, st>>>(d32, e32, n, d64, e64, e2);
+  //    (RPA_EIG_BISECT32=0: without the FP32 phase; RPA_EIG_BISECT_BLOCK threads a
+  //    block, 32 by default, a multiple of 32 at most 256)
+  promote_tri_kernel<<<grid_for(n, 256), 256, 0, st>>>(d32, e32, n, d64, e64, e2, e2f);
   CU_E(cudaGetLastError());
-  bisect_kernel<<<(mp + 1 + 31) / 32, 32, 0, st>>>(d64, e64, e2, n, mp + 1, wt);
+  const char* b32_env = getenv("RPA_EIG_BISECT32");
+  const char* blk_env = getenv("RPA_EIG_BISECT_BLOCK");
+  const int use32 = !(b32_env && b32_env[0] == '0');
+  const int bb = std::max(32, std::min(256, (blk_env ? atoi(blk_env) : 32) / 32 * 32));
+  bisect_kernel<<<(mp + 1 + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, d32, e2f, n, mp + 1, use32,
+                                                      wt);
   CU_E(cudaGetLastError());
   std::vector<double> w(mp + 1);
   unsigned long long mx_bits = 0;

@@ -40,6 +40,7 @@ struct Refine {
   float *d32 = nullptr, *e32 = nullptr;  // FP32 tridiagonal T: diagonal, off-diagonal
   float2* tau32 = nullptr;            // its Householder scalars
   double *d64 = nullptr, *e64 = nullptr, *e2 = nullptr;  // T in FP64, e^2
+  float* e2f = nullptr;               // e^2 in FP32 (the FP32 bisection phase)
   double* wt = nullptr;               // m' + 1 smallest eigenvalues of T
   int* first = nullptr;               // cluster starts of those eigenvalues
   double* zt = nullptr;               // eigenvectors of T, n x m' row-major

@@ -8,7 +8,8 @@
 // eigenpairs are computed in FP64:
 //   * eigenvalue j (ascending) by bisection on the Sturm count of T - x I (the
 //     number of negative pivots of its LDL^T factorisation, Sylvester's law of
-//     inertia), each eigenvalue independently;
+//     inertia), each eigenvalue independently: in FP32 first, then, from the
+//     FP32 bracket once two FP64 counts confirm it, in FP64;
 //   * its eigenvector by inverse iteration with T - lambda_j I factored by
 //     Gaussian elimination with partial pivoting (three iterations from a fixed
 //     pseudo-random start), re-orthogonalised (modified Gram-Schmidt) against the
@@ -89,6 +90,63 @@ RPA_HD double bisect(const double* d, const double* e2, int n, int j, double lo,
       hi = mid;
   }
   return 0.5 * (lo + hi);
+}
+
+// The Sturm count in FP32 (T's FP32 diagonal d and squared off-diagonal e2):
+// exact for a matrix within a few FP32 ulps of T, so an FP32 bisection places
+// each eigenvalue of the graded T to ~1e-7 of itself at FP32 cost.
+RPA_HD int sturm_count_f(const float* d, const float* e2, int n, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (q <= pivmin) {
+    ++c;
+    q = fminf(q, -pivmin);
+  }
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (q <= pivmin) {
+      ++c;
+      q = fminf(q, -pivmin);
+    }
+  }
+  return c;
+}
+
+// FP32 bisection of [*lo, *hi] for eigenvalue j, to 4 FP32 ulps of the eigenvalue
+// (at most 64 halvings).  d32, e2_32: T's diagonal and squared off-diagonal in FP32.
+RPA_HD void bisect_f(const float* d32, const float* e2_32, int n, int j, float* lo, float* hi) {
+  float flo = *lo, fhi = *hi;
+  const float fpiv = 1.1754944e-38f;  // FLT_MIN
+  for (int it = 0; it < 64; ++it) {
+    if (fhi - flo <= 4.0f * 1.1920929e-7f * fmaxf(fabsf(flo), fabsf(fhi))) break;
+    const float mid = 0.5f * (flo + fhi);
+    if (mid <= flo || mid >= fhi) break;
+    if (sturm_count_f(d32, e2_32, n, mid, fpiv) <= j)
+      flo = mid;
+    else
+      fhi = mid;
+  }
+  *lo = flo;
+  *hi = fhi;
+}
+
+// Eigenvalue j of T: the FP32 bracket of bisect_f, widened by twice its width,
+// checked with two FP64 Sturm counts and bisected on in FP64 to the tolerance of
+// bisect().  A bracket that the FP64 counts reject (the FP32 counts disagreed with
+// FP64 near the eigenvalue) falls back to FP64 bisection of [lo, hi], so the FP32
+// phase only ever saves FP64 counts.
+RPA_HD double bisect_mixed(const double* d, const double* e2, const float* d32,
+                           const float* e2_32, int n, int j, double lo, double hi,
+                           double pivmin, double abstol) {
+  float flo = (float)lo, fhi = (float)hi;
+  bisect_f(d32, e2_32, n, j, &flo, &fhi);
+  const double w = (double)fhi - (double)flo;
+  const double blo = fmax(lo, (double)flo - 2.0 * w - abstol);
+  const double bhi = fmin(hi, (double)fhi + 2.0 * w + abstol);
+  if (blo < bhi && sturm_count(d, e2, n, blo, pivmin) <= j &&
+      sturm_count(d, e2, n, bhi, pivmin) > j)
+    return bisect(d, e2, n, j, blo, bhi, pivmin, abstol);
+  return bisect(d, e2, n, j, lo, hi, pivmin, abstol);
 }
 
 // Cluster starts of the ascending eigenvalues w[0..k-1]: a new cluster begins at j

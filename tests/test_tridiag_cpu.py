@@ -29,6 +29,8 @@ def lib(tmp_path_factory):
                     "-o", out], check=True)
     so = ctypes.CDLL(out)
     so.tri_eigvals.argtypes = [DP, DP, ctypes.c_int, ctypes.c_int, DP]
+    FP = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+    so.tri_eigvals_mixed.argtypes = [DP, DP, ctypes.c_int, ctypes.c_int, DP, FP, FP]
     so.tri_clusters.argtypes = [DP, ctypes.c_int, ctypes.c_double, IP]
     so.tri_vectors.argtypes = [DP, DP, ctypes.c_int, DP, ctypes.c_int, ctypes.c_double, DP]
     return so
@@ -39,6 +41,14 @@ def eigvals(lib, d, e, k):
     assert lib.tri_eigvals(np.ascontiguousarray(d, float), np.ascontiguousarray(e, float),
                            len(d), k, w) == 0
     return w
+
+
+def eigvals_mixed(lib, d, e, k):
+    w = np.zeros(k)
+    lo, hi = np.zeros(k, np.float32), np.zeros(k, np.float32)
+    assert lib.tri_eigvals_mixed(np.ascontiguousarray(d, float), np.ascontiguousarray(e, float),
+                                 len(d), k, w, lo, hi) == 0
+    return w, lo, hi
 
 
 def vectors(lib, d, e, w, tol):
@@ -106,6 +116,39 @@ def test_tight_cluster_is_reorthogonalised(lib):
     for c in range(nc):
         j0, j1 = first[c], first[c + 1]
         assert sin_angle(z[:, j0:j1], ref_z[:, j0:j1]) < 1e-9
+
+
+def graded(n, seed):
+    rng = np.random.default_rng(seed)
+    g = 10.0 ** (-8.0 * np.arange(n) / n)
+    d = -g * (1.0 + 0.1 * rng.random(n))
+    e = 0.2 * np.sqrt(g[:-1] * g[1:]) * np.sign(rng.standard_normal(n - 1))
+    return d.astype(np.float32).astype(float), e.astype(np.float32).astype(float)
+
+
+@pytest.mark.parametrize("kind", ["random", "graded", "cluster"])
+def test_fp32_bisection_finished_in_fp64_equals_fp64_bisection(lib, kind):
+    # T with FP32 entries (as the FP32 reduction leaves it): the FP32 phase only
+    # narrows the bracket, the FP64 result is that of plain FP64 bisection
+    rng = np.random.default_rng(4)
+    if kind == "random":
+        d, e = (rng.standard_normal(300).astype(np.float32).astype(float),
+                rng.standard_normal(299).astype(np.float32).astype(float))
+    elif kind == "graded":
+        d, e = graded(400, 5)
+    else:
+        d0 = rng.standard_normal(40).astype(np.float32).astype(float)
+        e0 = rng.standard_normal(39).astype(np.float32).astype(float)
+        d, e = np.concatenate([d0, d0]), np.concatenate([e0, [1e-20], e0])
+    k = 80
+    ref = eigvals(lib, d, e, k)
+    w, lo, hi = eigvals_mixed(lib, d, e, k)
+    scale = np.max(np.abs(ref))
+    assert np.all(np.abs(w - ref) <= 4 * np.finfo(float).eps * np.abs(ref) + 1e-20 * scale)
+    # the FP32 brackets (before widening) hold the eigenvalue to a few FP32 ulps
+    # of it in almost every case, so the FP64 fallback stays rare
+    held = (lo.astype(float) - 4 * np.abs(lo) * 1.2e-7 <= ref) & (ref <= hi.astype(float) + 4 * np.abs(hi) * 1.2e-7)
+    assert np.mean(held) >= 0.95, np.mean(held)
 
 
 def test_clusters_split_on_gaps(lib):
