@@ -51,6 +51,40 @@ def child(shape, slices, reps):
                       "stages": {k: v / reps for k, v in st.items() if v}}))
 
 
+def run_candidate(setting, a):
+    """Time one knob setting in a fresh process; its JSON line, or {"error": ...}."""
+    env = dict(os.environ)
+    env.update(setting)
+    r = subprocess.run([sys.executable, "-m", "paper_2405_20258_gb300.tune", "--child",
+                        "--shape", a.shape, "--slices", a.slices, "--reps", str(a.reps)],
+                       env=env, capture_output=True, text=True, cwd=os.path.dirname(HERE))
+    if r.returncode != 0:
+        return {"error": r.stderr.strip()[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def select(grid, run):
+    """Run the default setting and every point of the grid (knob -> values) through
+    run(setting); the fastest candidate whose E_c equals the default's to 1e-10
+    relative wins.  Returns (best or None, all results)."""
+    keys = list(grid)
+    results = []
+    base_ec = None
+    for values in [None] + list(itertools.product(*(grid[k] for k in keys))):
+        setting = {} if values is None else dict(zip(keys, values))
+        out = run(setting)
+        if "error" in out:
+            results.append({"env": setting, "error": out["error"]})
+            continue
+        if base_ec is None:
+            base_ec = out["ec"]
+        out = dict(out)
+        out["agrees"] = abs(out["ec"] - base_ec) <= 1e-10 * abs(base_ec)
+        results.append({"env": setting, **out})
+    ok = [r for r in results if "gemm_ms" in r and r["agrees"]]
+    return (min(ok, key=lambda r: r["gemm_ms"]) if ok else None), results
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--shape", default="4000,128,2000,400,32",
@@ -67,27 +101,13 @@ def main(argv=None):
         child(shape, slices, a.reps)
         return
     grid = json.loads(a.grid) if a.grid else CANDIDATES
-    keys = list(grid)
-    results = []
-    base_ec = None
-    for values in [None] + list(itertools.product(*(grid[k] for k in keys))):
-        env = dict(os.environ)
-        setting = {} if values is None else dict(zip(keys, values))
-        env.update(setting)
-        r = subprocess.run([sys.executable, "-m", "paper_2405_20258_gb300.tune", "--child",
-                            "--shape", a.shape, "--slices", a.slices, "--reps", str(a.reps)],
-                           env=env, capture_output=True, text=True, cwd=os.path.dirname(HERE))
-        if r.returncode != 0:
-            results.append({"env": setting, "error": r.stderr.strip()[-300:]})
-            continue
-        out = json.loads(r.stdout.strip().splitlines()[-1])
-        if base_ec is None:
-            base_ec = out["ec"]
-        out["agrees"] = abs(out["ec"] - base_ec) <= 1e-10 * abs(base_ec)
-        results.append({"env": setting, **out})
-        print(json.dumps(results[-1]), file=sys.stderr, flush=True)
-    ok = [r for r in results if "gemm_ms" in r and r["agrees"]]
-    best = min(ok, key=lambda r: r["gemm_ms"]) if ok else None
+
+    def run(setting):
+        out = run_candidate(setting, a)
+        print(json.dumps({"env": setting, **out}), file=sys.stderr, flush=True)
+        return out
+
+    best, results = select(grid, run)
     print(json.dumps({"shape": shape, "slices": slices, "best_env": best and best["env"],
                       "best_gemm_ms": best and best["gemm_ms"],
                       "default_gemm_ms": results[0].get("gemm_ms"),
