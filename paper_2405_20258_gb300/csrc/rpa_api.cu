@@ -619,8 +619,11 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   p->basis_iq = -1;
   const rpa_qpoint& q = *qp(p, iq);
   const int n = q.n_g;
-  if (p->opt.precision == RPA_MIXED) {
-    // the projection's A planes are cut on the side stream during the eigensolve
+  const bool refine_here = p->opt.precision == RPA_MIXED && p->refine_ready &&
+                           rpa::eig::applies(n, q.n_eig);
+  // the projection's A planes are cut on the side stream during the eigensolve,
+  // unless the opt-in eigensolver's tensor-core products take the planes then
+  if (p->opt.precision == RPA_MIXED && !(refine_here && rpa::eig::products_on_tc())) {
     const void* A;
     int dt, nl = 0;
     if ((s = matrix_a(p, iq, &A, &dt)) != RPA_OK) return s;
@@ -631,7 +634,7 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   }
   StageTimer timer(p, RPA_T_EIG0);
   bool refined = false;
-  if (p->opt.precision == RPA_MIXED && p->refine_ready && rpa::eig::applies(n, q.n_eig)) {
+  if (refine_here) {
     // FP32 reduction, FP64 tridiagonal solve, one filtered Rayleigh-Ritz step (rpa_eig.cu);
     // the eigenvectors land where the FP64 solver leaves them, for the gauge kernel
     int nl = 0;

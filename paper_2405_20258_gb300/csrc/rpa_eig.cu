@@ -152,6 +152,11 @@ bool applies(int n, int n_eig) {
   return n >= 1024 && n_eig + extra_vectors(n_eig) + 1 < n;
 }
 
+bool products_on_tc() {
+  const char* e = getenv("RPA_EIG_TC");
+  return !(e && e[0] == '0');
+}
+
 rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::string& err) {
   cusolverDnHandle_t sol = (cusolverDnHandle_t)sol_;
   cusolverDnParams_t params = (cusolverDnParams_t)params_;
@@ -361,8 +366,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   // sum_g conj(chi~[g'][g]) X(g, i) = (H X)(g', i), laid out column-major.  Its
   // digit slices are the projection's (6 by default: products exact to ~2^-47 of
   // the row and column scales); the stage timers leave them in this stage.
-  const char* tc_env = getenv("RPA_EIG_TC");
-  const bool on_tc = tcw != nullptr && !(tc_env && tc_env[0] == '0');
+  const bool on_tc = tcw != nullptr && products_on_tc();
   const cuDoubleComplex one = z(1.0), zero = z(0.0);
   auto hx = [&](const cplx* X, cplx* Y) -> rpa_status {
     if (!on_tc) {

@@ -34,6 +34,8 @@ int extra_vectors(int n_eig);
 // Whether the mixed path takes the subspace this way (opt-in with RPA_EIG_MIXED=1;
 // N_G >= 1024 and room for the extra vectors).
 bool applies(int n, int n_eig);
+// Whether its chi~ X products run on the tensor-core GEMM (RPA_EIG_TC, default on).
+bool products_on_tc();
 struct Refine {
   void* blas = nullptr;               // cublasHandle_t
   float2* h32 = nullptr;              // chi~ / max|chi~| in complex64, n x n (then reflectors)
