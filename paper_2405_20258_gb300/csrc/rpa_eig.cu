@@ -186,6 +186,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
       !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
       !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
       !al((void**)&c32, n * mp * sizeof(float2)) || !al((void**)&bt, n * mp * sizeof(cplx)) ||
+      !al((void**)&yb, mp * mp * sizeof(cplx)) ||
       !al((void**)&x0, n * mp * sizeof(cplx)) || !al((void**)&x1, n * mp * sizeof(cplx)) ||
       !al((void**)&x2, n * mp * sizeof(cplx)) || !al((void**)&tau, mp * sizeof(cplx)) ||
       !al((void**)&g, mp * mp * sizeof(cplx)) || !al((void**)&theta, mp * sizeof(double)) ||
@@ -250,7 +251,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
 
 void Refine::release() {
   void* b[] = {h32, d32, e32, tau32, d64, e64, e2, e2f, wt, first, zt, lanes, c32,
-               bt, x0, x1, x2, tau, g, theta, absmax, info, dwork};
+               bt, yb, x0, x1, x2, tau, g, theta, absmax, info, dwork};
   for (void* p : b)
     if (p) cudaFree(p);
   if (hwork) free(hwork);
@@ -360,14 +361,26 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   CU_E(cudaGetLastError());
   if (launches) *launches += 7;
 
-  // Y = H X for an n x m' block.  On the tensor cores (unless RPA_EIG_TC=0): the
-  // projection GEMM with the chi~ buffer as its A operand returns
-  // conj(sum_g chi~[g'][g] B[g][i]); with B = X^H (B[g][i] = conj(X(g, i))) that is
-  // sum_g conj(chi~[g'][g]) X(g, i) = (H X)(g', i), laid out column-major.  Its
-  // digit slices are the projection's (6 by default: products exact to ~2^-47 of
-  // the row and column scales); the stage timers leave them in this stage.
+  // Products on the tensor cores (unless RPA_EIG_TC=0) use the projection GEMM,
+  // which for a row-major A [rows][K] and a row-major B [K][cols] writes
+  // out[c][r] = conj(sum_k A[r][k] B[k][c]), i.e. the column-major rows x cols
+  // matrix conj(A B).  Its digit slices are the projection's (6 by default:
+  // products exact to ~2^-47 of the row and column scales); the stage timers leave
+  // these launches in this stage.  Column-major blocks enter through Zgeam's
+  // conjugate transpose, which turns a column-major X into the row-major conj(X).
   const bool on_tc = tcw != nullptr && products_on_tc();
   const cuDoubleComplex one = z(1.0), zero = z(0.0);
+  auto tc_gemm = [&](const cplx* a_rm, int rows, int k, const cplx* b_rm, int cols,
+                     cplx* out) -> rpa_status {
+    const tc::Hook saved = tcw->hook;
+    tcw->hook = tc::Hook{};
+    int nl = 0;
+    const rpa_status r = tc::project(*tcw, a_rm, RPA_C128, rows, k, b_rm, cols, out, st, err, &nl);
+    tcw->hook = saved;
+    if (launches) *launches += nl;
+    return r;
+  };
+  // Y = H X (n x m'): A = the chi~ buffer (chi~[g'][g] = conj(H(g', g))), B = conj(X)
   auto hx = [&](const cplx* X, cplx* Y) -> rpa_status {
     if (!on_tc) {
       CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc,
@@ -376,13 +389,32 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
     }
     CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)X, n,
                      &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
-    const tc::Hook saved = tcw->hook;
-    tcw->hook = tc::Hook{};
-    int nl = 0;
-    const rpa_status r = tc::project(*tcw, hc, RPA_C128, n, n, bt, mp, Y, st, err, &nl);
-    tcw->hook = saved;
-    if (launches) *launches += nl;
-    return r;
+    return tc_gemm(hc, n, n, bt, mp, Y);
+  };
+  // G = Q^H Z (m' x m') for Z = H Q: A = Z read row-major ([m'][n], A[j][g] = Z(g, j)),
+  // B = conj(Q); the GEMM gives conj(Z^T conj(Q)) = Z^H Q = Q^H H Q = G (H Hermitian)
+  auto qhz = [&](const cplx* Q, const cplx* Z, cplx* G) -> rpa_status {
+    if (!on_tc) {
+      CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)Q,
+                       n, (const cuDoubleComplex*)Z, n, &zero, (cuDoubleComplex*)G, mp));
+      return RPA_OK;
+    }
+    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)Q, n,
+                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
+    return tc_gemm(Z, mp, n, bt, mp, G);
+  };
+  // U = Q Y[:, 0:cols] (n x cols, Y m' x m'): A = conj(Q), B = conj(Y[:, 0:cols])
+  auto qy = [&](const cplx* Q, const cplx* Y, int cols, cplx* U) -> rpa_status {
+    if (!on_tc) {
+      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, cols, mp, &one, (const cuDoubleComplex*)Q,
+                       n, (const cuDoubleComplex*)Y, mp, &zero, (cuDoubleComplex*)U, n));
+      return RPA_OK;
+    }
+    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)Q, n,
+                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
+    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, cols, mp, &one, (const cuDoubleComplex*)Y, mp,
+                     &zero, (const cuDoubleComplex*)yb, cols, (cuDoubleComplex*)yb, cols));
+    return tc_gemm(bt, n, mp, yb, cols, U);
   };
 
   // 4.-5. RPA_EIG_STEPS (default 1, at most 8) filtered Rayleigh-Ritz steps.  Each
@@ -437,8 +469,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
                           (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)), info));
     // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H
     if ((r = hx(xk, xn)) != RPA_OK) return r;
-    CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)xk,
-                     n, (const cuDoubleComplex*)xn, n, &zero, (cuDoubleComplex*)g, mp));
+    if ((r = qhz(xk, xn, g)) != RPA_OK) return r;
     CS_E(cusolverDnXsyevd(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mp,
                           CUDA_C_64F, g, mp, CUDA_R_64F, theta, CUDA_C_64F, dwork, dbytes, hwork,
                           hbytes, info));
@@ -446,8 +477,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
     if (step + 1 < steps) {
       // U = Q Y (all m' Ritz vectors, into the buffer H Q occupied) starts the next
       // step; its filter damps beyond the largest Ritz value
-      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, mp, &one, (const cuDoubleComplex*)xk,
-                       n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)xn, n));
+      if ((r = qy(xk, g, mp, xn)) != RPA_OK) return r;
       std::vector<double> th(mp);
       CU_E(cudaMemcpyAsync(th.data(), theta, sizeof(double) * mp, cudaMemcpyDeviceToHost, st));
       CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
@@ -462,8 +492,7 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
       continue;
     }
     // the N_eig Ritz pairs: U = Q Y[:, 0:N_eig]
-    CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, n_eig, mp, &one, (const cuDoubleComplex*)xk,
-                     n, (const cuDoubleComplex*)g, mp, &zero, (cuDoubleComplex*)vec_out, n));
+    if ((r = qy(xk, g, n_eig, vec_out)) != RPA_OK) return r;
     CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
     CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
     CU_E(cudaStreamSynchronize(st));

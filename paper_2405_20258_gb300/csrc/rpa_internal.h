@@ -48,7 +48,8 @@ struct Refine {
   double* zt = nullptr;               // eigenvectors of T, n x m' row-major
   double* lanes = nullptr;            // inverse-iteration scratch, 6 n x m'
   float2* c32 = nullptr;              // T's eigenvectors, then chi~'s, n x m' complex64
-  cplx* bt = nullptr;                 // X^H of a block, the tensor-core product's B operand
+  cplx* bt = nullptr;                 // conj-transposed block, a tensor-core GEMM operand
+  cplx* yb = nullptr;                 // conj-transposed Ritz coefficients, m' x m'
   cplx *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;  // n x m' blocks (column-major)
   cplx* tau = nullptr;                // Householder scalars
   cplx* g = nullptr;                  // m' x m' Rayleigh quotient
