@@ -133,6 +133,46 @@ __global__ void z_to_c64_kernel(const double* z, int n, int k, float2* c) {
   }
 }
 
+// dinv[j] = 1 / ||x[:, j]|| in FP64 (1 for a zero column); one 256-thread block per
+// column of the column-major n x cols block, grid = cols
+__global__ void inv_colnorm_kernel(const cplx* x, int n, int cols, double* dinv) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  if (j >= cols) return;  // whole blocks only
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cplx v = x[(long)j * n + i];
+    s += v.re * v.re + v.im * v.im;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    dinv[j] = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
+  }
+}
+
+// x[:, j] *= dinv[j]
+__global__ void scale_cols_kernel(cplx* x, int n, int cols, const double* dinv) {
+  const long tot = (long)n * cols;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < tot;
+       o += (long)gridDim.x * blockDim.x) {
+    const double f = dinv[o / n];
+    x[o].re *= f;
+    x[o].im *= f;
+  }
+}
+
+// zero the strictly lower triangle of the column-major m x m matrix g
+__global__ void zero_lower_kernel(cplx* g, int m) {
+  const long tot = (long)m * m;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < tot;
+       o += (long)gridDim.x * blockDim.x)
+    if (o % m > o / m) g[o] = cplx{0.0, 0.0};
+}
+
 // widest cluster of T's eigenvalues re-orthogonalised by one thread
 constexpr int kMaxCluster = 64;
 
@@ -186,7 +226,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
       !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
       !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
       !al((void**)&c32, n * mp * sizeof(float2)) || !al((void**)&bt, n * mp * sizeof(cplx)) ||
-      !al((void**)&yb, mp * mp * sizeof(cplx)) ||
+      !al((void**)&yb, mp * mp * sizeof(cplx)) || !al((void**)&dinv, mp * sizeof(double)) ||
       !al((void**)&x0, n * mp * sizeof(cplx)) || !al((void**)&x1, n * mp * sizeof(cplx)) ||
       !al((void**)&x2, n * mp * sizeof(cplx)) || !al((void**)&tau, mp * sizeof(cplx)) ||
       !al((void**)&g, mp * mp * sizeof(cplx)) || !al((void**)&theta, mp * sizeof(double)) ||
@@ -230,6 +270,22 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
     return RPA_EEIG;
   }
   db = std::max(db, (size_t)lw * sizeof(cuDoubleComplex));
+  if (cusolverDnXpotrf_bufferSize(sol, params, CUBLAS_FILL_MODE_UPPER, mp_max, CUDA_C_64F, g,
+                                  mp_max, CUDA_C_64F, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
+    err = "cusolverDnXpotrf_bufferSize failed";
+    release();
+    return RPA_EEIG;
+  }
+  db = std::max(db, d1);
+  hb = std::max(hb, h1);
+  if (cusolverDnXtrtri_bufferSize(sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, mp_max,
+                                  CUDA_C_64F, g, mp_max, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
+    err = "cusolverDnXtrtri_bufferSize failed";
+    release();
+    return RPA_EEIG;
+  }
+  db = std::max(db, d1);
+  hb = std::max(hb, h1);
   if (cusolverDnXsyevd_bufferSize(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
                                   mp_max, CUDA_C_64F, g, mp_max, CUDA_R_64F, theta, CUDA_C_64F,
                                   &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
@@ -251,7 +307,7 @@ rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::
 
 void Refine::release() {
   void* b[] = {h32, d32, e32, tau32, d64, e64, e2, e2f, wt, first, zt, lanes, c32,
-               bt, yb, x0, x1, x2, tau, g, theta, absmax, info, dwork};
+               bt, yb, dinv, x0, x1, x2, tau, g, theta, absmax, info, dwork};
   for (void* p : b)
     if (p) cudaFree(p);
   if (hwork) free(hwork);
@@ -417,6 +473,52 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
     return tc_gemm(bt, n, mp, yb, cols, U);
   };
 
+  // Orthonormal basis of a filtered block Y by column-scaled Cholesky-QR2 (with
+  // RPA_EIG_QR=chol and the tensor-core products): two passes of Y <- Y D^-1 with
+  // D = diag(||y_j||), G = Y^H Y, G = R^H R (FP64 Cholesky), Y <- Y R^-1 (FP64
+  // triangular inverse, the product on the tensor cores).  The columns of a filtered
+  // block span ~1e14 in norm; scaled they are conditioned ~1e7 on these spectra,
+  // within what Cholesky-QR2 takes.  The scaling is applied to the block itself so
+  // that the row-scaled digits of the products see columns of one size.  Y and
+  // spare are swapped as the passes go; done stays false when a Cholesky factor
+  // fails (then Y, rescaled, still spans the filtered block for Householder QR).
+  const char* qr_env = getenv("RPA_EIG_QR");
+  const bool chol_qr = on_tc && qr_env && strcmp(qr_env, "chol") == 0;
+  auto chol_qr2 = [&](cplx*& Y, cplx*& spare, bool& done) -> rpa_status {
+    done = false;
+    for (int pass = 0; pass < 2; ++pass) {
+      inv_colnorm_kernel<<<mp, 256, 0, st>>>(Y, n, mp, dinv);
+      CU_E(cudaGetLastError());
+      scale_cols_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(Y, n, mp, dinv);
+      CU_E(cudaGetLastError());
+      rpa_status rq = qhz(Y, Y, g);  // G = Y^H Y
+      if (rq != RPA_OK) return rq;
+      CU_E(cudaMemsetAsync(info + 3, 0, sizeof(int), st));
+      CS_E(cusolverDnXpotrf(sol, params, CUBLAS_FILL_MODE_UPPER, mp, CUDA_C_64F, g, mp,
+                            CUDA_C_64F, dwork, dbytes, hwork, hbytes, info + 3));
+      int pinf = 0;
+      CU_E(cudaMemcpyAsync(&pinf, info + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU_E(cudaStreamSynchronize(st));
+      if (pinf != 0) return RPA_OK;
+      CS_E(cusolverDnXtrtri(sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, mp, CUDA_C_64F, g,
+                            mp, dwork, dbytes, hwork, hbytes, info + 3));
+      zero_lower_kernel<<<grid_for((long)mp * mp, 256), 256, 0, st>>>(g, mp);
+      CU_E(cudaGetLastError());
+      if ((rq = qy(Y, g, mp, spare)) != RPA_OK) return rq;  // Y R^-1
+      std::swap(Y, spare);
+      if (launches) *launches += 3;
+    }
+    int tinf = 0;
+    CU_E(cudaMemcpyAsync(&tinf, info + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU_E(cudaStreamSynchronize(st));
+    if (tinf != 0) {
+      err = "mixed eigensolver: triangular inverse info " + std::to_string(tinf);
+      return RPA_EEIG;
+    }
+    done = true;
+    return RPA_OK;
+  };
+
   // 4.-5. RPA_EIG_STEPS (default 1, at most 8) filtered Rayleigh-Ritz steps.  Each
   //    applies a degree-3 Chebyshev filter damping [a, 0] -- a = lambda_{m'+1} of T
   //    first, the largest Ritz value of the block after that -- scaled at lambda_1,
@@ -462,11 +564,16 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
       std::swap(xk, xn);  // X_k <- X_{k+1}; xn now holds the oldest block (free)
       sigma = s1;
     }
-    // orthonormal basis Q of the filtered block
-    CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F,
-                          dwork, dbytes, hwork, hbytes, info));
-    CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
-                          (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)), info));
+    // orthonormal basis Q of the filtered block (into xk; xm is free)
+    bool qr_done = false;
+    if (chol_qr && (r = chol_qr2(xk, xm, qr_done)) != RPA_OK) return r;
+    if (!qr_done) {
+      CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F,
+                            dwork, dbytes, hwork, hbytes, info));
+      CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
+                            (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)),
+                            info));
+    }
     // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H
     if ((r = hx(xk, xn)) != RPA_OK) return r;
     if ((r = qhz(xk, xn, g)) != RPA_OK) return r;

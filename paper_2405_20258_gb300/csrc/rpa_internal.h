@@ -50,6 +50,7 @@ struct Refine {
   float2* c32 = nullptr;              // T's eigenvectors, then chi~'s, n x m' complex64
   cplx* bt = nullptr;                 // conj-transposed block, a tensor-core GEMM operand
   cplx* yb = nullptr;                 // conj-transposed Ritz coefficients, m' x m'
+  double* dinv = nullptr;             // inverse column norms (Cholesky-QR)
   cplx *x0 = nullptr, *x1 = nullptr, *x2 = nullptr;  // n x m' blocks (column-major)
   cplx* tau = nullptr;                // Householder scalars
   cplx* g = nullptr;                  // m' x m' Rayleigh quotient

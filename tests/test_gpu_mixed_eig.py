@@ -1,7 +1,8 @@
 """GPU parity of the opt-in mixed eigensolver of chi~(0) (RPA_EIG_MIXED=1):
 FP32 Householder reduction, FP64 tridiagonal eigenpairs, one Chebyshev-filtered
 Rayleigh-Ritz step in FP64 with the chi~ X products on the tensor cores
-(RPA_EIG_TC=1) or in cuBLAS FP64 (RPA_EIG_TC=0), one step or two (RPA_EIG_STEPS).
+(RPA_EIG_TC=1) or in cuBLAS FP64 (RPA_EIG_TC=0), one step or two (RPA_EIG_STEPS),
+Householder or column-scaled Cholesky-QR2 (RPA_EIG_QR).
 
 Against the oracle at N_G = 1024 (the smallest size the solver takes): the
 N_eig eigenvalues, the subspace (largest principal-angle sine), and E_c within
@@ -30,11 +31,13 @@ def sin_angle(U, V):
     return np.linalg.norm(Qv - Qu @ (Qu.conj().T @ Qv), 2)
 
 
-@pytest.mark.parametrize("tc,steps", [("1", "1"), ("0", "1"), ("1", "2")])
-def test_mixed_eigensolver_vs_oracle_1024(monkeypatch, tc, steps):
+@pytest.mark.parametrize("tc,steps,qr", [("1", "1", "householder"), ("0", "1", "householder"),
+                                         ("1", "2", "householder"), ("1", "1", "chol")])
+def test_mixed_eigensolver_vs_oracle_1024(monkeypatch, tc, steps, qr):
     monkeypatch.setenv("RPA_EIG_MIXED", "1")
     monkeypatch.setenv("RPA_EIG_TC", tc)
     monkeypatch.setenv("RPA_EIG_STEPS", steps)
+    monkeypatch.setenv("RPA_EIG_QR", qr)
     qp = inputs.make_qpoint(1024, 32, 1000)
     A = inputs.matrix_elements(qp)
     n_eig, n_freq = 128, 16
