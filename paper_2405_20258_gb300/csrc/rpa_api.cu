@@ -592,6 +592,15 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
                       p->st, p->err, &nl);
     p->launches += nl;
     if (s != RPA_OK) return s;
+    const char* dg = getenv("RPA_TC_CHI0_DIAG");
+    if (dg && dg[0] == '1') {
+      // the diagonal in FP64 (opt-in): chi_work is free until the eigensolve
+      StageTimer t(p, RPA_T_CHI0);
+      CU(p, rpa::launch_chi0_diagonal(A, dt, n_vc, q.n_g, p->sf0, p->sv, scale,
+                                      (double*)p->chi_work, 2 * (size_t)q.n_g * q.n_g, p->chi,
+                                      p->st));
+      p->launches += 2;
+    }
   } else {
     StageTimer t(p, RPA_T_CHI0);
     CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));

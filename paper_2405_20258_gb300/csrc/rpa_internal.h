@@ -118,6 +118,11 @@ cudaError_t launch_all_freq_weights(const double* delta, const double* ow, int n
 // every chi_s(w_k), so that the tensor-core rounding leaves Tr chi_s untouched.
 cudaError_t launch_chis_diagonal(const cplx* mt, int n_eig, int n_vc, const double* f,
                                  int n_freq, double scale, cplx* chis, cudaStream_t st);
+// chi[g][g] = scale sv[g]^2 sum_vc sf0[vc]^2 |A[vc][g]|^2 in FP64 (the mixed path's
+// chi~ diagonal); scratch holds up to 64 n_g doubles (fewer chunks if smaller).
+cudaError_t launch_chi0_diagonal(const void* A, int dtype, long n_vc, int n_g, const double* sf0,
+                                 const double* sv, double scale, double* scratch,
+                                 size_t scratch_doubles, cplx* chi, cudaStream_t st);
 // ec = (1/2pi) sum_k weight_k [sum_i log1p(-lam[k][i]) + trace_k]; bad |= 1 if 1 - lam <= 0.
 cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
                           const double* trace, const double* weight, double* ec, int* bad,

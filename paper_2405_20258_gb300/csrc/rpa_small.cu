@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "rpa_internal.h"
 
 namespace rpa {
@@ -396,6 +398,65 @@ cudaError_t launch_all_freq_weights(const double* delta, const double* ow, int n
                                     const double* omega, int n_freq, double* f, cudaStream_t st) {
   all_freq_weights_kernel<<<grid_for((long)n_freq * n_vc, 256), 256, 0, st>>>(delta, ow, n_vc,
                                                                               omega, n_freq, f);
+  return cudaGetLastError();
+}
+
+// FP64 diagonal of chi~(0), which the digit-sliced GEMM gets slightly wrong: it
+// multiplies only digit pairs s + t <= S - 1, and on the diagonal the dropped pairs
+// include |d_s|^2 terms of one sign, a bias that adds up over every transition.
+// part[c][g] = sum over the rows r of chunk c of sf0[r]^2 |A[r][g]|^2 (a thread per
+// g, coalesced along G); then chi[g][g] = scale sv[g]^2 sum_c part[c][g] in chunk
+// order (deterministic).
+__global__ void chi0_diag_partial_kernel(const void* A, int dtype, long n_vc, int n_g,
+                                         const double* sf0, long rows_per_chunk, double* part) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_g) return;
+  const long r0 = (long)blockIdx.y * rows_per_chunk;
+  const long r1 = min(n_vc, r0 + rows_per_chunk);
+  double acc = 0.0;
+  if (dtype == RPA_C64) {
+    const float2* a = (const float2*)A;
+    for (long r = r0; r < r1; ++r) {
+      const float2 v = a[r * n_g + g];
+      const double w = sf0[r], re = v.x, im = v.y;
+      acc = fma(w * w, fma(re, re, im * im), acc);
+    }
+  } else {
+    const double2* a = (const double2*)A;
+    for (long r = r0; r < r1; ++r) {
+      const double2 v = a[r * n_g + g];
+      const double w = sf0[r];
+      acc = fma(w * w, fma(v.x, v.x, v.y * v.y), acc);
+    }
+  }
+  part[(long)blockIdx.y * n_g + g] = acc;
+}
+
+__global__ void chi0_diag_finish_kernel(const double* part, int n_chunks, int n_g,
+                                        const double* sv, double scale, cplx* chi) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_g) return;
+  double t = 0.0;
+  for (int c = 0; c < n_chunks; ++c) t += part[(long)c * n_g + g];
+  const double s = sv[g];
+  chi[(long)g * n_g + g] = {scale * s * s * t, 0.0};
+}
+
+cudaError_t launch_chi0_diagonal(const void* A, int dtype, long n_vc, int n_g, const double* sf0,
+                                 const double* sv, double scale, double* scratch,
+                                 size_t scratch_doubles, cplx* chi, cudaStream_t st) {
+  if (n_g < 1 || n_vc < 1) return cudaSuccess;
+  // enough chunks to fill the GPU with a few thousand rows each, within the scratch
+  long chunks = std::min<long>(64, (n_vc + 1023) / 1024);
+  chunks = std::min<long>(chunks, (long)(scratch_doubles / (size_t)n_g));
+  if (chunks < 1) return cudaErrorInvalidValue;
+  const long rows = (n_vc + chunks - 1) / chunks;
+  const int nc = (int)((n_vc + rows - 1) / rows);
+  dim3 grid((n_g + 255) / 256, nc);
+  chi0_diag_partial_kernel<<<grid, 256, 0, st>>>(A, dtype, n_vc, n_g, sf0, rows, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  chi0_diag_finish_kernel<<<(n_g + 255) / 256, 256, 0, st>>>(scratch, nc, n_g, sv, scale, chi);
   return cudaGetLastError();
 }
 
