@@ -4,8 +4,8 @@ The digit-sliced GEMM multiplies only digit pairs s + t <= S - 1; on the diagona
 of chi~ = X^H X the dropped pairs include |d_s|^2 terms of one sign, so their
 omission is a bias that adds up over the transitions.  A CPU emulation of the
 GEMM at N_G = 4000 (N_eig = 400) puts the resulting |dE_c| at 1.9e-7 Ha with 4
-slices, and 4.7e-10 Ha (4 slices) or 4.7e-8 Ha (3 slices) with the diagonal
-recomputed in FP64.  Checked here: the diagonal against the oracle's, E_c against
+slices, and 4.7e-10 Ha (4 slices) or 4.7e-8 Ha (3 slices; 9.1e-7 at N_eig = 200)
+with the diagonal recomputed in FP64.  Checked here: the diagonal against the oracle's, E_c against
 the oracle at N_G = 400, and against the FP64 path at N_G = 4000 with 3 and 4
 slices.
 
