@@ -278,10 +278,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--route", default="eig", choices=["eig", "cholesky"])
+    ap.add_argument("--route", default="cholesky", choices=["eig", "cholesky"])
     ap.add_argument("--slices", default="4,6,3", help="digit slices of chi0, projection, chi_s")
-    ap.add_argument("--chi0-diag", action="store_true",
-                    help="mixed path: recompute chi~'s diagonal in FP64 after the sliced GEMM")
+    ap.add_argument("--no-chi0-diag", action="store_true",
+                    help="mixed path: keep the sliced GEMM's diagonal of chi~ (no FP64 recompute)")
     ap.add_argument("--eig", default="fp64", choices=["fp64", "mixed"],
                     help="eigensolver of chi~(0) on the mixed path: cuSOLVER FP64, or the opt-in "
                          "FP32-reduction / FP64-tridiagonal solver with one filtered step")
@@ -297,8 +297,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.eig == "mixed":
         os.environ["RPA_EIG_MIXED"] = "1"  # read by the library when a plan is created
-    if args.chi0_diag:
-        os.environ["RPA_TC_CHI0_DIAG"] = "1"  # read by the library at each chi~ stage
+    if args.no_chi0_diag:
+        os.environ["RPA_TC_CHI0_DIAG"] = "0"  # read by the library at each chi~ stage
     rank, world, local, dist = setup_dist(args)
     if args.impl == "reference":
         reference_arm(args, w, rank, dist)
@@ -527,7 +527,7 @@ def main():
         "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
                    "slices": list(slices) if mixed else None, "energy_route": args.route,
                    "eigensolver": args.eig if mixed else "fp64",
-                   "chi0_fp64_diagonal": bool(args.chi0_diag) if mixed else None,
+                   "chi0_fp64_diagonal": (not args.no_chi0_diag) if mixed else None,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
         "contraction_tflops": contraction_tflops,

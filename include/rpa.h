@@ -70,8 +70,10 @@ typedef enum {
 } rpa_precision;
 
 typedef enum {
-  RPA_ROUTE_EIG = 0,      /* eigenvalues of each chi_s(k): sum ln(1 - l) + l              */
-  RPA_ROUTE_CHOLESKY = 1  /* ln det(1 - chi_s) from a Cholesky factor + FP64 trace term     */
+  RPA_ROUTE_CHOLESKY = 0, /* default: ln det(1 - chi_s) = sum ln(1 - l) from a tiled FP64
+                             Cholesky factor + the FP64 trace term (the paper evaluates
+                             Tr ln through a factorisation)                               */
+  RPA_ROUTE_EIG = 1       /* eigenvalues of each chi_s(k): sum ln(1 - l) + l (cuSOLVER)   */
 } rpa_energy_route;
 
 typedef enum { RPA_C128 = 0, RPA_C64 = 1 } rpa_dtype;
@@ -147,7 +149,7 @@ typedef struct rpa_plan_s* rpa_plan_t;
 /* Create a plan for n_q q-points: validate, record the descriptors, allocate
  * workspace for the largest q-point, build the frequency grid on the device.
  * stream: a cudaStream_t (NULL = legacy default stream).  opt may be NULL
- * (FP64, eigenvalue route, s = 0.5).  On failure *out is NULL. */
+ * (FP64, Cholesky route, s = 0.5).  On failure *out is NULL. */
 rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q,
                            const rpa_options* opt, void* stream);
 rpa_status rpa_plan_destroy(rpa_plan_t plan);

@@ -58,6 +58,7 @@ struct rpa_plan_s {
   int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
   cplx *chi = nullptr, *chi_work = nullptr, *C = nullptr, *B = nullptr, *mt = nullptr;
   cplx *chis = nullptr, *chis_work = nullptr;
+  cplx* chol_inv = nullptr;   // inverses of the diagonal tiles of the tiled Cholesky
   void* gen_a = nullptr;      // device-drawn A for q-points with m == NULL
   int gen_iq = -1;            // which q-point gen_a currently holds
   void* sol_dev = nullptr;
@@ -136,7 +137,7 @@ void free_plan(rpa_plan_t p) {
                   p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
-                  p->infos, p->fall, p->order};
+                  p->infos, p->fall, p->order, p->chol_inv};
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
@@ -362,7 +363,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   if (!q || n_q < 1) return fail(nullptr, RPA_EINVAL, "need n_q >= 1 q-point descriptors");
   rpa_options o{};
   o.precision = RPA_FP64;
-  o.energy_route = RPA_ROUTE_EIG;
+  o.energy_route = RPA_ROUTE_CHOLESKY;
   o.omega_scale = 0.5;
   if (opt) o = *opt;
   if (!(o.omega_scale > 0.0)) o.omega_scale = 0.5;
@@ -425,6 +426,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   ALLOC(mt, E * V);
   ALLOC(chis, F * E * E);
   ALLOC(chis_work, F * E * E);
+  ALLOC(chol_inv, rpa::cholesky_scratch_count((int)F));
 #undef ALLOC
   if (need_gen) {
     cudaError_t e = cudaMalloc(&p->gen_a, gen_bytes);
@@ -593,8 +595,9 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
     p->launches += nl;
     if (s != RPA_OK) return s;
     const char* dg = getenv("RPA_TC_CHI0_DIAG");
-    if (dg && dg[0] == '1') {
-      // the diagonal in FP64 (opt-in): chi_work is free until the eigensolve
+    if (!(dg && dg[0] == '0')) {
+      // the diagonal in FP64 (RPA_TC_CHI0_DIAG=0 leaves the sliced GEMM's): the
+      // digit pairs the GEMM drops bias it; chi_work is free until the eigensolve
       StageTimer t(p, RPA_T_CHI0);
       CU(p, rpa::launch_chi0_diagonal(A, dt, n_vc, q.n_g, p->sf0, p->sv, scale,
                                       (double*)p->chi_work, 2 * (size_t)q.n_g * q.n_g, p->chi,
@@ -770,12 +773,14 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
   if (p->opt.energy_route == RPA_ROUTE_CHOLESKY) {
     {
       StageTimer t(p, RPA_T_EIGS);
+      int nl = 0;
       CU(p, rpa::launch_cholesky_logdet(p->chis_work, p->chis, E, F, p->logdet, p->flags + 1,
-                                        p->st));
+                                        p->chol_inv, p->st, &nl));
+      p->launches += nl;
     }
     StageTimer t(p, RPA_T_ENERGY);
     CU(p, rpa::launch_logdet_sum(p->logdet, F, p->trace, wt, p->ec, p->flags + 1, p->st));
-    p->launches += 2;
+    p->launches += 1;
   } else {
     {
       StageTimer t(p, RPA_T_EIGS);

@@ -130,9 +130,21 @@ cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
 // ec = (1/2pi) sum_k weight_k [logdet_k + trace_k]
 cudaError_t launch_logdet_sum(const double* logdet, int n_freq, const double* trace,
                               const double* weight, double* ec, int* bad, cudaStream_t st);
-// Batched in-place Cholesky of I - chis[k] and logdet[k] = 2 sum ln L_ii.
+// ---- tiled FP64 Cholesky (rpa_chol.cu) ----------------------------------------
+
+// Complex elements of the scratch `inv` that a factorisation of `batch` matrices needs.
+size_t cholesky_scratch_count(int batch);
+// In-place Cholesky A = L L^H of `batch` Hermitian positive definite n x n matrices
+// (row-major, stride n*n; the lower triangle is read and overwritten by L, the upper
+// triangle is not touched).  logdet[b] += 2 sum_i ln L_ii when logdet is not NULL;
+// bad |= 16 where a pivot is not > 0 (it is then taken as 1).  *launches += kernels.
+cudaError_t launch_cholesky_tiled(cplx* a, int n, int batch, double* logdet, int* bad, cplx* inv,
+                                  cudaStream_t st, int* launches);
+// work[k] = I - chis[k] (lower triangle), then its Cholesky factor and
+// logdet[k] = ln det(I - chis[k]) = 2 sum ln L_ii.
 cudaError_t launch_cholesky_logdet(cplx* work, const cplx* chis, int n, int batch,
-                                   double* logdet, int* bad, cudaStream_t st);
+                                   double* logdet, int* bad, cplx* inv, cudaStream_t st,
+                                   int* launches);
 cudaError_t launch_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,
                               int dtype, cudaStream_t st);
 

@@ -1,6 +1,6 @@
 // Small FP64 kernels of the RPA path: per-q scalars, the imaginary-frequency
 // quadrature, eigenvector gauge, the FP64 trace term, the energy reductions,
-// batched Cholesky log-determinants and the counter-based input generator.
+// and the counter-based input generator.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -270,54 +270,6 @@ __global__ void logdet_sum_kernel(const double* logdet, int n_freq, const double
   *ec = tot / (2.0 * kPi);
 }
 
-// One block per matrix: work = I - chis (Hermitian, row-major), right-looking
-// Cholesky of the lower triangle, logdet = 2 sum ln L_jj.
-__global__ void cholesky_logdet_kernel(cplx* work, const cplx* chis, int n, double* logdet,
-                                       int* bad) {
-  __shared__ double piv;
-  cplx* a = work + (size_t)blockIdx.x * n * n;
-  const cplx* x = chis + (size_t)blockIdx.x * n * n;
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
-    int i = (int)(e / n), j = (int)(e % n);
-    cplx v = x[e];
-    a[e] = {(i == j ? 1.0 : 0.0) - v.re, -v.im};
-  }
-  __syncthreads();
-  double ld = 0.0;
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double d = a[(size_t)j * n + j].re;
-      if (!(d > 0.0) || !isfinite(d)) {
-        atomicOr(bad, 16);
-        d = 1.0;
-      }
-      piv = sqrt(d);
-      a[(size_t)j * n + j] = {piv, 0.0};
-    }
-    __syncthreads();
-    const double p = piv;
-    if (threadIdx.x == 0) ld += 2.0 * log(p);
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      cplx& l = a[(size_t)i * n + j];
-      l.re /= p;
-      l.im /= p;
-    }
-    __syncthreads();
-    const int rem = n - j - 1;
-    for (long e = threadIdx.x; e < (long)rem * rem; e += blockDim.x) {
-      int i = j + 1 + (int)(e / rem), m = j + 1 + (int)(e % rem);
-      if (m > i) continue;
-      cplx li = a[(size_t)i * n + j], lm = a[(size_t)m * n + j];
-      cplx& t = a[(size_t)i * n + m];
-      // t -= li * conj(lm)
-      t.re -= li.re * lm.re + li.im * lm.im;
-      t.im -= li.im * lm.re - li.re * lm.im;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) logdet[blockIdx.x] = ld;
-}
-
 // ---- counter-based generator (splitmix64 of Steele, Lea and Flood 2014) ----
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -477,12 +429,6 @@ cudaError_t launch_logsum(const double* lam, int n_eig, int ld_lam, int n_freq,
 cudaError_t launch_logdet_sum(const double* logdet, int n_freq, const double* trace,
                               const double* weight, double* ec, int* bad, cudaStream_t st) {
   logdet_sum_kernel<<<1, 32, 0, st>>>(logdet, n_freq, trace, weight, ec, bad);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cholesky_logdet(cplx* work, const cplx* chis, int n, int batch,
-                                   double* logdet, int* bad, cudaStream_t st) {
-  cholesky_logdet_kernel<<<batch, 512, 0, st>>>(work, chis, n, logdet, bad);
   return cudaGetLastError();
 }
 

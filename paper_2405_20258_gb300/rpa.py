@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "librpa.so")
 
 RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_EEIG, RPA_ENUMERIC, RPA_ETIMEOUT, RPA_ESTATE = range(8)
 RPA_FP64, RPA_MIXED = 0, 1
-RPA_ROUTE_EIG, RPA_ROUTE_CHOLESKY = 0, 1
+RPA_ROUTE_CHOLESKY, RPA_ROUTE_EIG = 0, 1
 RPA_C128, RPA_C64 = 0, 1
 RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
 
@@ -175,7 +175,7 @@ def device_qpoint(qp, n_eig, n_freq, A=None, device="cuda", m_dtype=None, genera
 class Plan:
     """Owner of an ``rpa_plan_t``; methods mirror the C entry points."""
 
-    def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
+    def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_CHOLESKY, omega_scale=0.5,
                  stream=None, timing=False, slices=(0, 0, 0), debug_stall=0):
         lib = load()
         self.qpoints = list(qpoints)
@@ -245,7 +245,7 @@ class Plan:
 
 
 # names of the C ABI, for callers that prefer the flat form
-def rpa_plan_create(qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_EIG, omega_scale=0.5,
+def rpa_plan_create(qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_CHOLESKY, omega_scale=0.5,
                     stream=None, timing=False, slices=(0, 0, 0)):
     return Plan(qpoints, precision, energy_route, omega_scale, stream, timing, slices)
 

@@ -3,10 +3,14 @@ and return every intermediate on the host, and align eigenvector phases."""
 import numpy as np
 
 
-def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=False, m_dtype=None,
+def run_gpu(qp, A, n_eig, n_freq, precision=0, route="eig", keep=True, generate=False, m_dtype=None,
             slices=(0, 0, 0), **extra):
+    """route: "eig" (eigenvalues of every chi_s, returned as lam_k) or "cholesky"."""
     import torch
     from paper_2405_20258_gb300 import rpa
+
+    want_lam = route == "eig"
+    route = rpa.RPA_ROUTE_EIG if want_lam else rpa.RPA_ROUTE_CHOLESKY
 
     dq = rpa.device_qpoint(qp, n_eig, n_freq, A=None if generate else A,
                            m_dtype=m_dtype, **extra)
@@ -20,7 +24,7 @@ def run_gpu(qp, A, n_eig, n_freq, precision=0, route=0, keep=True, generate=Fals
         mt = torch.empty((n_eig, n_vc), dtype=torch.complex128, device=dev) if keep else None
         chis = torch.empty((n_freq, n_eig, n_eig), dtype=torch.complex128, device=dev) if keep else None
         tr = torch.empty(n_freq, dtype=torch.float64, device=dev) if keep else None
-        lam = torch.empty((n_freq, n_eig), dtype=torch.float64, device=dev) if keep and route == 0 else None
+        lam = torch.empty((n_freq, n_eig), dtype=torch.float64, device=dev) if keep and want_lam else None
         plan.chi0_static(0, chi)
         plan.subspace_basis(0, lam0, C)
         plan.chi_freq(0, mt, chis, tr)

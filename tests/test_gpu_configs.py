@@ -67,11 +67,13 @@ def test_uneven_batch_of_qpoints():
     with rpa.Plan(dqs, precision=rpa.RPA_MIXED) as p:
         ecs = p.ecorr(-1)
     assert all(np.isfinite(ecs)) and all(e < 0 for e in ecs)
-    small = sorted(range(len(sizes)), key=lambda i: sizes[i]["n_g"] * sizes[i]["n_c"])[:2]
-    with rpa.Plan([dqs[i] for i in small], precision=rpa.RPA_FP64) as p:
+    # every q-point against the FP64 path (its own plan: FP64 contractions)
+    with rpa.Plan(dqs, precision=rpa.RPA_FP64) as p:
         e64 = p.ecorr(-1)
-    for j, i in enumerate(small):
-        assert abs(ecs[i] - e64[j]) <= max(1e-6, 2e-13 * abs(e64[j])), (i, ecs[i], e64[j])
+    errs = [abs(a - b) for a, b in zip(ecs, e64)]
+    print("uneven batch, mixed vs FP64 |dE_c| (Ha) per q-point:", errs)
+    for i, e in enumerate(errs):
+        assert e <= 1e-6, (i, ecs[i], e64[i])
 
 
 def test_large_qpoint_subsample_against_oracle():
@@ -79,4 +81,4 @@ def test_large_qpoint_subsample_against_oracle():
     A = inputs.matrix_elements(qp)
     ref = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, 150, 48)["ec"]
     got = run_gpu(qp, A, 150, 48, precision=1, keep=False)["ec"]
-    assert abs(got - ref) <= 1e-6 + 1e-13 * abs(ref)
+    assert abs(got - ref) <= 1e-6

@@ -44,7 +44,7 @@ def check(qp, A, ow, vg, extra, n_eig, n_freq):
     assert np.max(np.abs(got["trace_k"] - ref["trace_k"]) / np.abs(ref["trace_k"])) < 1e-12
     lsc = np.max(np.abs(ref["lam_k"]))
     assert np.max(np.abs(np.sort(got["lam_k"], axis=1) - ref["lam_k"])) < 1e-11 * lsc
-    assert abs(got["ec"] - ref["ec"]) <= max(1e-8, 1e-12 * abs(ref["ec"]))
+    assert abs(got["ec"] - ref["ec"]) <= 1e-8
     return ref, got
 
 
@@ -78,7 +78,7 @@ def test_generated_kpoints_match_host_generator():
     qp, A, ow, vg, extra = ext_problem(70, 2, 15, n_k=2, occ=True, slab=False)
     ref = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, 20, 4, ow=ow)["ec"]
     got = run_gpu(qp, A, 20, 4, keep=False, generate=True, **extra)
-    assert abs(got["ec"] - ref) < 1e-12 * abs(ref)
+    assert abs(got["ec"] - ref) <= 1e-8
 
 
 def test_pair_weight_of_wrong_sign_is_rejected():

@@ -83,7 +83,7 @@ def test_complex64_input_mixed():
 def test_cholesky_route_mixed():
     qp, A = problem(160, 4, 30)
     ref = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, 40, 6)
-    mx = run_gpu(qp, A, 40, 6, precision=1, route=1, keep=False, slices=(7, 7, 7))
+    mx = run_gpu(qp, A, 40, 6, precision=1, route="cholesky", keep=False, slices=(7, 7, 7))
     assert abs(mx["ec"] - ref["ec"]) < 1e-11 * abs(ref["ec"])
 
 
