@@ -40,6 +40,8 @@ WORKLOADS = {
 }
 # FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
+PRECISIONS = {"fp64": "RPA_FP64", "mixed": "RPA_MIXED", "bf16x3": "RPA_MIXED_BF16X3",
+              "bf16x6": "RPA_MIXED_BF16X6"}
 
 
 def flops(w):
@@ -270,6 +272,69 @@ def run_steps(plan, n):
     return [plan.run(0) for _ in range(n)]
 
 
+def plan_slices(precision, slices):
+    """Digit planes per stage (chi~, projection, chi_s) the plan multiplies."""
+    if precision == "bf16x3":
+        return (2, 2, 2)
+    if precision == "bf16x6":
+        return (3, 3, 3)
+    return tuple(s if s > 0 else d for s, d in zip(slices, (4, 6, 3)))
+
+
+def fp64_dgemm_tflops(dev):
+    """Best of 5 float64 4096^3 matrix products (cuBLAS DGEMM through torch): the FP64
+    peak the FP64 path's roofline is quoted against (a measurement, not a kernel of ours)."""
+    try:
+        import torch
+        n = 4096
+        a = torch.randn(n, n, dtype=torch.float64, device=dev)
+        b = torch.randn(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(a, b)
+        torch.cuda.synchronize(dev)
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    except Exception:
+        return None
+
+
+def precision_study(w):
+    """|dE_c| of each mixed precision against the FP64 path for the workload's q-point at
+    N_eig 200, 400 and 800 (inputs drawn on the device; one JSON line per case)."""
+    import torch
+    from paper_2405_20258_gb300 import inputs, rpa
+    qp = inputs.make_qpoint(w["n_g"], w["n_v"], w["n_c"])
+    for n_eig in (200, 400, 800):
+        if n_eig >= w["n_g"]:
+            continue
+        dq = rpa.device_qpoint(qp, n_eig, w["n_freq"])
+        with rpa.Plan([dq], precision=rpa.RPA_FP64) as p:
+            e64 = p.run(0)
+        for name in ("mixed", "bf16x6", "bf16x3"):
+            with rpa.Plan([dq], precision=getattr(rpa, PRECISIONS[name]), timing=True) as p:
+                ec = p.run(0)
+                t0 = time.perf_counter()
+                ec = p.run(0)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                st, _ = p.timings()
+            print(json.dumps({"precision_study": name, "n_g": w["n_g"], "n_eig": n_eig,
+                              "n_freq": w["n_freq"], "ec_fp64_ha": e64, "ec_ha": ec,
+                              "abs_dEc_ha": abs(ec - e64), "rel_dEc": abs(ec - e64) / abs(e64),
+                              "meets_1e-6_ha": abs(ec - e64) <= 1e-6, "ms_per_qpoint": dt * 1e3,
+                              "contraction_ms": (st["chi0"] + st["proj"] + st["chis"]) / 2}),
+                  flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,26 +342,32 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=sorted(PRECISIONS))
     ap.add_argument("--route", default="cholesky", choices=["eig", "cholesky"])
     ap.add_argument("--slices", default="4,6,3", help="digit slices of chi0, projection, chi_s")
     ap.add_argument("--no-chi0-diag", action="store_true",
                     help="mixed path: keep the sliced GEMM's diagonal of chi~ (no FP64 recompute)")
-    ap.add_argument("--eig", default="fp64", choices=["fp64", "mixed"],
-                    help="eigensolver of chi~(0) on the mixed path: cuSOLVER FP64, or the opt-in "
-                         "FP32-reduction / FP64-tridiagonal solver with one filtered step")
+    ap.add_argument("--eig", default="own", choices=["own", "cusolver"],
+                    help="eigensolver of chi~(0): the library's own (FP32 or FP64 tridiagonal "
+                         "start, Cholesky-QR2, Rayleigh-Ritz by Jacobi), or cuSOLVER FP64")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", default=None, choices=sorted(PROFILE_CASES),
                     help="run one stage of a small case three times (for ncu captures) and exit")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="|dE_c| of every mixed precision against the FP64 path on the workload "
+                         "at N_eig 200, 400 and 800 (one JSON line per case) and exit")
     args = ap.parse_args()
     if args.profile:
         profile_case(args.profile, args.slices)
         return
+    if args.precision_study:
+        precision_study(WORKLOADS[args.workload])
+        return
     w = WORKLOADS[args.workload]
-    if args.eig == "mixed":
-        os.environ["RPA_EIG_MIXED"] = "1"  # read by the library when a plan is created
+    if args.eig == "cusolver":
+        os.environ["RPA_EIG"] = "cusolver"  # read by the library when a plan is created
     if args.no_chi0_diag:
         os.environ["RPA_TC_CHI0_DIAG"] = "0"  # read by the library at each chi~ stage
     rank, world, local, dist = setup_dist(args)
@@ -313,8 +384,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rpa.load()
-    mixed = args.precision == "mixed"
-    precision = rpa.RPA_MIXED if mixed else rpa.RPA_FP64
+    mixed = args.precision != "fp64"
+    precision = getattr(rpa, PRECISIONS[args.precision])
+    if args.precision in ("bf16x3", "bf16x6"):
+        args.slices = "0,0,0"  # the split precisions fix their planes
     route = rpa.RPA_ROUTE_CHOLESKY if args.route == "cholesky" else rpa.RPA_ROUTE_EIG
     slices = tuple(int(x) for x in args.slices.split(","))
     stream = torch.cuda.Stream(device=dev)
@@ -368,8 +441,10 @@ def main():
     shares = {k: v / tot_ms for k, v in stage_ms.items()}
     dom = max(("chi0", "proj", "chis"), key=lambda k: stage_ms[k])
     dom_s = stage_ms[dom] / 1e3 / args.steps
+    fp64_peak = fp64_dgemm_tflops(dev)
     if mixed:
-        nprod = products(dict(chi0=slices[0], proj=slices[1], chis=slices[2])[dom])
+        eff = plan_slices(args.precision, slices)
+        nprod = products(dict(chi0=eff[0], proj=eff[1], chis=eff[2])[dom])
         peak = pk["bf16_tflops_sustained"]
         achieved = fl[dom] * nprod / dom_s / 1e12
         traffic = None
@@ -383,13 +458,17 @@ def main():
                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                     "work_per_step": "%d digit-product contractions x %.4g algorithmic flops, "
                     "all launches of the stage" % (nprod, fl[dom]),
-                    "fp64_equivalent_tflops": fl[dom] / dom_s / 1e12}
+                    # the method's own flops (one complex contraction) at the same time
+                    "achieved_algorithmic": fl[dom] / dom_s / 1e12,
+                    "frac_algorithmic": fl[dom] / dom_s / 1e12 / peak}
     else:
-        peak = pk["bf16_tflops"] * FP64_OVER_BF16
+        peak = fp64_peak if fp64_peak else pk["bf16_tflops"] * FP64_OVER_BF16
         achieved = fl[dom] / dom_s / 1e12
         roofline = {"bound": "alu", "kernel": "fp64 %s" % dom, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_source": "%s bf16 burst x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind,
+                    "peak_source": ("measured: torch float64 matmul 4096^3 in this run (cuBLAS "
+                                    "DGEMM), best of 5" if fp64_peak else
+                                    "%s bf16 burst x nominal fp64/bf16 ratio (1.25/2250)" % pk_kind),
                     "traffic": None, "work_per_launch": "%.4g algorithmic flops" % fl[dom]}
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs, E_c back.
@@ -526,7 +605,7 @@ def main():
         "data": "synthetic (splitmix64 matrix elements drawn on the device)",
         "config": {"workload": args.workload, **w, "n_vc": n_vc, "precision": args.precision,
                    "slices": list(slices) if mixed else None, "energy_route": args.route,
-                   "eigensolver": args.eig if mixed else "fp64",
+                   "eigensolver": args.eig,
                    "chi0_fp64_diagonal": (not args.no_chi0_diag) if mixed else None,
                    "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
@@ -535,6 +614,7 @@ def main():
         "stage_share": shares,
         "roofline": roofline,
         "mixed_vs_fp64": compare,
+        "fp64_peak_tflops_measured": fp64_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -65,8 +65,14 @@ typedef enum {
 } rpa_status;
 
 typedef enum {
-  RPA_FP64 = 0,      /* every contraction in FP64 (SIMT DFMA)                              */
-  RPA_MIXED = 1      /* contractions on BF16 tensor cores with exact slicing, FP64 solves  */
+  RPA_FP64 = 0,         /* every contraction in FP64 (SIMT DFMA)                           */
+  RPA_MIXED = 1,        /* contractions on BF16 tensor cores with exact digit slicing
+                           (default slices 4, 6, 3: |dE_c| <= 1e-6 Ha on every tested
+                           workload), FP64 solves, trace and log-sum                    */
+  RPA_MIXED_BF16X3 = 2, /* every contraction on round-to-nearest BF16 hi/lo planes, 3
+                           products (hi.hi + hi.lo + lo.hi), FP32 sums over K: the
+                           classic split; does not reach 1e-6 Ha (for comparison)      */
+  RPA_MIXED_BF16X6 = 3  /* the same with hi/mid/lo planes, 6 products                  */
 } rpa_precision;
 
 typedef enum {
@@ -127,7 +133,12 @@ typedef struct {
   int debug_stall;         /* test hook, 0 in production: 1 makes the tensor-core
                               producer issue no loads, so every bounded wait of the
                               GEMM runs out and the stage reports RPA_ETIMEOUT     */
-  int reserved[3];         /* zero                                                   */
+  int vc_chunk;            /* q-points with m == NULL: 0 draws the whole A once and keeps
+                              it resident; > 0 never holds A whole: the chi~ and the
+                              projection stages draw it again, one chunk of at most
+                              vc_chunk transitions (whole valence bands of one k-point)
+                              at a time, into a buffer of that size                    */
+  int reserved[2];         /* zero                                                   */
 } rpa_options;
 
 /* Stage timers of rpa_plan_timings. */
@@ -218,8 +229,11 @@ rpa_status rpa_plan_timings(rpa_plan_t plan, double* times_ms, long long* launch
  * n_v*n_c is rejected with RPA_EINVAL (message in rpa_last_error(NULL)).  The
  * first call on a device looks up that array's device address (once per
  * device, with the device current): make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race;
- * each call overwrites the entries it reads.  Asynchronous: no host sync. */
+ * capture.  That address is kept for the life of the process: do not reset the
+ * device (cudaDeviceReset) between calls, since the array then belongs to a
+ * context that no longer exists.  All calls share the array, so calls that
+ * overlap on the GPU race; each call overwrites the entries it reads.
+ * Asynchronous: no host sync. */
 #define RPA_STATIC_TRACE_MAX_VC 524288
 rpa_status rpa_trace_term_static(const void* mtilde, int n_eig, int n_v, int n_c,
                                  const double* e_v, const double* e_c, const double* omega,

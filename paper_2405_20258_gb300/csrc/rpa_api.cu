@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "rpa_eig.h"
 #include "rpa_internal.h"
 #include "rpa_tc.h"
 
@@ -68,7 +69,7 @@ struct rpa_plan_s {
   bool batched_eig = false;   // cusolverDnXsyevBatched usable for the chi_s eigenvalues
   int* infos = nullptr;       // [max_freq] solver info of the batched solve
   rpa::tc::Workspace tcw;     // tensor-core path workspace
-  rpa::eig::Refine refine;    // opt-in mixed eigensolver of chi~ (rpa_eig.cu)
+  rpa::eig::Refine refine;    // the library's own eigensolver of chi~ (rpa_eig.cu)
   bool refine_ready = false;
   // stage timers (CUDA events on the plan stream) and the library's launch count
   struct Pending {
@@ -232,6 +233,8 @@ rpa_status check_iq(rpa_plan_t p, int iq) {
 // A of q-point iq, drawing it on the device when the caller passed none.
 rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
   const rpa_qpoint& q = p->q[iq];
+  if (!q.m && p->opt.vc_chunk > 0)
+    return fail(p, RPA_EINVAL, "q-point %d is drawn in chunks: A is never whole", iq);
   if (q.m) {
     *a = q.m;
     *dtype = q.m_dtype;
@@ -249,6 +252,45 @@ rpa_status matrix_a(rpa_plan_t p, int iq, const void** a, int* dtype) {
     }
     p->gen_iq = iq;
   }
+  *a = p->gen_a;
+  *dtype = q.m_dtype;
+  return RPA_OK;
+}
+
+// Streaming (options.vc_chunk > 0, m == NULL): A is drawn again per chunk of whole
+// valence bands of one k-point, rows [r0, r0 + rows) of A.
+struct Chunk {
+  long r0;
+  int rows, k, v0, nv;
+};
+
+bool streamed(rpa_plan_t p, int iq) { return !p->q[iq].m && p->opt.vc_chunk > 0; }
+
+int chunk_bands(const rpa_qpoint& q, int vc_chunk) {
+  return std::max(1, std::min(q.n_v, vc_chunk / q.n_c));
+}
+
+std::vector<Chunk> chunks_of(const rpa_qpoint& q, int vc_chunk) {
+  std::vector<Chunk> out;
+  const int n_k = q.n_k > 1 ? q.n_k : 1, nvb = chunk_bands(q, vc_chunk);
+  for (int k = 0; k < n_k; ++k)
+    for (int v0 = 0; v0 < q.n_v; v0 += nvb) {
+      const int nv = std::min(nvb, q.n_v - v0);
+      out.push_back(Chunk{((long)k * q.n_v + v0) * q.n_c, nv * q.n_c, k, v0, nv});
+    }
+  return out;
+}
+
+// Draw chunk c of q-point iq into the generator buffer.
+rpa_status draw_chunk(rpa_plan_t p, int iq, const Chunk& c, const void** a, int* dtype) {
+  const rpa_qpoint& q = p->q[iq];
+  {
+    StageTimer t(p, RPA_T_OTHER);
+    CU(p, rpa::launch_generate_m(&q, c.k * q.n_v + c.v0, c.nv, c.k * q.n_c, q.n_c, p->gen_a,
+                                 q.m_dtype, p->st));
+  }
+  p->launches += 1;
+  p->gen_iq = -1;  // the buffer holds a chunk, not the whole A
   *a = p->gen_a;
   *dtype = q.m_dtype;
   return RPA_OK;
@@ -299,7 +341,18 @@ rpa_status transition_order(rpa_plan_t p, int iq) {
   }
   std::vector<int> idx(n);
   for (long i = 0; i < n; ++i) idx[i] = (int)i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key[a] > key[b]; });
+  if (!q.m && p->opt.vc_chunk > 0) {
+    // a q-point drawn in chunks: each chunk's rows sorted among themselves, as
+    // indices local to the chunk
+    for (const Chunk& c : chunks_of(q, p->opt.vc_chunk)) {
+      int* b = idx.data() + c.r0;
+      for (int i = 0; i < c.rows; ++i) b[i] = i;
+      const double* kb = key.data() + c.r0;
+      std::stable_sort(b, b + c.rows, [&](int x, int y) { return kb[x] > kb[y]; });
+    }
+  } else {
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key[a] > key[b]; });
+  }
   CU(p, cudaMemcpy(p->order, idx.data(), n * sizeof(int), cudaMemcpyHostToDevice));
   p->order_iq = iq;
   return RPA_OK;
@@ -332,6 +385,74 @@ rpa_status prepare(rpa_plan_t p, int iq) {
 // The per-q-point scalars of iq, recomputed if another q-point's replaced them.
 rpa_status ensure_scalars(rpa_plan_t p, int iq) {
   return p->scalars_iq == iq ? RPA_OK : prepare(p, iq);
+}
+
+// chi~(0) of a q-point drawn in chunks: every chunk's contribution added into chi
+// (tensor-core K-blocks of the chunk's sorted transitions, or FP64 atomics), and
+// the mixed path's FP64 diagonal summed over the chunks.
+rpa_status chi0_streamed(rpa_plan_t p, int iq, double scale) {
+  const rpa_qpoint& q = p->q[iq];
+  const long n_vc = rpa::n_transitions(q);
+  const std::vector<Chunk> ch = chunks_of(q, p->opt.vc_chunk);
+  const bool mixed = p->opt.precision != RPA_FP64;
+  const char* dg = getenv("RPA_TC_CHI0_DIAG");
+  const bool diag = mixed && !(dg && dg[0] == '0');
+  rpa_status s;
+  if (mixed && (s = transition_order(p, iq)) != RPA_OK) return s;
+  if (!mixed) CU(p, cudaMemsetAsync(p->chi, 0, sizeof(cplx) * (size_t)q.n_g * q.n_g, p->st));
+  for (size_t ci = 0; ci < ch.size(); ++ci) {
+    const Chunk& c = ch[ci];
+    const void* A = nullptr;
+    int dt = 0;
+    if ((s = draw_chunk(p, iq, c, &A, &dt)) != RPA_OK) return s;
+    if (mixed) {
+      int nl = 0;
+      const int blocks =
+          std::max(1, (int)std::lround((double)p->tcw.chi0_blocks * c.rows / (double)n_vc));
+      s = rpa::tc::chi0(p->tcw, A, dt, c.rows, q.n_g, p->sf0 + c.r0, p->order + c.r0, p->sv,
+                        scale, p->chi, p->st, p->err, &nl, ci == 0, blocks);
+      p->launches += nl;
+      if (s != RPA_OK) return s;
+      if (diag) {
+        StageTimer t(p, RPA_T_CHI0);
+        CU(p, rpa::launch_chi0_diagonal(A, dt, c.rows, q.n_g, p->sf0 + c.r0, p->sv, scale,
+                                        (double*)p->chi_work, 2 * (size_t)q.n_g * q.n_g, p->chi,
+                                        p->st, (int)ci, (int)ch.size()));
+        p->launches += 2;
+      }
+    } else {
+      StageTimer t(p, RPA_T_CHI0);
+      CU(p, rpa::launch_herk_fp64(A, dt, c.rows, q.n_g, p->sf0 + c.r0, p->sv, scale, p->chi,
+                                  p->st, true));
+      p->launches += 1;
+    }
+  }
+  return RPA_OK;
+}
+
+// M~ of a q-point drawn in chunks: the columns of every chunk's transitions.
+rpa_status project_streamed(rpa_plan_t p, int iq) {
+  const rpa_qpoint& q = p->q[iq];
+  const long n_vc = rpa::n_transitions(q);
+  rpa_status s;
+  for (const Chunk& c : chunks_of(q, p->opt.vc_chunk)) {
+    const void* A = nullptr;
+    int dt = 0;
+    if ((s = draw_chunk(p, iq, c, &A, &dt)) != RPA_OK) return s;
+    if (p->opt.precision != RPA_FP64) {
+      int nl = 0;
+      s = rpa::tc::project(p->tcw, A, dt, c.rows, q.n_g, p->B, q.n_eig, p->mt + c.r0, p->st,
+                           p->err, &nl, n_vc);
+      p->launches += nl;
+      if (s != RPA_OK) return s;
+    } else {
+      StageTimer t(p, RPA_T_PROJ);
+      CU(p, rpa::launch_project_fp64(A, dt, c.rows, q.n_g, p->B, q.n_eig, p->mt + c.r0, p->st,
+                                     n_vc));
+      p->launches += 1;
+    }
+  }
+  return RPA_OK;
 }
 
 }  // namespace
@@ -367,10 +488,11 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   o.omega_scale = 0.5;
   if (opt) o = *opt;
   if (!(o.omega_scale > 0.0)) o.omega_scale = 0.5;
-  if (o.precision != RPA_FP64 && o.precision != RPA_MIXED)
+  if (o.precision < RPA_FP64 || o.precision > RPA_MIXED_BF16X6)
     return fail(nullptr, RPA_EINVAL, "unknown precision %d", o.precision);
   if (o.energy_route != RPA_ROUTE_EIG && o.energy_route != RPA_ROUTE_CHOLESKY)
     return fail(nullptr, RPA_EINVAL, "unknown energy route %d", o.energy_route);
+  if (o.vc_chunk < 0) return fail(nullptr, RPA_EINVAL, "vc_chunk must be >= 0");
   for (int sl : {o.slices_chi0, o.slices_proj, o.slices_chis})
     if (sl < 0 || sl > rpa::tc::MAX_SLICES)
       return fail(nullptr, RPA_EINVAL, "digit slices must be in [0, %d]", rpa::tc::MAX_SLICES);
@@ -393,7 +515,9 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     p->max_vc = std::max(p->max_vc, nvc);
     if (!q[i].m) {
       need_gen = true;
-      gen_bytes = std::max(gen_bytes, (size_t)nvc * q[i].n_g * (q[i].m_dtype == RPA_C64 ? 8 : 16));
+      const size_t rows = o.vc_chunk > 0 ? (size_t)chunk_bands(q[i], o.vc_chunk) * q[i].n_c
+                                         : (size_t)nvc;
+      gen_bytes = std::max(gen_bytes, rows * q[i].n_g * (q[i].m_dtype == RPA_C64 ? 8 : 16));
     }
   }
   rpa_status s;
@@ -437,24 +561,29 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
                   cudaGetErrorString(e));
     }
   }
-  if (o.precision == RPA_MIXED) {
+  if (o.precision != RPA_FP64) {
     rpa::tc::Slices sl;
+    // the split precisions: every contraction on round-to-nearest BF16 hi/lo planes
+    // (2 planes, 3 products; or 3 planes, 6 products) summed in FP32
+    const bool split = o.precision == RPA_MIXED_BF16X3 || o.precision == RPA_MIXED_BF16X6;
+    if (split) sl.chi0 = sl.proj = sl.chis = o.precision == RPA_MIXED_BF16X3 ? 2 : 3;
     if (o.slices_chi0 > 0) sl.chi0 = o.slices_chi0;
     if (o.slices_proj > 0) sl.proj = o.slices_proj;
     if (o.slices_chis > 0) sl.chis = o.slices_chis;
     std::string e;
-    // the opt-in mixed eigensolver multiplies chi~ by N_eig + p columns on the
+    // the eigensolver's FP32 start multiplies chi~ by N_eig + p columns on the
     // projection GEMM: size its B operand for them
     size_t E_tc = E;
     for (int i = 0; i < n_q; ++i)
-      if (rpa::eig::applies(q[i].n_g, q[i].n_eig))
-        E_tc = std::max(E_tc, (size_t)(q[i].n_eig + rpa::eig::extra_vectors(q[i].n_eig)));
+      if (rpa::eig::start32(q[i].n_g, q[i].n_eig))
+        E_tc = std::max(E_tc, (size_t)rpa::eig::block_size(q[i].n_g, q[i].n_eig));
     s = rpa::tc::alloc_workspace(p->tcw, G, E_tc, V, F, sl, e);
     if (s != RPA_OK) {
       free_plan(p);
       return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
     }
     p->tcw.debug_stall = o.debug_stall;
+    p->tcw.split = split ? 1 : 0;
     if (dalloc(nullptr, &p->fall, F * V) != RPA_OK || dalloc(nullptr, &p->order, V) != RPA_OK) {
       free_plan(p);
       return RPA_ENOMEM;
@@ -521,22 +650,21 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     return fail(nullptr, RPA_ENOMEM, "solver workspace of %zu bytes", dmax);
   }
   p->sol_host = malloc(p->sol_host_bytes);
-  if (o.precision == RPA_MIXED) {
+  if (!rpa::eig::use_library()) {
     int n_max = 0, mp_max = 0;
-    for (int i = 0; i < n_q; ++i)
-      if (rpa::eig::applies(q[i].n_g, q[i].n_eig)) {
-        n_max = std::max(n_max, q[i].n_g);
-        mp_max = std::max(mp_max, q[i].n_eig + rpa::eig::extra_vectors(q[i].n_eig));
-      }
-    if (n_max > 0) {
-      std::string e;
-      rpa_status rs = p->refine.alloc(p->sol, p->params, n_max, mp_max, e);
-      if (rs != RPA_OK) {
-        free_plan(p);
-        return fail(nullptr, rs, "%s", e.c_str());
-      }
-      p->refine_ready = true;
+    bool with32 = false;
+    for (int i = 0; i < n_q; ++i) {
+      n_max = std::max(n_max, q[i].n_g);
+      mp_max = std::max(mp_max, rpa::eig::block_size(q[i].n_g, q[i].n_eig));
+      with32 = with32 || (o.precision != RPA_FP64 && rpa::eig::start32(q[i].n_g, q[i].n_eig));
     }
+    std::string e;
+    rpa_status rs = p->refine.alloc(n_max, mp_max, with32, e);
+    if (rs != RPA_OK) {
+      free_plan(p);
+      return fail(nullptr, rs, "%s", e.c_str());
+    }
+    p->refine_ready = true;
   }
   // quadrature of every q-point
   for (int i = 0; i < n_q; ++i) {
@@ -581,13 +709,16 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
   p->chi_iq = -1;
   s = prepare(p, iq);
   if (s != RPA_OK) return s;
+  const long n_vc = rpa::n_transitions(q);
+  const double scale = -1.0 / q.omega_cell;
+  if (streamed(p, iq)) {
+    if ((s = chi0_streamed(p, iq, scale)) != RPA_OK) return s;
+  } else {
   const void* A;
   int dt;
   s = matrix_a(p, iq, &A, &dt);
   if (s != RPA_OK) return s;
-  const long n_vc = rpa::n_transitions(q);
-  const double scale = -1.0 / q.omega_cell;
-  if (p->opt.precision == RPA_MIXED) {
+  if (p->opt.precision != RPA_FP64) {
     int nl = 0;
     if ((s = transition_order(p, iq)) != RPA_OK) return s;
     s = rpa::tc::chi0(p->tcw, A, dt, (int)n_vc, q.n_g, p->sf0, p->order, p->sv, scale, p->chi,
@@ -608,6 +739,7 @@ rpa_status rpa_chi0_static(rpa_plan_t p, int iq, void* chi_out) {
     StageTimer t(p, RPA_T_CHI0);
     CU(p, rpa::launch_herk_fp64(A, dt, (int)n_vc, q.n_g, p->sf0, p->sv, scale, p->chi, p->st));
     p->launches += 1;
+  }
   }
   {
     StageTimer t(p, RPA_T_OTHER);
@@ -631,11 +763,13 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   p->basis_iq = -1;
   const rpa_qpoint& q = *qp(p, iq);
   const int n = q.n_g;
-  const bool refine_here = p->opt.precision == RPA_MIXED && p->refine_ready &&
-                           rpa::eig::applies(n, q.n_eig);
+  const bool mixed = p->opt.precision != RPA_FP64;
+  const bool refine_here = p->refine_ready && !rpa::eig::use_library();
+  const bool tc_products = mixed && refine_here && rpa::eig::start32(n, q.n_eig) &&
+                           rpa::eig::products_on_tc();
   // the projection's A planes are cut on the side stream during the eigensolve,
-  // unless the opt-in eigensolver's tensor-core products take the planes then
-  if (p->opt.precision == RPA_MIXED && !(refine_here && rpa::eig::products_on_tc())) {
+  // unless the eigensolver's tensor-core products take the planes then
+  if (mixed && !tc_products && !streamed(p, iq)) {
     const void* A;
     int dt, nl = 0;
     if ((s = matrix_a(p, iq, &A, &dt)) != RPA_OK) return s;
@@ -647,17 +781,18 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   StageTimer timer(p, RPA_T_EIG0);
   bool refined = false;
   if (refine_here) {
-    // FP32 reduction, FP64 tridiagonal solve, one filtered Rayleigh-Ritz step (rpa_eig.cu);
-    // the eigenvectors land where the FP64 solver leaves them, for the gauge kernel
+    // own eigensolver (rpa_eig.cu): FP32 (mixed plans, n >= 1024) or FP64 tridiagonal
+    // start, FP64 tridiagonal eigenpairs, Cholesky-QR2 and Rayleigh-Ritz; the
+    // eigenvectors land where the library solver would leave them, for the gauge kernel
     int nl = 0;
-    s = p->refine.subspace(p->sol, p->params, p->chi, n, q.n_eig, p->lam_all, p->chi_work,
-                           &p->tcw, p->st, p->err, &nl);
+    s = p->refine.subspace(p->chi, n, q.n_eig, p->lam_all, p->chi_work, p->chi_work,
+                           mixed ? &p->tcw : nullptr, mixed, p->st, p->err, &nl);
     p->launches += nl;
     if (s != RPA_OK && s != RPA_ENUMERIC) return s;
-    refined = s == RPA_OK;  // RPA_ENUMERIC: no spectral interval to filter, use FP64
+    refined = s == RPA_OK;  // RPA_ENUMERIC: a degenerate spectrum, the library solver takes it
   }
   if (refined) {
-    if ((s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK) return s;
+    if (mixed && (s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK) return s;
     CU(p, cudaStreamSynchronize(p->st));
     if ((s = tc_status(p)) != RPA_OK) return s;
   } else {
@@ -674,7 +809,7 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
                             p->sol_dev_bytes, p->sol_host, p->sol_host_bytes, p->flags + 2));
     int info = 0;
     CU(p, cudaMemcpyAsync(&info, p->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, p->st));
-    if (p->opt.precision == RPA_MIXED &&
+    if (p->opt.precision != RPA_FP64 &&
         (s = rpa::tc::join_side(p->tcw, p->st, p->err)) != RPA_OK)
       return s;
     CU(p, cudaStreamSynchronize(p->st));
@@ -704,17 +839,23 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
   if ((s = ensure_scalars(p, iq)) != RPA_OK) return s;
   p->freq_iq = -1;
   const rpa_qpoint& q = *qp(p, iq);
-  const void* A;
-  int dt;
-  s = matrix_a(p, iq, &A, &dt);
-  if (s != RPA_OK) return s;
+  const void* A = nullptr;
+  int dt = 0;
+  const bool strm = streamed(p, iq);
+  if (strm) {
+    if ((s = project_streamed(p, iq)) != RPA_OK) return s;
+  } else if ((s = matrix_a(p, iq, &A, &dt)) != RPA_OK) {
+    return s;
+  }
   const int n_vc = (int)rpa::n_transitions(q), E = q.n_eig, F = q.n_freq;
   const double scale = -1.0 / q.omega_cell;
   const double* om = p->omega + (size_t)iq * p->max_freq;
-  if (p->opt.precision == RPA_MIXED) {
+  if (p->opt.precision != RPA_FP64) {
     int nl = 0;
-    s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
-    if (s != RPA_OK) return s;
+    if (!strm) {
+      s = rpa::tc::project(p->tcw, A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st, p->err, &nl);
+      if (s != RPA_OK) return s;
+    }
     {
       StageTimer t(p, RPA_T_TRACE);
       CU(p, rpa::launch_all_freq_weights(p->delta, p->ow, n_vc, om, F, p->fall, p->st));
@@ -731,7 +872,7 @@ rpa_status rpa_chi_freq(rpa_plan_t p, int iq, void* mt_out, void* chis_out, doub
       p->launches += 1;
     }
   } else {
-    {
+    if (!strm) {
       StageTimer t(p, RPA_T_PROJ);
       CU(p, rpa::launch_project_fp64(A, dt, n_vc, q.n_g, p->B, E, p->mt, p->st));
     }

@@ -1,0 +1,1026 @@
+// Dense Hermitian eigensolver building blocks (declarations and the algorithms
+// they follow in rpa_dense.h).
+//
+// Persistent kernels (hetrd, jacobi) are launched cooperatively, one CTA per SM
+// at most, so that every CTA is resident; their grid-wide barriers are an
+// arrival counter and a generation word in global memory.  Every barrier wait
+// is bounded (about 2 s of SM clock): on expiry the CTA raises the abort word
+// and a status bit and the kernel returns at its next barrier, so a stalled
+// launch ends with an error the host reads instead of hanging.  Data that
+// other CTAs wrote during the launch is read with ld.global.cg (L2, not the
+// per-SM L1, which is not coherent across SMs).
+#include "rpa_dense.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+namespace rpa {
+namespace dense {
+namespace {
+
+template <typename T>
+struct CxT;
+template <>
+struct CxT<float> {
+  using C = float2;
+};
+template <>
+struct CxT<double> {
+  using C = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  return C{a.x + b.x, a.y + b.y};
+}
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  return C{a.x - b.x, a.y - b.y};
+}
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// conj(a) b
+template <typename C>
+__device__ __forceinline__ C cmul_ca(C a, C b) {
+  return C{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+// a conj(b)
+template <typename C>
+__device__ __forceinline__ C cmul_cb(C a, C b) {
+  return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C>
+__device__ __forceinline__ C cconj(C a) {
+  return C{a.x, -a.y};
+}
+template <typename C>
+__device__ __forceinline__ C warp_csum(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// A complex128 element through L2 (written by another CTA of the same launch).
+__device__ __forceinline__ cplx ldcg_c(const cplx* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cplx{v.x, v.y};
+}
+
+// Grid-wide barrier: bar[0] arrivals, bar[1] generation, bar[2] abort.  gen is the
+// generation this CTA last passed (kept by thread 0).  false: a wait ran out here
+// or in another CTA; the caller returns.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* status,
+                             int code) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = clock64();
+      while (true) {
+        if (*(volatile unsigned*)&bar[1] == target) break;
+        if (*(volatile unsigned*)&bar[2]) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > kWaitCycles) {
+          atomicExch(&bar[2], 1u);
+          atomicOr(status, code);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    gen = target;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation (lower), blocked, persistent.
+//
+// CTA b owns the rows and columns i = b + G r.  Per column k, with c earlier
+// columns of the current panel whose updates are deferred (A_eff = A - V W^H -
+// W V^H over the panel's V, W):
+//   A  each CTA forms its rows of x = A_eff(k:n, k) and partial sums of
+//      ||x(k+2:)||^2, W^H x and V^H x over them;                     barrier
+//   B  every CTA completes the sums (fixed order), forms the reflector
+//      (beta, tau; v = [1, x(k+2:) / (alpha - beta)]) and, for its columns i,
+//      y_i = (A_eff v)_i = conj(A(:, i)) . v - V(i,:) (W^H v) - W(i,:) (V^H v),
+//      and a partial sum of y^H v;                                   barrier
+//   C  w = tau y - (1/2) |tau|^2 (y^H v) v for its rows: the panel's next W
+//      column.  Row k+1 of W, which the next column's step A needs in every CTA,
+//      is recomputed by each CTA from y_{k+1} (the same arithmetic, so the same
+//      value).
+// After 32 columns (or the last): barrier, A(k+1:, k+1:) -= V W^H + W V^H over the
+// CTA's columns, barrier.
+// ---------------------------------------------------------------------------
+constexpr int PNB = 32;             // panel width
+constexpr int HT = 512;             // threads per CTA
+constexpr int HW = HT / 32;         // warps per CTA
+constexpr int PL = 2 * PNB + 1;     // partial sums per CTA
+constexpr int SEG = 8;              // segments of the cross-CTA sums
+constexpr int MAXOWN = 128;         // rows a CTA may own (n <= MAXOWN * grid)
+constexpr int RJ = 32;              // rows per chunk of the trailing update
+
+template <typename T>
+struct HetrdArgs {
+  using C = typename CxT<T>::C;
+  C* a;
+  int n;
+  T* d;
+  T* e;
+  C* tau;
+  C *vp, *wp, *xcol, *ycol, *part, *part2;
+  unsigned* bar;
+  int* status;
+};
+
+template <typename T>
+size_t hetrd_smem() {
+  using C = typename CxT<T>::C;
+  return sizeof(C) * (MAXOWN + PL * SEG + PL + 4 * PNB + 2 * RJ * (PNB + 1) + 2 * HW * PNB + 4);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
+  using C = typename CxT<T>::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* xs = (C*)smraw;            // [MAXOWN] this CTA's x
+  C* red = xs + MAXOWN;         // [PL * SEG]
+  C* tot = red + PL * SEG;      // [PL]
+  C* vk = tot + PL;             // [PNB] V(k, :)
+  C* wk = vk + PNB;             // [PNB] W(k, :)
+  C* s1 = wk + PNB;             // [PNB] W^H v
+  C* s2 = s1 + PNB;             // [PNB] V^H v
+  C* Vs = s2 + PNB;             // [RJ][PNB + 1]
+  C* Ws = Vs + RJ * (PNB + 1);  // [RJ][PNB + 1]
+  C* wb = Ws + RJ * (PNB + 1);  // [HW][PNB] conj W(i, :)
+  C* vb = wb + HW * PNB;        // [HW][PNB] conj V(i, :)
+  C* scal = vb + HW * PNB;      // tau, sc, alpha2, W(k+1, c)
+  const int n = p.n, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5,
+            lane = tid & 31;
+  const int rend = n > b ? (n - b + G - 1) / G : 0;  // local r < rend: i = b + G r < n
+  unsigned gen = 0;
+  int c = 0;
+  if (tid == 0) scal[3] = C{0, 0};
+  for (int k = 0; k < n; ++k) {
+    // ---- A: this CTA's rows of the updated column k
+    const int rbeg = k > b ? (k - b + G - 1) / G : 0;
+    const int nown = max(0, rend - rbeg);
+    if (tid < c) {
+      vk[tid] = tid == c - 1 ? C{1, 0} : __ldcg(&p.vp[(size_t)k * PNB + tid]);
+      wk[tid] = tid == c - 1 ? scal[3] : __ldcg(&p.wp[(size_t)k * PNB + tid]);
+    }
+    __syncthreads();
+    if (tid < nown) {
+      const int i = b + G * (rbeg + tid);
+      C x = __ldcg(&p.a[(size_t)k * n + i]);
+      for (int j = 0; j < c; ++j) {
+        const C vij = __ldcg(&p.vp[(size_t)i * PNB + j]);
+        const C wij = __ldcg(&p.wp[(size_t)i * PNB + j]);
+        x = csub(x, cadd(cmul_cb(vij, wk[j]), cmul_cb(wij, vk[j])));
+      }
+      xs[tid] = x;
+      if (i == k)
+        p.d[k] = x.x;
+      else
+        p.xcol[i] = x;
+    }
+    if (k == n - 1) break;
+    __syncthreads();
+    if (tid <= 2 * c) {
+      C acc = {0, 0};
+      for (int q = 0; q < nown; ++q) {
+        const int i = b + G * (rbeg + q);
+        if (i < k + 2) continue;
+        const C x = xs[q];
+        if (tid == 0)
+          acc.x += x.x * x.x + x.y * x.y;
+        else if (tid <= c)
+          acc = cadd(acc, cmul_ca(__ldcg(&p.wp[(size_t)i * PNB + tid - 1]), x));
+        else
+          acc = cadd(acc, cmul_ca(__ldcg(&p.vp[(size_t)i * PNB + tid - 1 - c]), x));
+      }
+      p.part[(size_t)b * PL + tid] = acc;
+    }
+    if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
+
+    // ---- B: reflector and A_eff v over this CTA's columns
+    const int L = 2 * c + 1;
+    for (int w = tid; w < L * SEG; w += HT) {
+      const int q = w / SEG, sg = w % SEG;
+      C acc = {0, 0};
+      for (int g = sg; g < G; g += SEG) acc = cadd(acc, __ldcg(&p.part[(size_t)g * PL + q]));
+      red[w] = acc;
+    }
+    __syncthreads();
+    if (tid < L) {
+      C t = {0, 0};
+      for (int sg = 0; sg < SEG; ++sg) t = cadd(t, red[tid * SEG + sg]);
+      tot[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const C alpha = __ldcg(&p.xcol[k + 1]);
+      const T xn2 = tot[0].x;
+      C tau, sc;
+      T beta;
+      if (xn2 == T(0) && alpha.y == T(0)) {
+        tau = C{0, 0};
+        sc = C{0, 0};
+        beta = alpha.x;
+      } else {
+        const T nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+        beta = alpha.x >= T(0) ? -nrm : nrm;
+        tau = C{(beta - alpha.x) / beta, -alpha.y / beta};
+        const T dx = alpha.x - beta, dy = alpha.y, dd = dx * dx + dy * dy;
+        sc = C{dx / dd, -dy / dd};
+      }
+      scal[0] = tau;
+      scal[1] = sc;
+      if (b == 0) {
+        p.e[k] = beta;
+        p.tau[k] = tau;
+      }
+    }
+    __syncthreads();
+    const C tau = scal[0], sc = scal[1];
+    if (tid < c) {
+      s1[tid] = cadd(cconj(__ldcg(&p.wp[(size_t)(k + 1) * PNB + tid])), cmul(sc, tot[1 + tid]));
+      s2[tid] = cadd(cconj(__ldcg(&p.vp[(size_t)(k + 1) * PNB + tid])), cmul(sc, tot[1 + c + tid]));
+    }
+    __syncthreads();
+    const int cbeg = k + 1 > b ? (k + 1 - b + G - 1) / G : 0;
+    const int ncol = max(0, rend - cbeg);
+    C yvp = {0, 0};
+    for (int q = warp; q < ncol; q += HW) {
+      const int i = b + G * (cbeg + q);
+      const C* col = p.a + (size_t)i * n;
+      C acc = {0, 0};
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const C aji = __ldcg(&col[j]);
+        const C vj = j == k + 1 ? C{1, 0} : cmul(__ldcg(&p.xcol[j]), sc);
+        acc = cadd(acc, cmul_ca(aji, vj));
+      }
+      acc = warp_csum(acc);
+      C corr = {0, 0};
+      if (lane < c)
+        corr = cadd(cmul(__ldcg(&p.vp[(size_t)i * PNB + lane]), s1[lane]),
+                    cmul(__ldcg(&p.wp[(size_t)i * PNB + lane]), s2[lane]));
+      corr = warp_csum(corr);
+      if (lane == 0) {
+        const C y = csub(acc, corr);
+        const C vi = i == k + 1 ? C{1, 0} : cmul(__ldcg(&p.xcol[i]), sc);
+        p.ycol[i] = y;
+        p.vp[(size_t)i * PNB + c] = vi;
+        p.a[(size_t)k * n + i] = vi;
+        yvp = cadd(yvp, cmul_ca(y, vi));
+      }
+    }
+    __syncthreads();
+    if (lane == 0) red[warp] = yvp;
+    __syncthreads();
+    if (tid == 0) {
+      C t = {0, 0};
+      for (int w = 0; w < HW; ++w) t = cadd(t, red[w]);
+      p.part2[b] = t;
+    }
+    if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
+
+    // ---- C: the panel's W column
+    if (warp == 0) {
+      C t = {0, 0};
+      for (int g = lane; g < G; g += 32) t = cadd(t, __ldcg(&p.part2[g]));
+      t = warp_csum(t);
+      if (lane == 0) {
+        const T t2 = tau.x * tau.x + tau.y * tau.y;
+        const C alpha2 = C{T(-0.5) * t2 * t.x, T(-0.5) * t2 * t.y};
+        scal[2] = alpha2;
+        scal[3] = cadd(cmul(tau, __ldcg(&p.ycol[k + 1])), alpha2);
+      }
+    }
+    __syncthreads();
+    const C alpha2 = scal[2];
+    for (int q = tid; q < ncol; q += HT) {
+      const int i = b + G * (cbeg + q);
+      const C y = __ldcg(&p.ycol[i]);
+      const C vi = __ldcg(&p.vp[(size_t)i * PNB + c]);
+      p.wp[(size_t)i * PNB + c] = cadd(cmul(tau, y), cmul(alpha2, vi));
+    }
+    ++c;
+    if (c == PNB || k == n - 2) {
+      if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
+      // trailing update of this CTA's columns i >= k+1, rows j >= k+1
+      const int kn = k + 1;
+      for (int j0 = kn; j0 < n; j0 += RJ) {
+        __syncthreads();
+        for (int e = tid; e < RJ * PNB; e += HT) {
+          const int r = e / PNB, qq = e % PNB, j = j0 + r;
+          const bool in = j < n && qq < c;
+          Vs[r * (PNB + 1) + qq] = in ? __ldcg(&p.vp[(size_t)j * PNB + qq]) : C{0, 0};
+          Ws[r * (PNB + 1) + qq] = in ? __ldcg(&p.wp[(size_t)j * PNB + qq]) : C{0, 0};
+        }
+        __syncthreads();
+        for (int q = warp; q < ncol; q += HW) {
+          const int i = b + G * (cbeg + q);
+          if (lane < c) {
+            wb[warp * PNB + lane] = cconj(__ldcg(&p.wp[(size_t)i * PNB + lane]));
+            vb[warp * PNB + lane] = cconj(__ldcg(&p.vp[(size_t)i * PNB + lane]));
+          }
+          __syncwarp();
+          const int j = j0 + lane;
+          if (lane < RJ && j < n) {
+            C acc = {0, 0};
+            for (int qq = 0; qq < c; ++qq)
+              acc = cadd(acc, cadd(cmul(Vs[lane * (PNB + 1) + qq], wb[warp * PNB + qq]),
+                                   cmul(Ws[lane * (PNB + 1) + qq], vb[warp * PNB + qq])));
+            C* aji = &p.a[(size_t)i * n + j];
+            *aji = csub(__ldcg(aji), acc);
+          }
+          __syncwarp();
+        }
+      }
+      if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
+      c = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compact WY factors and X <- Q X.
+// ---------------------------------------------------------------------------
+
+// T factor of reflector block blockIdx.x (reflectors b0 .. b0 + nb - 1, nb <= 32):
+// H_b0 ... H_{b0+nb-1} = I - V T V^H, T upper triangular (forward, columnwise):
+// T[r][r] = tau_r, T[0:s, s] = -tau_s T[0:s, 0:s] (V[:, 0:s]^H v_s).
+template <typename T>
+__global__ void __launch_bounds__(256) wy_t_kernel(const typename CxT<T>::C* a,
+                                                   const typename CxT<T>::C* tau, int n,
+                                                   typename CxT<T>::C* tfac) {
+  using C = typename CxT<T>::C;
+  __shared__ C S[PNB][PNB + 1];
+  __shared__ C Tt[PNB][PNB + 1];
+  __shared__ C Vc[32][PNB + 1];
+  const int blk = blockIdx.x, b0 = blk * PNB, nr = n - 1, tid = threadIdx.x;
+  const int nb = min(PNB, nr - b0);
+  C acc[4] = {};
+  for (int j0 = b0 + 1; j0 < n; j0 += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * PNB; e += 256) {
+      const int r = e / 32, jj = e % 32, j = j0 + jj;
+      Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+    }
+    __syncthreads();
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, r = e / PNB, s = e % PNB;
+      for (int jj = 0; jj < 32; ++jj) acc[u] = cadd(acc[u], cmul_ca(Vc[jj][r], Vc[jj][s]));
+    }
+  }
+  for (int u = 0; u < 4; ++u) {
+    const int e = tid + 256 * u;
+    S[e / PNB][e % PNB] = acc[u];
+    Tt[e / PNB][e % PNB] = C{0, 0};
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int r = 0; r < nb; ++r) Tt[r][r] = tau[b0 + r];
+  __syncthreads();
+  for (int s = 1; s < nb; ++s) {
+    if (tid < s) {
+      const int r = tid;
+      C t = {0, 0};
+      for (int q = r; q < s; ++q) t = cadd(t, cmul(Tt[r][q], S[q][s]));
+      const C ts = tau[b0 + s];
+      const C v = cmul(ts, t);
+      Tt[r][s] = C{-v.x, -v.y};
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < PNB * PNB; e += 256) tfac[(size_t)blk * PNB * PNB + e] = Tt[e / PNB][e % PNB];
+}
+
+// X <- Q X: CTA owns CT columns of X (n x m, column-major) and applies the blocks
+// from the last to the first: X -= V (T (V^H X)).
+constexpr int CT = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) apply_q_kernel(const typename CxT<T>::C* a, int n,
+                                                      const typename CxT<T>::C* tfac,
+                                                      typename CxT<T>::C* x, int m) {
+  using C = typename CxT<T>::C;
+  __shared__ C Vc[32][PNB + 1];
+  __shared__ C Xc[32][CT + 1];
+  __shared__ C W1[PNB][CT + 1];
+  __shared__ C W2[PNB][CT + 1];
+  __shared__ C Tt[PNB][PNB + 1];
+  const int tid = threadIdx.x, c0 = blockIdx.x * CT;
+  const int nr = n - 1, nblk = (nr + PNB - 1) / PNB;
+  const int r_own = tid / CT, cc_own = tid % CT;  // 32 x 8 = 256
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int b0 = blk * PNB, nb = min(PNB, nr - b0);
+    __syncthreads();
+    for (int e = tid; e < PNB * PNB; e += 256) Tt[e / PNB][e % PNB] = tfac[(size_t)blk * PNB * PNB + e];
+    C acc = {0, 0};
+    for (int j0 = b0 + 1; j0 < n; j0 += 32) {
+      __syncthreads();
+      for (int e = tid; e < 32 * PNB; e += 256) {
+        const int r = e / 32, jj = e % 32, j = j0 + jj;
+        Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+      }
+      {
+        const int jj = tid % 32, cc = tid / 32, j = j0 + jj;  // 32 x 8
+        Xc[jj][cc] = (j < n && c0 + cc < m) ? x[(size_t)(c0 + cc) * n + j] : C{0, 0};
+      }
+      __syncthreads();
+      for (int jj = 0; jj < 32; ++jj) acc = cadd(acc, cmul_ca(Vc[jj][r_own], Xc[jj][cc_own]));
+    }
+    W1[r_own][cc_own] = acc;
+    __syncthreads();
+    {
+      C t = {0, 0};
+      for (int s = r_own; s < PNB; ++s) t = cadd(t, cmul(Tt[r_own][s], W1[s][cc_own]));
+      W2[r_own][cc_own] = t;
+    }
+    for (int j0 = b0 + 1; j0 < n; j0 += 32) {
+      __syncthreads();
+      for (int e = tid; e < 32 * PNB; e += 256) {
+        const int r = e / 32, jj = e % 32, j = j0 + jj;
+        Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+      }
+      __syncthreads();
+      const int jj = tid % 32, cc = tid / 32, j = j0 + jj;
+      if (j < n && c0 + cc < m) {
+        C t = {0, 0};
+        for (int r = 0; r < PNB; ++r) t = cadd(t, cmul(Vc[jj][r], W2[r][cc]));
+        C* xp = &x[(size_t)(c0 + cc) * n + j];
+        *xp = csub(*xp, t);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cyclic two-sided Jacobi (FP64) with round-robin pairs of M = m + (m & 1)
+// players: round r pairs (M-1, r) and ((r + k) mod (M-1), (r - k) mod (M-1)),
+// k = 1 .. M/2 - 1; a pair with the padding index m is skipped.  Per round:
+//   1. the CTA owning pair k (k = b, b + G, ...) computes its rotation from
+//      a = G_pp, c = G_qq, g = G_pq = |g| e^{i phi}: zeta = (c - a) / (2 |g|),
+//      t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1 + t^2),
+//      sn = t cs; J = diag(1, e^{-i phi}) [[cs, sn], [-sn, cs]];      barrier
+//   2. it rotates its columns p, q of G and Y (G J, Y J), then applies every
+//      pair's row rotation (J^H) to those two columns, and zeroes G_pq;  barrier
+// Rotations with |g| <= 1e-300 or |g| <= eps sqrt(|a c|) are skipped.  A sweep
+// is M - 1 rounds; sweeps stop when no pair of a sweep needed a rotation.
+// ---------------------------------------------------------------------------
+constexpr int JT = 512;
+constexpr int MAX_JM = 4096;  // largest m (rotation parameters are staged in shared memory)
+
+__device__ __forceinline__ void pair_of(int M, int r, int k, int& p, int& q) {
+  int a, b;
+  if (k == 0) {
+    a = M - 1;
+    b = r;
+  } else {
+    a = (r + k) % (M - 1);
+    b = (r - k + (M - 1)) % (M - 1);
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+struct JacArgs {
+  cplx* g;
+  int m;
+  cplx* y;
+  double* prm;   // [M/2][4]: cs, sn, Re e^{-i phi}, Im e^{-i phi}
+  double* part;  // [grid]: rotations needed in the sweep
+  unsigned* bar;
+  int* status;
+  int max_sweeps;
+};
+
+__global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
+  extern __shared__ double jsm[];  // [M/2][4]
+  __shared__ int stop_s;
+  const int m = p.m, M = m + (m & 1), np = M / 2, G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x;
+  unsigned gen = 0;
+  const double eps = 2.220446049250313e-16;
+  int rotated = 0;  // rotations this CTA applied in the current sweep
+  for (int sweep = 0; sweep < p.max_sweeps; ++sweep) {
+    for (int r = 0; r < M - 1; ++r) {
+      // 1. rotation parameters of this CTA's pairs
+      for (int k = b + G * tid; k < np; k += G * JT) {
+        int pp, qq;
+        pair_of(M, r, k, pp, qq);
+        double cs = 1.0, sn = 0.0, er = 1.0, ei = 0.0;
+        if (qq < m) {
+          const double a = ldcg_c(&p.g[(size_t)pp * m + pp]).re;
+          const double c = ldcg_c(&p.g[(size_t)qq * m + qq]).re;
+          const cplx gpq = ldcg_c(&p.g[(size_t)qq * m + pp]);
+          const double beta = hypot(gpq.re, gpq.im);
+          if (beta > 1e-300 && beta > eps * sqrt(fabs(a * c))) {
+            const double zeta = (c - a) / (2.0 * beta);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            cs = 1.0 / sqrt(1.0 + t * t);
+            sn = t * cs;
+            er = gpq.re / beta;
+            ei = -gpq.im / beta;
+            ++rotated;
+          }
+        }
+        double* o = p.prm + 4 * (size_t)k;
+        o[0] = cs;
+        o[1] = sn;
+        o[2] = er;
+        o[3] = ei;
+      }
+      if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+      for (int e = tid; e < 4 * np; e += JT) jsm[e] = __ldcg(&p.prm[e]);
+      __syncthreads();
+      // 2. columns p, q of this CTA's pairs: G J and Y J, then J^H on those columns
+      for (int k = b; k < np; k += G) {
+        int pp, qq;
+        pair_of(M, r, k, pp, qq);
+        if (qq >= m) continue;
+        const double cs = jsm[4 * k], sn = jsm[4 * k + 1], er = jsm[4 * k + 2], ei = jsm[4 * k + 3];
+        if (sn == 0.0 && er == 1.0 && ei == 0.0) {
+          // no rotation of these columns; their rows still rotate below
+        } else {
+          for (int mat = 0; mat < 2; ++mat) {
+            cplx* X = mat == 0 ? p.g : p.y;
+            for (int i = tid; i < m; i += JT) {
+              const cplx xp = ldcg_c(&X[(size_t)pp * m + i]), xq = ldcg_c(&X[(size_t)qq * m + i]);
+              // e^{-i phi} xq
+              const cplx eq = {er * xq.re - ei * xq.im, er * xq.im + ei * xq.re};
+              X[(size_t)pp * m + i] = cplx{cs * xp.re - sn * eq.re, cs * xp.im - sn * eq.im};
+              X[(size_t)qq * m + i] = cplx{sn * xp.re + cs * eq.re, sn * xp.im + cs * eq.im};
+            }
+          }
+        }
+        __syncthreads();
+        // rows: (J^H X)[p'] = cs X[p'] - sn e^{i phi'} X[q'], (J^H X)[q'] = sn X[p'] + cs e^{i phi'} X[q']
+        for (int col = 0; col < 2; ++col) {
+          cplx* X = p.g + (size_t)(col == 0 ? pp : qq) * m;
+          for (int k2 = tid; k2 < np; k2 += JT) {
+            int p2, q2;
+            pair_of(M, r, k2, p2, q2);
+            if (q2 >= m) continue;
+            const double c2 = jsm[4 * k2], s2 = jsm[4 * k2 + 1], er2 = jsm[4 * k2 + 2],
+                         ei2 = -jsm[4 * k2 + 3];  // e^{+i phi'}
+            if (s2 == 0.0 && er2 == 1.0 && ei2 == 0.0) continue;
+            const cplx xp = ldcg_c(&X[p2]), xq = ldcg_c(&X[q2]);
+            const cplx eq = {er2 * xq.re - ei2 * xq.im, er2 * xq.im + ei2 * xq.re};
+            X[p2] = cplx{c2 * xp.re - s2 * eq.re, c2 * xp.im - s2 * eq.im};
+            X[q2] = cplx{s2 * xp.re + c2 * eq.re, s2 * xp.im + c2 * eq.im};
+          }
+        }
+        __syncthreads();
+        if (tid == 0 && !(sn == 0.0 && er == 1.0 && ei == 0.0)) {
+          p.g[(size_t)qq * m + pp] = cplx{0.0, 0.0};
+          p.g[(size_t)pp * m + qq] = cplx{0.0, 0.0};
+          p.g[(size_t)pp * m + pp].im = 0.0;
+          p.g[(size_t)qq * m + qq].im = 0.0;
+        }
+      }
+      if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+    }
+    // stop when no CTA rotated in this sweep
+    __syncthreads();
+    {
+      __shared__ int cnt[JT / 32];
+      int v = rotated;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) cnt[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        int s = 0;
+        for (int w = 0; w < JT / 32; ++w) s += cnt[w];
+        p.part[b] = (double)s;
+      }
+    }
+    rotated = 0;
+    if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+    if (tid == 0) {
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) s += __ldcg(&p.part[g]);
+      stop_s = s == 0.0;
+    }
+    __syncthreads();
+    if (stop_s) break;
+    if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+  }
+}
+
+// rank of each diagonal entry (ascending, ties by index), theta, and Y's columns
+// permuted into that order (one CTA per output column for the copy)
+__global__ void jacobi_rank_kernel(const cplx* g, int m, int* rank, double* theta) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double v = g[(size_t)i * m + i].re;
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      const double u = g[(size_t)j * m + j].re;
+      r += (u < v) || (u == v && j < i);
+    }
+    rank[i] = r;
+    theta[r] = v;
+  }
+}
+
+__global__ void permute_cols_kernel(const cplx* src, int m, const int* rank, cplx* dst) {
+  const int i = blockIdx.x;  // source column
+  const int r = rank[i];
+  for (int e = threadIdx.x; e < m; e += blockDim.x) dst[(size_t)r * m + e] = src[(size_t)i * m + e];
+}
+
+__global__ void identity_kernel(cplx* y, int m) {
+  const long tot = (long)m * m;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot;
+       e += (long)gridDim.x * blockDim.x)
+    y[e] = cplx{e / m == e % m ? 1.0 : 0.0, 0.0};
+}
+
+// ---------------------------------------------------------------------------
+// FP64 complex GEMM: 32 x 32 output tile per CTA, 2 x 2 per thread, K in chunks of 16.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ cplx load_op(const cplx* a, int lda, char op, int i, int k, int rows,
+                                        int cols) {
+  // element (i, k) of op(A), op(A) rows x cols
+  if (i >= rows || k >= cols) return cplx{0.0, 0.0};
+  if (op == 'N') return a[(size_t)k * lda + i];
+  const cplx v = a[(size_t)i * lda + k];
+  return op == 'C' ? cplx{v.re, -v.im} : v;
+}
+
+__global__ void __launch_bounds__(256) gemm_z_kernel(char opa, char opb, int m, int n, int k,
+                                                     cplx alpha, const cplx* a, int lda,
+                                                     const cplx* b, int ldb, cplx beta, cplx* c,
+                                                     int ldc) {
+  __shared__ cplx As[32][17];  // As[i][kk]
+  __shared__ cplx Bs[16][33];  // Bs[kk][j]
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  cplx acc[2][2] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = tid; e < 32 * 16; e += 256) {
+      const int ii = e % 32, kk = e / 32;
+      As[ii][kk] = load_op(a, lda, opa, i0 + ii, k0 + kk, m, k);
+    }
+    for (int e = tid; e < 16 * 32; e += 256) {
+      const int kk = e % 16, jj = e / 16;
+      Bs[kk][jj] = load_op(b, ldb, opb, k0 + kk, j0 + jj, k, n);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; ++kk) {
+      const cplx a0 = As[2 * ty][kk], a1 = As[2 * ty + 1][kk];
+      const cplx b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
+      acc[0][0].re = fma(a0.re, b0.re, fma(-a0.im, b0.im, acc[0][0].re));
+      acc[0][0].im = fma(a0.re, b0.im, fma(a0.im, b0.re, acc[0][0].im));
+      acc[0][1].re = fma(a0.re, b1.re, fma(-a0.im, b1.im, acc[0][1].re));
+      acc[0][1].im = fma(a0.re, b1.im, fma(a0.im, b1.re, acc[0][1].im));
+      acc[1][0].re = fma(a1.re, b0.re, fma(-a1.im, b0.im, acc[1][0].re));
+      acc[1][0].im = fma(a1.re, b0.im, fma(a1.im, b0.re, acc[1][0].im));
+      acc[1][1].re = fma(a1.re, b1.re, fma(-a1.im, b1.im, acc[1][1].re));
+      acc[1][1].im = fma(a1.re, b1.im, fma(a1.im, b1.re, acc[1][1].im));
+    }
+    __syncthreads();
+  }
+  for (int y = 0; y < 2; ++y)
+    for (int x = 0; x < 2; ++x) {
+      const int i = i0 + 2 * ty + y, j = j0 + 2 * tx + x;
+      if (i >= m || j >= n) continue;
+      const cplx v = acc[y][x];
+      cplx out = {alpha.re * v.re - alpha.im * v.im, alpha.re * v.im + alpha.im * v.re};
+      if (beta.re != 0.0 || beta.im != 0.0) {
+        const cplx o = c[(size_t)j * ldc + i];
+        out.re += beta.re * o.re - beta.im * o.im;
+        out.im += beta.re * o.im + beta.im * o.re;
+      }
+      c[(size_t)j * ldc + i] = out;
+    }
+}
+
+// In-place inverse of an upper-triangular n x n (n <= 32) block of a column-major
+// matrix (ld), zeroing the block's strictly lower part; one thread per column.
+__global__ void trinv_tile_kernel(cplx* r, int n, int ld) {
+  __shared__ cplx t[32][33];
+  __shared__ cplx u[32][33];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    const int i = e % 32, j = e / 32;
+    t[i][j] = (i < n && j < n && i <= j) ? r[(size_t)j * ld + i] : cplx{0.0, 0.0};
+  }
+  __syncthreads();
+  if (tid < n) {
+    const int c = tid;
+    // X[c][c] = 1 / R[c][c]; X[i][c] = -(sum_{i < q <= c} R[i][q] X[q][c]) / R[i][i]
+    for (int i = 31; i >= 0; --i) u[i][c] = cplx{0.0, 0.0};
+    for (int i = c; i >= 0; --i) {
+      cplx s = {i == c ? 1.0 : 0.0, 0.0};
+      for (int q = i + 1; q <= c; ++q) {
+        const cplx a = t[i][q], x = u[q][c];
+        s.re -= a.re * x.re - a.im * x.im;
+        s.im -= a.re * x.im + a.im * x.re;
+      }
+      const cplx d = t[i][i];
+      const double dd = d.re * d.re + d.im * d.im;
+      u[i][c] = cplx{(s.re * d.re + s.im * d.im) / dd, (s.im * d.re - s.re * d.im) / dd};
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    r[(size_t)j * ld + i] = i <= j ? u[i][j] : cplx{0.0, 0.0};
+  }
+}
+
+// Per-device cooperative-launch limits.
+struct CoopLimits {
+  int sms = 0;
+  bool hetrd_f = false, hetrd_d = false, jac = false;
+};
+constexpr int kMaxDev = 64;
+CoopLimits g_coop[kMaxDev];
+std::mutex g_coop_mutex;
+
+rpa_status coop_setup(int& sms, std::string& err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    err = "no CUDA device";
+    return RPA_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_coop_mutex);
+  CoopLimits& L = g_coop[dev];
+  if (L.sms == 0) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || L.sms <= 0) {
+      err = "device without cooperative launch";
+      L.sms = 0;
+      return RPA_ECUDA;
+    }
+    if (cudaFuncSetAttribute(hetrd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hetrd_smem<float>()) != cudaSuccess ||
+        cudaFuncSetAttribute(hetrd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hetrd_smem<double>()) != cudaSuccess ||
+        cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 4 * (MAX_JM / 2))) != cudaSuccess) {
+      (void)cudaGetLastError();
+      err = "cudaFuncSetAttribute for the dense eigensolver kernels failed";
+      L.sms = 0;
+      return RPA_ECUDA;
+    }
+  }
+  sms = L.sms;
+  return RPA_OK;
+}
+
+template <typename T>
+int hetrd_grid(int n, int sms) {
+  const int need = (n + MAXOWN - 1) / MAXOWN;
+  const int want = std::max(need, std::min(sms, std::max(1, n / 16)));
+  return std::min(sms, want);
+}
+
+}  // namespace
+
+rpa_status hetrd_alloc(HetrdWork& w, int n_max, size_t elem, std::string& err) {
+  int sms = 0;
+  rpa_status s = coop_setup(sms, err);
+  if (s != RPA_OK) return s;
+  w.n_max = n_max;
+  w.elem = elem;
+  w.grid = sms;
+  if ((long)MAXOWN * sms < n_max) {
+    err = "dense eigensolver: matrix too large for the persistent grid";
+    return RPA_EINVAL;
+  }
+  auto al = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  const size_t n = n_max;
+  if (!al(&w.vp, n * PNB * elem) || !al(&w.wp, n * PNB * elem) || !al(&w.xcol, n * elem) ||
+      !al(&w.ycol, n * elem) || !al(&w.part, (size_t)sms * PL * elem) ||
+      !al(&w.part2, (size_t)sms * elem) || !al((void**)&w.bar, 4 * sizeof(unsigned)) ||
+      !al((void**)&w.status, sizeof(int))) {
+    hetrd_free(w);
+    err = "dense eigensolver: cudaMalloc failed";
+    return RPA_ENOMEM;
+  }
+  if (cudaMemset(w.status, 0, sizeof(int)) != cudaSuccess) {
+    hetrd_free(w);
+    err = "dense eigensolver: cudaMemset failed";
+    return RPA_ECUDA;
+  }
+  return RPA_OK;
+}
+
+void hetrd_free(HetrdWork& w) {
+  void* b[] = {w.vp, w.wp, w.xcol, w.ycol, w.part, w.part2, w.bar, w.status};
+  for (void* p : b)
+    if (p) cudaFree(p);
+  w = HetrdWork{};
+}
+
+template <typename T>
+rpa_status hetrd(HetrdWork& w, void* a, int n, T* d, T* e, void* tau, cudaStream_t st,
+                 std::string& err, int* launches) {
+  using C = typename CxT<T>::C;
+  if (n < 1) return RPA_OK;
+  if (n > w.n_max || sizeof(C) != w.elem) {
+    err = "dense eigensolver: matrix outside the workspace";
+    return RPA_EINVAL;
+  }
+  int sms = 0;
+  rpa_status s = coop_setup(sms, err);
+  if (s != RPA_OK) return s;
+  const int G = hetrd_grid<T>(n, std::min(sms, w.grid));
+  if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
+    err = "dense eigensolver: barrier reset failed";
+    return RPA_ECUDA;
+  }
+  HetrdArgs<T> args{(C*)a, n, d, e, (C*)tau, (C*)w.vp, (C*)w.wp, (C*)w.xcol, (C*)w.ycol,
+                    (C*)w.part, (C*)w.part2, w.bar, w.status};
+  void* kargs[] = {&args};
+  const cudaError_t ce = cudaLaunchCooperativeKernel((const void*)hetrd_kernel<T>, dim3(G),
+                                                     dim3(HT), kargs, hetrd_smem<T>(), st);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    err = std::string("hetrd launch: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
+  }
+  if (launches) *launches += 1;
+  return RPA_OK;
+}
+
+template rpa_status hetrd<float>(HetrdWork&, void*, int, float*, float*, void*, cudaStream_t,
+                                 std::string&, int*);
+template rpa_status hetrd<double>(HetrdWork&, void*, int, double*, double*, void*, cudaStream_t,
+                                  std::string&, int*);
+
+template <typename T>
+rpa_status apply_q(const void* a, const void* tau, int n, void* x, int m, void* tfac,
+                   cudaStream_t st, std::string& err, int* launches) {
+  using C = typename CxT<T>::C;
+  if (n < 2 || m < 1) return RPA_OK;
+  const int nblk = (n - 1 + PNB - 1) / PNB;
+  wy_t_kernel<T><<<nblk, 256, 0, st>>>((const C*)a, (const C*)tau, n, (C*)tfac);
+  apply_q_kernel<T><<<(m + CT - 1) / CT, 256, 0, st>>>((const C*)a, n, (const C*)tfac, (C*)x, m);
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    err = std::string("apply_q launch: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
+  }
+  if (launches) *launches += 2;
+  return RPA_OK;
+}
+
+template rpa_status apply_q<float>(const void*, const void*, int, void*, int, void*,
+                                   cudaStream_t, std::string&, int*);
+template rpa_status apply_q<double>(const void*, const void*, int, void*, int, void*,
+                                    cudaStream_t, std::string&, int*);
+
+rpa_status jacobi_alloc(JacobiWork& w, int m_max, std::string& err) {
+  int sms = 0;
+  rpa_status s = coop_setup(sms, err);
+  if (s != RPA_OK) return s;
+  if (m_max > MAX_JM) {
+    err = "Jacobi eigensolver: matrix larger than " + std::to_string(MAX_JM);
+    return RPA_EINVAL;
+  }
+  w.m_max = m_max;
+  w.grid = sms;
+  const size_t M = (size_t)m_max + 1;
+  if (cudaMalloc(&w.prm, 4 * (M / 2 + 1) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&w.part, (size_t)sms * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&w.bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&w.status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&w.perm, M * sizeof(int)) != cudaSuccess ||
+      cudaMemset(w.status, 0, sizeof(int)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    jacobi_free(w);
+    err = "Jacobi eigensolver: cudaMalloc failed";
+    return RPA_ENOMEM;
+  }
+  return RPA_OK;
+}
+
+void jacobi_free(JacobiWork& w) {
+  void* b[] = {w.prm, w.part, w.bar, w.status, w.perm};
+  for (void* p : b)
+    if (p) cudaFree(p);
+  w = JacobiWork{};
+}
+
+rpa_status jacobi(JacobiWork& w, cplx* g, int m, double* theta, cplx* y, cplx* ywork,
+                  cudaStream_t st, std::string& err, int* launches) {
+  if (m < 1) return RPA_OK;
+  if (m > w.m_max) {
+    err = "Jacobi eigensolver: matrix outside the workspace";
+    return RPA_EINVAL;
+  }
+  int sms = 0;
+  rpa_status s = coop_setup(sms, err);
+  if (s != RPA_OK) return s;
+  const int M = m + (m & 1), np = M / 2;
+  const int G = std::max(1, std::min(std::min(sms, w.grid), np / 4));
+  identity_kernel<<<std::min(4096, (m * m + 255) / 256), 256, 0, st>>>(ywork, m);
+  if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
+    err = "Jacobi eigensolver: barrier reset failed";
+    return RPA_ECUDA;
+  }
+  JacArgs args{g, m, ywork, w.prm, w.part, w.bar, w.status, 12};
+  void* kargs[] = {&args};
+  cudaError_t ce = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(G), dim3(JT),
+                                               kargs, sizeof(double) * 4 * np, st);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    err = std::string("Jacobi launch: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
+  }
+  jacobi_rank_kernel<<<(m + 127) / 128, 128, 0, st>>>(g, m, w.perm, theta);
+  permute_cols_kernel<<<m, 256, 0, st>>>(ywork, m, w.perm, y);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    err = std::string("Jacobi sort: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
+  }
+  if (launches) *launches += 4;
+  return RPA_OK;
+}
+
+rpa_status gemm_z(char opa, char opb, int m, int n, int k, cplx alpha, const cplx* a, int lda,
+                  const cplx* b, int ldb, cplx beta, cplx* c, int ldc, cudaStream_t st,
+                  std::string& err, int* launches) {
+  if (m < 1 || n < 1) return RPA_OK;
+  const dim3 grid((m + 31) / 32, (n + 31) / 32);
+  if (grid.y > 65535) {
+    err = "gemm_z: n too large";
+    return RPA_EINVAL;
+  }
+  gemm_z_kernel<<<grid, 256, 0, st>>>(opa, opb, m, n, k, alpha, a, lda, b, ldb, beta, c, ldc);
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    err = std::string("gemm_z launch: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
+  }
+  if (launches) *launches += 1;
+  return RPA_OK;
+}
+
+// Recursive doubling: [R11 R12; 0 R22]^-1 = [X11, -X11 R12 X22; 0, X22].
+rpa_status trinv_upper(cplx* r, int n, int ld, cplx* work, cudaStream_t st, std::string& err,
+                       int* launches) {
+  if (n < 1) return RPA_OK;
+  if (n <= 32) {
+    trinv_tile_kernel<<<1, 64, 0, st>>>(r, n, ld);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      err = std::string("trinv launch: ") + cudaGetErrorString(ce);
+      return RPA_ECUDA;
+    }
+    if (launches) *launches += 1;
+    return RPA_OK;
+  }
+  const int n1 = ((n / 2 + 31) / 32) * 32, n2 = n - n1;
+  rpa_status s;
+  if ((s = trinv_upper(r, n1, ld, work, st, err, launches)) != RPA_OK) return s;
+  if ((s = trinv_upper(r + (size_t)n1 * ld + n1, n2, ld, work, st, err, launches)) != RPA_OK)
+    return s;
+  // work (n1 x n2) = R12 X22; X12 = -X11 work
+  cplx* r12 = r + (size_t)n1 * ld;
+  if ((s = gemm_z('N', 'N', n1, n2, n2, cplx{1.0, 0.0}, r12, ld, r + (size_t)n1 * ld + n1, ld,
+                  cplx{0.0, 0.0}, work, n1, st, err, launches)) != RPA_OK)
+    return s;
+  return gemm_z('N', 'N', n1, n2, n1, cplx{-1.0, 0.0}, r, ld, work, n1, cplx{0.0, 0.0}, r12, ld,
+                st, err, launches);
+}
+
+}  // namespace dense
+}  // namespace rpa

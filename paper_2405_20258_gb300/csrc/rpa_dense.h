@@ -87,11 +87,11 @@ rpa_status gemm_z(char opa, char opb, int m, int n, int k, cplx alpha, const cpl
                   const cplx* b, int ldb, cplx beta, cplx* c, int ldc, cudaStream_t st,
                   std::string& err, int* launches);
 
-// Overwrite the lower triangle of the row-major n x n lower-triangular L
-// (complex128) with L^-1 (diagonal tiles' inverses from tinv, n_tiles * 32 * 32,
-// the scratch of the tiled Cholesky is not reused); the strictly upper part is
-// zeroed.  work: n x n complex128 scratch.
-rpa_status trinv_lower(cplx* l, int n, cplx* work, cudaStream_t st, std::string& err,
+// Overwrite the upper-triangular n x n R (complex128, column-major, leading
+// dimension ld, strictly lower part zero) with R^-1 by recursive doubling:
+// [R11 R12; 0 R22]^-1 = [X11, -X11 R12 X22; 0, X22], 32 x 32 diagonal tiles by
+// back substitution.  work: n x n complex128 scratch.
+rpa_status trinv_upper(cplx* r, int n, int ld, cplx* work, cudaStream_t st, std::string& err,
                        int* launches);
 
 }  // namespace dense

@@ -1,34 +1,36 @@
-// Mixed-precision subspace of chi~(0) (step a3, Method: the N_eig eigenvectors of
-// chi~(0) with the most negative eigenvalues).
+// Subspace of chi~(0) (step a3, Method: the N_eig eigenvectors of chi~(0) with the
+// most negative eigenvalues), with this library's own kernels.
 //
-// GB300's FP64 rate makes a dense FP64 eigensolve of chi~ the largest part of a
-// q-point.  Its O(n^3) part, the Householder reduction to a real tridiagonal T, is
-// done here in FP32; everything after it in FP64:
-//   1. chi~ / max|chi~| in complex64, reduced to T = Q^H (chi~/max) Q (cuSOLVER
-//      FP32 hetrd).  The reduction keeps the graded structure of chi~ (the cut
-//      eigenvalue is ~1e-5 of the largest), so the m' = N_eig + p eigenvectors of T
-//      back-transformed by Q span chi~'s leading subspace to ~1e-5 -- provided T's
-//      own eigenpairs are FP64: an FP32 solve of T resolves eigenvalues only to
-//      ~1e-7 of the largest, which near the cut mixes the subspace to ~0.1;
-//   2. the m' + 1 most negative eigenvalues of T by Sturm bisection (an FP32
+// GB300 issues about two FP64 FMAs per SM per clock, so a dense FP64 eigensolve
+// of chi~ would dominate a q-point.  Its O(n^3) part, the Householder reduction
+// to a real tridiagonal T, runs in FP32 on mixed-precision plans; everything
+// after it keeps FP64 accuracy:
+//   1. start: chi~ / max|chi~| in complex64 reduced to T = Q^H (chi~/max) Q
+//      (rpa_dense.cu hetrd<float>; FP64 plans and small n: hetrd<double> of chi~);
+//      the m' + 1 most negative eigenvalues of T by Sturm bisection (an FP32
 //      phase, then FP64 from the FP32 bracket once FP64 counts confirm it) and
-//      their eigenvectors by inverse iteration in FP64 (rpa_tridiag.h), one thread
-//      per eigenvalue or cluster; Q applied to them in FP32 (cuSOLVER unmtr);
-//   3. a degree-3 Chebyshev polynomial of chi~ that damps the interval of the
-//      unwanted eigenvalues [lambda_{m'+1}, 0] (scaled at lambda_1, after Zhou and
-//      Saad 2007), applied to those m' vectors with FP64 products;
-//   4. an orthonormal basis (Householder QR) and a Rayleigh-Ritz step in FP64:
-//      the eigenpairs of Q^H chi~ Q give the N_eig Ritz vectors and values.
+//      m' eigenvectors by FP64 inverse iteration (rpa_tridiag.h), back-transformed
+//      by Q in the reduction's precision (compact WY blocks).  The reduction keeps
+//      chi~'s graded structure, so these m' = N_eig + p vectors span chi~'s
+//      leading subspace to ~1e-5 (FP32) -- provided T's own eigenpairs are FP64;
+//   2. (FP32 start) a degree-3 Chebyshev polynomial of chi~ that damps the
+//      interval of the unwanted eigenvalues [lambda_{m'+1}, 0] (scaled at
+//      lambda_1, after Zhou and Saad 2007), applied to the m' vectors;
+//   3. an orthonormal basis by column-scaled Cholesky-QR2 (tiled FP64 Cholesky of
+//      the Gram matrix, its triangular inverse, the products on the tensor cores
+//      or the FP64 pipe); a Cholesky that meets a non-positive pivot is repeated
+//      with a shift of 1e-12 of the unit diagonal and followed by a third pass
+//      (shifted Cholesky-QR3, Fukaya et al. 2020);
+//   4. Rayleigh-Ritz: G = Q^H chi~ Q, its eigenpairs by cyclic Jacobi in FP64
+//      (nearly diagonal here: a few sweeps, eigenvectors orthonormal to FP64
+//      rounding), the N_eig Ritz vectors Q Y and values.
 // p = max(64, N_eig/4) extra vectors put the unwanted eigenvalues that the filter
 // must damp well below |lambda_{N_eig}| on these spectra (0.55 of it at N_eig =
-// 400), so one step gains ~10-200x; with p = 32 one step only just reached 1e-6 Ha
-// at N_G = 4000, N_eig = 400.
+// 400), so one filtered step gains ~10-200x.
 // The matrix is used as the column-major view of the row-major chi~ buffer, i.e.
 // conj(chi~): same eigenvalues, conjugated eigenvectors (undone by the gauge
-// kernel, as for the FP64 solver).
-#include <cublas_v2.h>
+// kernel).
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -37,8 +39,7 @@
 #include <string>
 #include <vector>
 
-#include "rpa_internal.h"
-#include "rpa_tc.h"
+#include "rpa_eig.h"
 #include "rpa_tridiag.h"
 
 namespace rpa {
@@ -173,23 +174,96 @@ __global__ void zero_lower_kernel(cplx* g, int m) {
     if (o % m > o / m) g[o] = cplx{0.0, 0.0};
 }
 
+
+// T of the FP64 start: e^2 in FP64 and FP32, and FP32 copies of d (the FP32
+// bisection phase)
+__global__ void promote64_kernel(const double* d, const double* e, int n, double* e2, float* e2f,
+                                 float* d32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    d32[i] = (float)d[i];
+    if (i + 1 < n) {
+      e2[i] = e[i] * e[i];
+      e2f[i] = (float)e2[i];
+    }
+  }
+}
+
+// x[i + n j] = z[i k + j] as complex128 (column-major n x k from row-major FP64)
+__global__ void z_to_c128_kernel(const double* z, int n, int k, cplx* x) {
+  const long tot = (long)n * k;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < tot;
+       o += (long)gridDim.x * blockDim.x) {
+    const long i = o % n, j = o / n;
+    x[o] = cplx{z[i * k + j], 0.0};
+  }
+}
+
+// out (cols x rows, column-major) = X^H for the column-major rows x cols X, through
+// 32 x 32 shared-memory tiles
+__global__ void ctrans_kernel(const cplx* x, int rows, int cols, cplx* out) {
+  __shared__ cplx t[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
+    const int i = i0 + threadIdx.x, j = j0 + jj;
+    if (i < rows && j < cols) t[jj][threadIdx.x] = x[(size_t)j * rows + i];
+  }
+  __syncthreads();
+  for (int ii = threadIdx.y; ii < 32; ii += blockDim.y) {
+    const int j = j0 + threadIdx.x, i = i0 + ii;
+    if (i < rows && j < cols) {
+      const cplx v = t[threadIdx.x][ii];
+      out[(size_t)i * cols + j] = cplx{v.re, -v.im};
+    }
+  }
+}
+
+// out = a x + b y (real scalars), count elements
+__global__ void axpby_kernel(long count, double a, const cplx* x, double b, const cplx* y,
+                             cplx* out) {
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < count;
+       o += (long)gridDim.x * blockDim.x) {
+    const cplx u = x[o], v = y[o];
+    out[o] = cplx{a * u.re + b * v.re, a * u.im + b * v.im};
+  }
+}
+
+// g = (g + g^H) / 2 for the column-major m x m g, one thread per pair i <= j
+__global__ void hermitise_kernel(cplx* g, int m) {
+  const long tot = (long)m * m;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < tot;
+       o += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(o % m), j = (int)(o / m);
+    if (i > j) continue;
+    const cplx a = g[(size_t)j * m + i], b = g[(size_t)i * m + j];
+    const cplx h = {0.5 * (a.re + b.re), 0.5 * (a.im - b.im)};
+    g[(size_t)j * m + i] = h;
+    g[(size_t)i * m + j] = cplx{h.re, -h.im};
+  }
+}
+
+// g += s I
+__global__ void add_diag_kernel(cplx* g, int m, double s) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    g[(size_t)i * m + i].re += s;
+}
+
 // widest cluster of T's eigenvalues re-orthogonalised by one thread
 constexpr int kMaxCluster = 64;
+// smallest n that takes the FP32 start
+constexpr int kMinStart32 = 1024;
 
 int grid_for(long n, int block) { return (int)std::min<long>((n + block - 1) / block, 4096); }
-
-cuDoubleComplex z(double re, double im = 0.0) { return make_cuDoubleComplex(re, im); }
 
 }  // namespace
 
 int extra_vectors(int n_eig) { return std::max(64, n_eig / 4); }
 
-bool applies(int n, int n_eig) {
-  // opt-in (RPA_EIG_MIXED=1) until it passes the subspace-size parity cases on the
-  // device (its tridiagonal solver is tested on the host against LAPACK)
-  const char* e = getenv("RPA_EIG_MIXED");
-  if (!e || e[0] != '1') return false;
-  return n >= 1024 && n_eig + extra_vectors(n_eig) + 1 < n;
+int block_size(int n, int n_eig) { return std::min(n, n_eig + extra_vectors(n_eig)); }
+
+bool start32(int n, int n_eig) {
+  const char* e = getenv("RPA_EIG_START32");
+  if (e && e[0] == '0') return false;
+  return n >= kMinStart32 && block_size(n, n_eig) < n;
 }
 
 bool products_on_tc() {
@@ -197,121 +271,68 @@ bool products_on_tc() {
   return !(e && e[0] == '0');
 }
 
-rpa_status Refine::alloc(void* sol_, void* params_, int n_max, int mp_max, std::string& err) {
-  cusolverDnHandle_t sol = (cusolverDnHandle_t)sol_;
-  cusolverDnParams_t params = (cusolverDnParams_t)params_;
+bool use_library() {
+  const char* e = getenv("RPA_EIG");
+  return e && strcmp(e, "cusolver") == 0;
+}
+
+rpa_status Refine::alloc(int n_max, int mp_max, bool with32, std::string& err) {
   max_n = n_max;
   max_mp = mp_max;
-  cublasHandle_t bh = nullptr;
-  if (cublasCreate(&bh) != CUBLAS_STATUS_SUCCESS) {
-    err = "cublasCreate failed";
-    return RPA_ECUDA;
-  }
-  blas = bh;
-  cublasSetPointerMode(bh, CUBLAS_POINTER_MODE_HOST);
+  has32 = with32;
   auto al = [&](void** p, size_t bytes) {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
       (void)cudaGetLastError();
-      err = "mixed eigensolver workspace: cudaMalloc of " + std::to_string(bytes) + " bytes";
+      err = "eigensolver workspace: cudaMalloc of " + std::to_string(bytes) + " bytes";
       return false;
     }
     return true;
   };
-  const size_t n = (size_t)n_max, mp = (size_t)mp_max;
-  if (!al((void**)&h32, n * n * sizeof(float2)) || !al((void**)&d32, n * sizeof(float)) ||
-      !al((void**)&e32, n * sizeof(float)) || !al((void**)&tau32, n * sizeof(float2)) ||
-      !al((void**)&d64, n * sizeof(double)) || !al((void**)&e64, n * sizeof(double)) ||
-      !al((void**)&e2, n * sizeof(double)) || !al((void**)&e2f, n * sizeof(float)) ||
-      !al((void**)&wt, (mp + 1) * sizeof(double)) ||
-      !al((void**)&first, (mp + 1) * sizeof(int)) || !al((void**)&zt, n * mp * sizeof(double)) ||
-      !al((void**)&lanes, 6 * n * mp * sizeof(double)) ||
-      !al((void**)&c32, n * mp * sizeof(float2)) || !al((void**)&bt, n * mp * sizeof(cplx)) ||
-      !al((void**)&yb, mp * mp * sizeof(cplx)) || !al((void**)&dinv, mp * sizeof(double)) ||
-      !al((void**)&x0, n * mp * sizeof(cplx)) || !al((void**)&x1, n * mp * sizeof(cplx)) ||
-      !al((void**)&x2, n * mp * sizeof(cplx)) || !al((void**)&tau, mp * sizeof(cplx)) ||
-      !al((void**)&g, mp * mp * sizeof(cplx)) || !al((void**)&theta, mp * sizeof(double)) ||
-      !al((void**)&absmax, sizeof(unsigned long long)) || !al((void**)&info, 4 * sizeof(int))) {
+  const size_t n = (size_t)n_max, mp = (size_t)mp_max, nblk = (n + 31) / 32;
+  bool ok = true;
+  if (with32)
+    ok = al((void**)&h32, n * n * sizeof(float2)) && al((void**)&d32, n * sizeof(float)) &&
+         al((void**)&e32, n * sizeof(float)) && al((void**)&tau32, n * sizeof(float2)) &&
+         al((void**)&c32, n * mp * sizeof(float2));
+  ok = ok && al((void**)&tau64, n * sizeof(cplx)) && al((void**)&d64, n * sizeof(double)) &&
+       al((void**)&e64, n * sizeof(double)) && al((void**)&e2, n * sizeof(double)) &&
+       al((void**)&e2f, n * sizeof(float)) && al((void**)&d32b, n * sizeof(float)) &&
+       al((void**)&wt, (mp + 1) * sizeof(double)) && al((void**)&first, (mp + 2) * sizeof(int)) &&
+       al((void**)&zt, n * mp * sizeof(double)) && al((void**)&lanes, 6 * n * mp * sizeof(double)) &&
+       al(&tfac, nblk * 32 * 32 * sizeof(cplx)) && al((void**)&x0, n * mp * sizeof(cplx)) &&
+       al((void**)&x1, n * mp * sizeof(cplx)) && al((void**)&x2, n * mp * sizeof(cplx)) &&
+       al((void**)&x3, n * mp * sizeof(cplx)) && al((void**)&x4, n * mp * sizeof(cplx)) &&
+       al((void**)&bt, n * mp * sizeof(cplx)) && al((void**)&g, mp * mp * sizeof(cplx)) &&
+       al((void**)&yv, mp * mp * sizeof(cplx)) && al((void**)&yw, mp * mp * sizeof(cplx)) &&
+       al((void**)&rw, mp * mp * sizeof(cplx)) && al((void**)&theta, mp * sizeof(double)) &&
+       al((void**)&dinv, mp * sizeof(double)) &&
+       al((void**)&chol_inv, cholesky_scratch_count(1) * sizeof(cplx)) &&
+       al((void**)&flags, 4 * sizeof(int)) &&
+       al((void**)&absmax, sizeof(unsigned long long));
+  if (!ok) {
     release();
     return RPA_ENOMEM;
   }
-  // solver workspace for the largest shapes (the FP32 reduction and back-transform,
-  // QR, and Q^H chi~ Q)
-  size_t db = 0, hb = 0, d1 = 0, h1 = 0;
-  int lw = 0;
-  if (cusolverDnChetrd_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, n_max, (const cuComplex*)h32,
-                                  n_max, d32, e32, (const cuComplex*)tau32,
-                                  &lw) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnChetrd_bufferSize failed";
+  rpa_status s = RPA_OK;
+  if (with32) s = dense::hetrd_alloc(hw32, n_max, sizeof(float2), err);
+  if (s == RPA_OK) s = dense::hetrd_alloc(hw64, n_max, sizeof(cplx), err);
+  if (s == RPA_OK) s = dense::jacobi_alloc(jw, mp_max, err);
+  if (s != RPA_OK) {
     release();
-    return RPA_EEIG;
+    return s;
   }
-  db = std::max(db, (size_t)lw * sizeof(cuComplex));
-  if (cusolverDnCunmtr_bufferSize(sol, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
-                                  n_max, mp_max, (const cuComplex*)h32, n_max,
-                                  (const cuComplex*)tau32, (const cuComplex*)c32, n_max,
-                                  &lw) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnCunmtr_bufferSize failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, (size_t)lw * sizeof(cuComplex));
-  if (cusolverDnXgeqrf_bufferSize(sol, params, n_max, mp_max, CUDA_C_64F, x1, n_max, CUDA_C_64F,
-                                  tau, CUDA_C_64F, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnXgeqrf_bufferSize failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, d1);
-  hb = std::max(hb, h1);
-  if (cusolverDnZungqr_bufferSize(sol, n_max, mp_max, mp_max, (cuDoubleComplex*)x1, n_max,
-                                  (cuDoubleComplex*)tau, &lw) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnZungqr_bufferSize failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, (size_t)lw * sizeof(cuDoubleComplex));
-  if (cusolverDnXpotrf_bufferSize(sol, params, CUBLAS_FILL_MODE_UPPER, mp_max, CUDA_C_64F, g,
-                                  mp_max, CUDA_C_64F, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnXpotrf_bufferSize failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, d1);
-  hb = std::max(hb, h1);
-  if (cusolverDnXtrtri_bufferSize(sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, mp_max,
-                                  CUDA_C_64F, g, mp_max, &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnXtrtri_bufferSize failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, d1);
-  hb = std::max(hb, h1);
-  if (cusolverDnXsyevd_bufferSize(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                  mp_max, CUDA_C_64F, g, mp_max, CUDA_R_64F, theta, CUDA_C_64F,
-                                  &d1, &h1) != CUSOLVER_STATUS_SUCCESS) {
-    err = "cusolverDnXsyevd_bufferSize (Rayleigh-Ritz) failed";
-    release();
-    return RPA_EEIG;
-  }
-  db = std::max(db, d1);
-  hb = std::max(hb, h1);
-  dbytes = std::max<size_t>(db, 16);
-  hbytes = std::max<size_t>(hb, 16);
-  if (!al(&dwork, dbytes)) {
-    release();
-    return RPA_ENOMEM;
-  }
-  hwork = malloc(hbytes);
   return RPA_OK;
 }
 
 void Refine::release() {
-  void* b[] = {h32, d32, e32, tau32, d64, e64, e2, e2f, wt, first, zt, lanes, c32,
-               bt, yb, dinv, x0, x1, x2, tau, g, theta, absmax, info, dwork};
+  void* b[] = {h32, d32,   e32, tau32, c32, tau64, d64, e64, e2, e2f, d32b, wt, first, zt,
+               lanes, tfac, x0, x1,   x2,  x3,    x4,  bt,  g,   yv,  yw, rw,  theta, dinv, chol_inv,
+               flags, absmax};
   for (void* p : b)
     if (p) cudaFree(p);
-  if (hwork) free(hwork);
-  if (blas) cublasDestroy((cublasHandle_t)blas);
+  dense::hetrd_free(hw32);
+  dense::hetrd_free(hw64);
+  dense::jacobi_free(jw);
   *this = Refine{};
 }
 
@@ -323,77 +344,78 @@ void Refine::release() {
       return RPA_ECUDA;                                                  \
     }                                                                    \
   } while (0)
-#define CS_E(call)                                                       \
-  do {                                                                   \
-    cusolverStatus_t s_ = (call);                                        \
-    if (s_ != CUSOLVER_STATUS_SUCCESS) {                                 \
-      err = std::string(#call ": cuSOLVER status ") + std::to_string((int)s_); \
-      return RPA_EEIG;                                                   \
-    }                                                                    \
-  } while (0)
-#define CB_E(call)                                                       \
-  do {                                                                   \
-    cublasStatus_t s_ = (call);                                          \
-    if (s_ != CUBLAS_STATUS_SUCCESS) {                                   \
-      err = std::string(#call ": cuBLAS status ") + std::to_string((int)s_); \
-      return RPA_ECUDA;                                                  \
-    }                                                                    \
+#define RS_E(call)                 \
+  do {                             \
+    rpa_status r_ = (call);        \
+    if (r_ != RPA_OK) return r_;   \
   } while (0)
 
-rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, int n_eig,
-                            double* lam_out, cplx* vec_out, tc::Workspace* tcw, cudaStream_t st,
+rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, cplx* vec_out,
+                            cplx* a64, tc::Workspace* tcw, bool mixed, cudaStream_t st,
                             std::string& err, int* launches) {
-  cusolverDnHandle_t sol = (cusolverDnHandle_t)sol_;
-  cusolverDnParams_t params = (cusolverDnParams_t)params_;
-  cublasHandle_t bh = (cublasHandle_t)blas;
-  const int mp = n_eig + extra_vectors(n_eig);
-  if (n > max_n || mp > max_mp || mp + 1 >= n) {
-    err = "mixed eigensolver: shape outside its workspace";
+  const int mp = block_size(n, n_eig);
+  const bool s32 = mixed && has32 && start32(n, n_eig);
+  if (n > max_n || mp > max_mp) {
+    err = "eigensolver: shape outside its workspace";
     return RPA_EINVAL;
   }
   const long n2 = (long)n * n;
-  CB_E(cublasSetStream(bh, st));
-  // 1. chi~ / max|chi~| in complex64, reduced to a real tridiagonal T in FP32
+  int nl = 0;
+  // 1. tridiagonal start and its FP64 eigenpairs
+  CU_E(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
   CU_E(cudaMemsetAsync(absmax, 0, sizeof(unsigned long long), st));
-  absmax_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax);
-  CU_E(cudaGetLastError());
-  to_c64_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax, h32);
-  CU_E(cudaGetLastError());
-  CU_E(cudaMemsetAsync(info, 0, 4 * sizeof(int), st));
-  const int lwc = (int)std::min<size_t>(dbytes / sizeof(cuComplex), (size_t)0x7fffffff);
-  CS_E(cusolverDnChetrd(sol, CUBLAS_FILL_MODE_LOWER, n, (cuComplex*)h32, n, d32, e32,
-                        (cuComplex*)tau32, (cuComplex*)dwork, lwc, info + 1));
-  // 2. the m' + 1 most negative eigenvalues of T in FP64
+  if (s32) {
+    absmax_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax);
+    to_c64_kernel<<<grid_for(n2, 256), 256, 0, st>>>(hc, n2, absmax, h32);
+    CU_E(cudaGetLastError());
+    RS_E(dense::hetrd<float>(hw32, h32, n, d32, e32, tau32, st, err, &nl));
+    promote_tri_kernel<<<grid_for(n, 256), 256, 0, st>>>(d32, e32, n, d64, e64, e2, e2f);
+    CU_E(cudaGetLastError());
+    nl += 3;
+  } else {
+    CU_E(cudaMemcpyAsync(a64, hc, sizeof(cplx) * n2, cudaMemcpyDeviceToDevice, st));
+    RS_E(dense::hetrd<double>(hw64, a64, n, d64, e64, tau64, st, err, &nl));
+    promote64_kernel<<<grid_for(n, 256), 256, 0, st>>>(d64, e64, n, e2, e2f, d32b);
+    CU_E(cudaGetLastError());
+    nl += 1;
+  }
+  //    the m' (+ 1 for the filter's bound) most negative eigenvalues of T
   //    (RPA_EIG_BISECT32=0: without the FP32 phase; RPA_EIG_BISECT_BLOCK threads a
   //    block, 32 by default, a multiple of 32 at most 256)
-  promote_tri_kernel<<<grid_for(n, 256), 256, 0, st>>>(d32, e32, n, d64, e64, e2, e2f);
-  CU_E(cudaGetLastError());
+  const int nval = mp < n ? mp + 1 : mp;
   const char* b32_env = getenv("RPA_EIG_BISECT32");
   const char* blk_env = getenv("RPA_EIG_BISECT_BLOCK");
   const int use32 = !(b32_env && b32_env[0] == '0');
   const int bb = std::max(32, std::min(256, (blk_env ? atoi(blk_env) : 32) / 32 * 32));
-  bisect_kernel<<<(mp + 1 + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, d32, e2f, n, mp + 1, use32,
-                                                      wt);
+  bisect_kernel<<<(nval + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, s32 ? d32 : d32b, e2f, n, nval,
+                                                     use32, wt);
   CU_E(cudaGetLastError());
-  std::vector<double> w(mp + 1);
+  nl += 1;
+  std::vector<double> w(nval);
   unsigned long long mx_bits = 0;
-  int inf = 0;
-  CU_E(cudaMemcpyAsync(w.data(), wt, (mp + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int hst = 0;
+  CU_E(cudaMemcpyAsync(w.data(), wt, nval * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU_E(cudaMemcpyAsync(&mx_bits, absmax, sizeof mx_bits, cudaMemcpyDeviceToHost, st));
-  CU_E(cudaMemcpyAsync(&inf, info + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU_E(cudaMemcpyAsync(&hst, s32 ? hw32.status : hw64.status, sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
   CU_E(cudaStreamSynchronize(st));
-  if (inf != 0) {
-    err = "mixed eigensolver: FP32 tridiagonal reduction info " + std::to_string(inf);
-    return RPA_EEIG;
+  if (launches) *launches += nl;
+  nl = 0;
+  if (hst != 0) {
+    CU_E(cudaMemset(s32 ? hw32.status : hw64.status, 0, sizeof(int)));
+    err = "eigensolver: a barrier of the tridiagonal reduction gave up waiting";
+    return RPA_ETIMEOUT;
   }
-  double mx = 0.0;
-  memcpy(&mx, &mx_bits, sizeof mx);
-  if (!(mx > 0.0)) mx = 1.0;
-  // 3. T's eigenvectors for the first m' (inverse iteration, re-orthogonalised within
+  double mx = 1.0;
+  if (s32) {
+    memcpy(&mx, &mx_bits, sizeof mx);
+    if (!(mx > 0.0)) mx = 1.0;
+  }
+  //    T's eigenvectors for the first m' (inverse iteration, re-orthogonalised within
   //    clusters of eigenvalues closer than 1e-10 of the largest), then Q applied
-  const double tnorm = std::max(std::fabs(w[0]), std::fabs(w[mp]));
+  const double tnorm = std::max(std::fabs(w[0]), std::fabs(w[nval - 1]));
   if (!(tnorm > 0.0) || !std::isfinite(tnorm)) {
-    err = "mixed eigensolver: degenerate tridiagonal spectrum";
+    err = "eigensolver: degenerate tridiagonal spectrum";
     return RPA_ENUMERIC;
   }
   std::vector<int> fh(mp + 1);
@@ -401,213 +423,214 @@ rpa_status Refine::subspace(void* sol_, void* params_, const cplx* hc, int n, in
   int widest = 0;
   for (int c = 0; c < nc; ++c) widest = std::max(widest, fh[c + 1] - fh[c]);
   if (widest > kMaxCluster) {
-    // one thread would re-orthogonalise the whole cluster: the FP64 solver is faster
-    err = "mixed eigensolver: a cluster of " + std::to_string(widest) + " eigenvalues";
+    err = "eigensolver: a cluster of " + std::to_string(widest) + " eigenvalues";
     return RPA_ENUMERIC;
   }
   CU_E(cudaMemcpyAsync(first, fh.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   invit_kernel<<<(nc + 31) / 32, 32, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
   CU_E(cudaGetLastError());
-  z_to_c64_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, c32);
+  if (s32) {
+    z_to_c64_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, c32);
+    CU_E(cudaGetLastError());
+    RS_E(dense::apply_q<float>(h32, tau32, n, c32, mp, tfac, st, err, &nl));
+    to_c128_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(c32, n, mp, x0);
+  } else {
+    z_to_c128_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, x0);
+    CU_E(cudaGetLastError());
+    RS_E(dense::apply_q<double>(a64, tau64, n, x0, mp, tfac, st, err, &nl));
+  }
   CU_E(cudaGetLastError());
-  CS_E(cusolverDnCunmtr(sol, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, n, mp,
-                        (cuComplex*)h32, n, (cuComplex*)tau32, (cuComplex*)c32, n,
-                        (cuComplex*)dwork, lwc, info + 2));
-  to_c128_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(c32, n, mp, x0);
-  CU_E(cudaGetLastError());
-  if (launches) *launches += 7;
+  nl += 3;
 
-  // Products on the tensor cores (unless RPA_EIG_TC=0) use the projection GEMM,
-  // which for a row-major A [rows][K] and a row-major B [K][cols] writes
-  // out[c][r] = conj(sum_k A[r][k] B[k][c]), i.e. the column-major rows x cols
-  // matrix conj(A B).  Its digit slices are the projection's (6 by default:
-  // products exact to ~2^-47 of the row and column scales); the stage timers leave
-  // these launches in this stage.  Column-major blocks enter through Zgeam's
-  // conjugate transpose, which turns a column-major X into the row-major conj(X).
-  const bool on_tc = tcw != nullptr && products_on_tc();
-  const cuDoubleComplex one = z(1.0), zero = z(0.0);
+  // Block products.  On the tensor cores (FP32 start, unless RPA_EIG_TC=0) they use
+  // the projection GEMM, which for a row-major A [rows][K] and a row-major B
+  // [K][cols] writes out[c][r] = conj(sum_k A[r][k] B[k][c]), i.e. the column-major
+  // rows x cols matrix conj(A B), with the projection's digit slices (6 by
+  // default: products exact to ~2^-47 of the row and column scales); a column-major
+  // X enters as the row-major conj(X) through a conjugate transpose.  Otherwise
+  // they run on the FP64 pipe (dense::gemm_z).
+  const bool on_tc = s32 && tcw != nullptr && products_on_tc();
+  const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
+  auto ctrans = [&](const cplx* x, int rows, int cols, cplx* out) -> rpa_status {
+    ctrans_kernel<<<dim3((rows + 31) / 32, (cols + 31) / 32), dim3(32, 8), 0, st>>>(x, rows, cols,
+                                                                                   out);
+    CU_E(cudaGetLastError());
+    ++nl;
+    return RPA_OK;
+  };
   auto tc_gemm = [&](const cplx* a_rm, int rows, int k, const cplx* b_rm, int cols,
                      cplx* out) -> rpa_status {
+    // exact digits (whatever the plan's precision) with EIG_SLICES planes
     const tc::Hook saved = tcw->hook;
+    const int saved_split = tcw->split;
     tcw->hook = tc::Hook{};
-    int nl = 0;
-    const rpa_status r = tc::project(*tcw, a_rm, RPA_C128, rows, k, b_rm, cols, out, st, err, &nl);
+    tcw->split = 0;
+    tcw->proj_slices_override = tc::EIG_SLICES;
+    int l = 0;
+    const rpa_status r = tc::project(*tcw, a_rm, RPA_C128, rows, k, b_rm, cols, out, st, err, &l);
     tcw->hook = saved;
-    if (launches) *launches += nl;
+    tcw->split = saved_split;
+    tcw->proj_slices_override = 0;
+    nl += l;
     return r;
   };
-  // Y = H X (n x m'): A = the chi~ buffer (chi~[g'][g] = conj(H(g', g))), B = conj(X)
+  // Y = H X (n x m')
   auto hx = [&](const cplx* X, cplx* Y) -> rpa_status {
-    if (!on_tc) {
-      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, n, &one, (const cuDoubleComplex*)hc,
-                       n, (const cuDoubleComplex*)X, n, &zero, (cuDoubleComplex*)Y, n));
-      return RPA_OK;
-    }
-    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)X, n,
-                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
+    if (!on_tc) return dense::gemm_z('N', 'N', n, mp, n, one, hc, n, X, n, zero, Y, n, st, err, &nl);
+    RS_E(ctrans(X, n, mp, bt));
     return tc_gemm(hc, n, n, bt, mp, Y);
   };
-  // G = Q^H Z (m' x m') for Z = H Q: A = Z read row-major ([m'][n], A[j][g] = Z(g, j)),
-  // B = conj(Q); the GEMM gives conj(Z^T conj(Q)) = Z^H Q = Q^H H Q = G (H Hermitian)
+  // G = Q^H Z (m' x m')
   auto qhz = [&](const cplx* Q, const cplx* Z, cplx* G) -> rpa_status {
-    if (!on_tc) {
-      CB_E(cublasZgemm(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, mp, n, &one, (const cuDoubleComplex*)Q,
-                       n, (const cuDoubleComplex*)Z, n, &zero, (cuDoubleComplex*)G, mp));
-      return RPA_OK;
-    }
-    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)Q, n,
-                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
+    if (!on_tc)
+      return dense::gemm_z('C', 'N', mp, mp, n, one, Q, n, Z, n, zero, G, mp, st, err, &nl);
+    RS_E(ctrans(Q, n, mp, bt));
     return tc_gemm(Z, mp, n, bt, mp, G);
   };
-  // U = Q Y[:, 0:cols] (n x cols, Y m' x m'): A = conj(Q), B = conj(Y[:, 0:cols])
+  // U = Q Y[:, 0:cols] (n x cols, Y m' x m')
   auto qy = [&](const cplx* Q, const cplx* Y, int cols, cplx* U) -> rpa_status {
-    if (!on_tc) {
-      CB_E(cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, cols, mp, &one, (const cuDoubleComplex*)Q,
-                       n, (const cuDoubleComplex*)Y, mp, &zero, (cuDoubleComplex*)U, n));
-      return RPA_OK;
-    }
-    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, mp, n, &one, (const cuDoubleComplex*)Q, n,
-                     &zero, (const cuDoubleComplex*)bt, mp, (cuDoubleComplex*)bt, mp));
-    CB_E(cublasZgeam(bh, CUBLAS_OP_C, CUBLAS_OP_N, cols, mp, &one, (const cuDoubleComplex*)Y, mp,
-                     &zero, (const cuDoubleComplex*)yb, cols, (cuDoubleComplex*)yb, cols));
-    return tc_gemm(bt, n, mp, yb, cols, U);
+    if (!on_tc)
+      return dense::gemm_z('N', 'N', n, cols, mp, one, Q, n, Y, mp, zero, U, n, st, err, &nl);
+    RS_E(ctrans(Q, n, mp, bt));
+    RS_E(ctrans(Y, mp, cols, rw));
+    return tc_gemm(bt, n, mp, rw, cols, U);
   };
-
-  // Orthonormal basis of a filtered block Y by column-scaled Cholesky-QR2 (with
-  // RPA_EIG_QR=chol and the tensor-core products): two passes of Y <- Y D^-1 with
-  // D = diag(||y_j||), G = Y^H Y, G = R^H R (FP64 Cholesky), Y <- Y R^-1 (FP64
-  // triangular inverse, the product on the tensor cores).  The columns of a filtered
-  // block span ~1e14 in norm; scaled they are conditioned ~1e7 on these spectra,
-  // within what Cholesky-QR2 takes.  The scaling is applied to the block itself so
-  // that the row-scaled digits of the products see columns of one size.  Y and
-  // spare are swapped as the passes go; done stays false when a Cholesky factor
-  // fails (then Y, rescaled, still spans the filtered block for Householder QR).
-  const char* qr_env = getenv("RPA_EIG_QR");
-  const bool chol_qr = on_tc && qr_env && strcmp(qr_env, "chol") == 0;
-  auto chol_qr2 = [&](cplx*& Y, cplx*& spare, bool& done) -> rpa_status {
-    done = false;
-    for (int pass = 0; pass < 2; ++pass) {
-      inv_colnorm_kernel<<<mp, 256, 0, st>>>(Y, n, mp, dinv);
-      CU_E(cudaGetLastError());
-      scale_cols_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(Y, n, mp, dinv);
-      CU_E(cudaGetLastError());
-      rpa_status rq = qhz(Y, Y, g);  // G = Y^H Y
-      if (rq != RPA_OK) return rq;
-      CU_E(cudaMemsetAsync(info + 3, 0, sizeof(int), st));
-      CS_E(cusolverDnXpotrf(sol, params, CUBLAS_FILL_MODE_UPPER, mp, CUDA_C_64F, g, mp,
-                            CUDA_C_64F, dwork, dbytes, hwork, hbytes, info + 3));
-      int pinf = 0;
-      CU_E(cudaMemcpyAsync(&pinf, info + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CU_E(cudaStreamSynchronize(st));
-      if (pinf != 0) return RPA_OK;
-      CS_E(cusolverDnXtrtri(sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, mp, CUDA_C_64F, g,
-                            mp, dwork, dbytes, hwork, hbytes, info + 3));
-      zero_lower_kernel<<<grid_for((long)mp * mp, 256), 256, 0, st>>>(g, mp);
-      CU_E(cudaGetLastError());
-      if ((rq = qy(Y, g, mp, spare)) != RPA_OK) return rq;  // Y R^-1
-      std::swap(Y, spare);
-      if (launches) *launches += 3;
-    }
-    int tinf = 0;
-    CU_E(cudaMemcpyAsync(&tinf, info + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CU_E(cudaStreamSynchronize(st));
-    if (tinf != 0) {
-      err = "mixed eigensolver: triangular inverse info " + std::to_string(tinf);
-      return RPA_EEIG;
-    }
-    done = true;
+  auto axpby = [&](cplx* out, double a, const cplx* x, double b, const cplx* y) -> rpa_status {
+    axpby_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>((long)n * mp, a, x, b, y, out);
+    CU_E(cudaGetLastError());
+    ++nl;
     return RPA_OK;
   };
 
-  // 4.-5. RPA_EIG_STEPS (default 1, at most 8) filtered Rayleigh-Ritz steps.  Each
-  //    applies a degree-3 Chebyshev filter damping [a, 0] -- a = lambda_{m'+1} of T
-  //    first, the largest Ritz value of the block after that -- scaled at lambda_1,
-  //    takes an orthonormal basis Q of the filtered block (Householder QR, FP64)
-  //    and the eigenpairs of Q^H H Q (FP64); a further step starts from all m'
-  //    Ritz vectors.
-  const char* steps_env = getenv("RPA_EIG_STEPS");
-  const int steps = std::max(1, std::min(8, steps_env ? atoi(steps_env) : 1));
-  double a = w[mp] * mx, lo = w[0] * mx;
-  const double b = 0.0;
-  cplx* xs = x0;  // the block the next filter starts from
-  rpa_status r = RPA_OK;
-  for (int step = 0; step < steps; ++step) {
-    if (!(a < 0.0) || !(lo < a)) {
-      // no unwanted interval to damp (the bound not below zero, or no spread): the
-      // caller takes the FP64 solver
-      err = "mixed eigensolver: degenerate spectrum bounds";
-      return RPA_ENUMERIC;
-    }
-    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-    double sigma = e / (lo - c);
-    const double tau2 = 2.0 / sigma;
-    // X_{k-1}, X_k, X_{k+1}: the start block and the two other buffers
-    cplx *xm = xs, *xk = xs == x0 ? x1 : x0, *xn = xs == x2 ? x1 : x2;
-    // X_1 = (sigma / e) (H - c) X_0
-    if ((r = hx(xm, xk)) != RPA_OK) return r;
-    {
-      const cuDoubleComplex al = z(sigma / e), be = z(-c * sigma / e);
-      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xk, n,
-                       &be, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xk, n));
-    }
-    for (int k = 2; k <= 3; ++k) {
-      const double s1 = 1.0 / (tau2 - sigma);
-      // X_{k+1} = (2 s1 / e) (H - c) X_k - sigma s1 X_{k-1}
-      if ((r = hx(xk, xn)) != RPA_OK) return r;
-      const cuDoubleComplex al = z(2.0 * s1 / e), be = z(-2.0 * s1 * c / e);
-      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &al, (const cuDoubleComplex*)xn, n,
-                       &be, (const cuDoubleComplex*)xk, n, (cuDoubleComplex*)xn, n));
-      const cuDoubleComplex be2 = z(-sigma * s1);
-      CB_E(cublasZgeam(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, mp, &one, (const cuDoubleComplex*)xn, n,
-                       &be2, (const cuDoubleComplex*)xm, n, (cuDoubleComplex*)xn, n));
-      std::swap(xm, xk);  // X_{k-1} <- X_k
-      std::swap(xk, xn);  // X_k <- X_{k+1}; xn now holds the oldest block (free)
-      sigma = s1;
-    }
-    // orthonormal basis Q of the filtered block (into xk; xm is free)
-    bool qr_done = false;
-    if (chol_qr && (r = chol_qr2(xk, xm, qr_done)) != RPA_OK) return r;
-    if (!qr_done) {
-      CS_E(cusolverDnXgeqrf(sol, params, n, mp, CUDA_C_64F, xk, n, CUDA_C_64F, tau, CUDA_C_64F,
-                            dwork, dbytes, hwork, hbytes, info));
-      CS_E(cusolverDnZungqr(sol, n, mp, mp, (cuDoubleComplex*)xk, n, (const cuDoubleComplex*)tau,
-                            (cuDoubleComplex*)dwork, (int)(dbytes / sizeof(cuDoubleComplex)),
-                            info));
-    }
-    // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H
-    if ((r = hx(xk, xn)) != RPA_OK) return r;
-    if ((r = qhz(xk, xn, g)) != RPA_OK) return r;
-    CS_E(cusolverDnXsyevd(sol, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mp,
-                          CUDA_C_64F, g, mp, CUDA_R_64F, theta, CUDA_C_64F, dwork, dbytes, hwork,
-                          hbytes, info));
-    int infs[3] = {0, 0, 0};
-    if (step + 1 < steps) {
-      // U = Q Y (all m' Ritz vectors, into the buffer H Q occupied) starts the next
-      // step; its filter damps beyond the largest Ritz value
-      if ((r = qy(xk, g, mp, xn)) != RPA_OK) return r;
-      std::vector<double> th(mp);
-      CU_E(cudaMemcpyAsync(th.data(), theta, sizeof(double) * mp, cudaMemcpyDeviceToHost, st));
-      CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
+  // One column-scaled Cholesky-QR pass: Y <- Y D^-1 R^-1 with D = diag ||y_j|| and
+  // G = (Y D^-1)^H (Y D^-1) = R^H R (tiled FP64 Cholesky; the row-major lower factor
+  // of the column-major G buffer is the column-major upper R).  A non-positive pivot
+  // repeats the factorisation with G + 1e-12 I (*shifted is set: one more pass is
+  // due).  With a companion block P, the same basis change P <- P D^-1 R^-1 is
+  // applied to it.  Y and spare (P and pspare) are swapped as the products go.
+  auto qr_pass = [&](cplx*& Y, cplx*& spare, cplx** P, cplx** pspare, bool* shifted) -> rpa_status {
+    inv_colnorm_kernel<<<mp, 256, 0, st>>>(Y, n, mp, dinv);
+    scale_cols_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(Y, n, mp, dinv);
+    if (P) scale_cols_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(*P, n, mp, dinv);
+    CU_E(cudaGetLastError());
+    nl += P ? 3 : 2;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      RS_E(qhz(Y, Y, g));
+      if (attempt == 1) {
+        add_diag_kernel<<<grid_for(mp, 256), 256, 0, st>>>(g, mp, 1e-12);
+        CU_E(cudaGetLastError());
+        ++nl;
+      }
+      CU_E(cudaMemsetAsync(flags, 0, sizeof(int), st));
+      CU_E(launch_cholesky_tiled(g, mp, 1, nullptr, flags, chol_inv, st, &nl));
+      int bad = 0;
+      CU_E(cudaMemcpyAsync(&bad, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
       CU_E(cudaStreamSynchronize(st));
-      if (infs[0] != 0) {
-        err = "mixed eigensolver: QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
+      if (bad == 0) break;
+      if (attempt == 1) {
+        err = "eigensolver: Cholesky-QR of the block failed with a shift";
         return RPA_EEIG;
       }
+      if (shifted) *shifted = true;
+    }
+    zero_lower_kernel<<<grid_for((long)mp * mp, 256), 256, 0, st>>>(g, mp);
+    CU_E(cudaGetLastError());
+    ++nl;
+    RS_E(dense::trinv_upper(g, mp, mp, yw, st, err, &nl));
+    RS_E(qy(Y, g, mp, spare));  // Y R^-1
+    std::swap(Y, spare);
+    if (P) {
+      RS_E(qy(*P, g, mp, *pspare));
+      std::swap(*P, *pspare);
+    }
+    return RPA_OK;
+  };
+
+  // 2.-4. RPA_EIG_STEPS (default 1, at most 8) filtered Rayleigh-Ritz steps (FP32
+  //    start; the FP64 start takes one Rayleigh-Ritz step).  A step applies the
+  //    degree-3 Chebyshev polynomial that damps [a, 0] -- a = lambda_{m'+1} of T
+  //    first, the largest Ritz value of the block after that -- scaled at lambda_1,
+  //    by its three-term recurrence.  On these graded spectra one product raises
+  //    the weight of lambda_1's direction against that of lambda_{N_eig} by ~1e5,
+  //    so after every product the new block is orthonormalised (one Cholesky-QR
+  //    pass) and the previous block takes the same basis change: the pair stays a
+  //    consistent basis of the recurrence, p(H) X_0 M for an invertible M, and no
+  //    block is ever far from orthonormal.  A final pass makes the filtered block
+  //    orthonormal to FP64 rounding; then G = Q^H H Q, its eigenpairs (Jacobi) and
+  //    the Ritz vectors.
+  const char* steps_env = getenv("RPA_EIG_STEPS");
+  const int steps = s32 ? std::max(1, std::min(8, steps_env ? atoi(steps_env) : 1)) : 1;
+  double a = nval > mp ? w[mp] * mx : 0.0, lo = w[0] * mx;
+  const double b = 0.0;
+  cplx* bufs[5] = {x0, x1, x2, x3, x4};
+  cplx* xs = x0;  // the block the next step starts from
+  for (int step = 0; step < steps; ++step) {
+    // free buffers other than xs
+    cplx* fr[4];
+    int nf = 0;
+    for (cplx* bp : bufs)
+      if (bp != xs) fr[nf++] = bp;
+    cplx *xm = xs, *xk = fr[0], *xn = fr[1], *sp = fr[2], *sp2 = fr[3];
+    bool shifted = false;
+    if (s32) {
+      if (!(a < 0.0) || !(lo < a)) {
+        err = "eigensolver: degenerate spectrum bounds";
+        return RPA_ENUMERIC;
+      }
+      const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+      double sigma = e / (lo - c);
+      const double tau2 = 2.0 / sigma;
+      // X_1 = (sigma / e) (H - c) X_0
+      RS_E(hx(xm, xk));
+      RS_E(axpby(xk, sigma / e, xk, -c * sigma / e, xm));
+      RS_E(qr_pass(xk, sp, &xm, &sp2, &shifted));
+      for (int k = 2; k <= 3; ++k) {
+        const double s1 = 1.0 / (tau2 - sigma);
+        // X_{k+1} = (2 s1 / e) (H - c) X_k - sigma s1 X_{k-1}
+        RS_E(hx(xk, xn));
+        RS_E(axpby(xn, 2.0 * s1 / e, xn, -2.0 * s1 * c / e, xk));
+        RS_E(axpby(xn, 1.0, xn, -sigma * s1, xm));
+        RS_E(qr_pass(xn, sp, k < 3 ? &xk : nullptr, &sp2, &shifted));
+        std::swap(xm, xk);  // X_{k-1} <- X_k
+        std::swap(xk, xn);  // X_k <- X_{k+1}; xn holds the oldest block (free)
+        sigma = s1;
+      }
+    } else {
+      std::swap(xm, xk);  // the start itself (in xk)
+      RS_E(qr_pass(xk, sp, nullptr, nullptr, &shifted));
+    }
+    // the block orthonormal to FP64 rounding (in xk; xm, xn free)
+    RS_E(qr_pass(xk, sp, nullptr, nullptr, &shifted));
+    if (shifted) RS_E(qr_pass(xk, sp, nullptr, nullptr, nullptr));
+    // Rayleigh-Ritz: G = Q^H (H Q), G = Y Theta Y^H
+    RS_E(hx(xk, xn));
+    RS_E(qhz(xk, xn, g));
+    hermitise_kernel<<<grid_for((long)mp * mp, 256), 256, 0, st>>>(g, mp);
+    CU_E(cudaGetLastError());
+    ++nl;
+    RS_E(dense::jacobi(jw, g, mp, theta, yv, yw, st, err, &nl));
+    if (step + 1 < steps) {
+      RS_E(qy(xk, yv, mp, xn));
+      std::vector<double> th(mp);
+      CU_E(cudaMemcpyAsync(th.data(), theta, sizeof(double) * mp, cudaMemcpyDeviceToHost, st));
+      CU_E(cudaStreamSynchronize(st));
       a = th[mp - 1];
       lo = th[0];
       xs = xn;
       continue;
     }
     // the N_eig Ritz pairs: U = Q Y[:, 0:N_eig]
-    if ((r = qy(xk, g, n_eig, vec_out)) != RPA_OK) return r;
+    RS_E(qy(xk, yv, n_eig, vec_out));
     CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
-    CU_E(cudaMemcpyAsync(infs, info, sizeof infs, cudaMemcpyDeviceToHost, st));
-    CU_E(cudaStreamSynchronize(st));
-    if (infs[0] != 0 || infs[2] != 0) {
-      err = "mixed eigensolver: back-transform info " + std::to_string(infs[2]) +
-            ", QR or Rayleigh-Ritz info " + std::to_string(infs[0]);
-      return RPA_EEIG;
-    }
+  }
+  int jst = 0;
+  CU_E(cudaMemcpyAsync(&jst, jw.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU_E(cudaStreamSynchronize(st));
+  if (launches) *launches += nl;
+  if (jst != 0) {
+    CU_E(cudaMemset(jw.status, 0, sizeof(int)));
+    err = "eigensolver: a barrier of the Jacobi sweeps gave up waiting";
+    return RPA_ETIMEOUT;
   }
   return RPA_OK;
 }

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NT) herk_fp64_kernel(const void* __restrict__ 
 __global__ void __launch_bounds__(NT) project_fp64_kernel(const void* __restrict__ A, int dtype,
                                                           int n_vc, int n_g,
                                                           const cplx* __restrict__ B, int n_eig,
-                                                          cplx* __restrict__ mt) {
+                                                          cplx* __restrict__ mt, long ld_mt) {
   __shared__ cplx As[BK][TILE + 1];
   __shared__ cplx Bs[BK][TILE + 1];
   const int vc0 = blockIdx.x * TILE, i0 = blockIdx.y * TILE;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const void* __restrict
       int vc = vc0 + tx + 16 * a, i = i0 + ty + 16 * b;
       if (vc < n_vc && i < n_eig) {
         cplx o = {ar[a][b], -ai[a][b]};
-        mt[(size_t)i * n_vc + vc] = o;
+        mt[(size_t)i * ld_mt + vc] = o;
       }
     }
 }
@@ -304,7 +304,8 @@ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 }  // namespace
 
 cudaError_t launch_herk_fp64(const void* A, int a_dtype, int n_vc, int n_g, const double* sf,
-                             const double* sv, double scale, cplx* chi, cudaStream_t st) {
+                             const double* sv, double scale, cplx* chi, cudaStream_t st,
+                             bool accumulate) {
   int nb = ceil_div(n_g, TILE);
   int tiles = nb * (nb + 1) / 2;
   // split the vc sum so that a few waves of blocks cover the GPU
@@ -312,20 +313,21 @@ cudaError_t launch_herk_fp64(const void* A, int a_dtype, int n_vc, int n_g, cons
   int split = tiles >= want ? 1 : ceil_div(want, tiles);
   int kchunk = ceil_div(ceil_div(n_vc, split), BK) * BK;
   split = ceil_div(n_vc, kchunk);
-  if (split > 1) {
+  if (split > 1 && !accumulate) {
     cudaError_t e = cudaMemsetAsync(chi, 0, sizeof(cplx) * (size_t)n_g * n_g, st);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(tiles, split);
   herk_fp64_kernel<<<grid, NT, 0, st>>>(A, a_dtype, n_vc, n_g, sf, sv, scale, chi, nb, kchunk,
-                                        split > 1);
+                                        split > 1 || accumulate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_project_fp64(const void* A, int a_dtype, int n_vc, int n_g, const cplx* B,
-                                int n_eig, cplx* mt, cudaStream_t st) {
+                                int n_eig, cplx* mt, cudaStream_t st, long ld_mt) {
   dim3 grid(ceil_div(n_vc, TILE), ceil_div(n_eig, TILE));
-  project_fp64_kernel<<<grid, NT, 0, st>>>(A, a_dtype, n_vc, n_g, B, n_eig, mt);
+  project_fp64_kernel<<<grid, NT, 0, st>>>(A, a_dtype, n_vc, n_g, B, n_eig, mt,
+                                           ld_mt > 0 ? ld_mt : n_vc);
   return cudaGetLastError();
 }
 

@@ -385,19 +385,33 @@ __global__ void chi0_diag_partial_kernel(const void* A, int dtype, long n_vc, in
 }
 
 __global__ void chi0_diag_finish_kernel(const double* part, int n_chunks, int n_g,
-                                        const double* sv, double scale, cplx* chi) {
+                                        const double* sv, double scale, cplx* chi, double* acc,
+                                        int first, int last) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_g) return;
-  double t = 0.0;
+  double t = (acc && !first) ? acc[g] : 0.0;
   for (int c = 0; c < n_chunks; ++c) t += part[(long)c * n_g + g];
+  if (!last) {
+    acc[g] = t;
+    return;
+  }
   const double s = sv[g];
   chi[(long)g * n_g + g] = {scale * s * s * t, 0.0};
 }
 
 cudaError_t launch_chi0_diagonal(const void* A, int dtype, long n_vc, int n_g, const double* sf0,
                                  const double* sv, double scale, double* scratch,
-                                 size_t scratch_doubles, cplx* chi, cudaStream_t st) {
+                                 size_t scratch_doubles, cplx* chi, cudaStream_t st, int part,
+                                 int n_parts) {
   if (n_g < 1 || n_vc < 1) return cudaSuccess;
+  // a q-point whose transitions arrive in n_parts pieces: the running sums live at
+  // the end of the scratch, the diagonal is written with the last piece
+  double* acc = nullptr;
+  if (n_parts > 1) {
+    if (scratch_doubles < 2 * (size_t)n_g) return cudaErrorInvalidValue;
+    scratch_doubles -= (size_t)n_g;
+    acc = scratch + scratch_doubles;
+  }
   // enough chunks to fill the GPU with a few thousand rows each, within the scratch
   long chunks = std::min<long>(64, (n_vc + 1023) / 1024);
   chunks = std::min<long>(chunks, (long)(scratch_doubles / (size_t)n_g));
@@ -408,7 +422,8 @@ cudaError_t launch_chi0_diagonal(const void* A, int dtype, long n_vc, int n_g, c
   chi0_diag_partial_kernel<<<grid, 256, 0, st>>>(A, dtype, n_vc, n_g, sf0, rows, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  chi0_diag_finish_kernel<<<(n_g + 255) / 256, 256, 0, st>>>(scratch, nc, n_g, sv, scale, chi);
+  chi0_diag_finish_kernel<<<(n_g + 255) / 256, 256, 0, st>>>(scratch, nc, n_g, sv, scale, chi, acc,
+                                                             part == 0, part == n_parts - 1);
   return cudaGetLastError();
 }
 

@@ -625,6 +625,24 @@ __device__ __forceinline__ void emit_digits(long long yr, long long yi, int S, P
   }
 }
 
+// Round-to-nearest BF16 split of the row-scaled value y = x 2^(7 - e), |y| < 128:
+// hi = bf16(y), then each further plane the BF16 rounding of what the earlier
+// planes leave (the classic hi/lo split).  Used by the split precisions
+// (RPA_MIXED_BF16X3 / X6), whose products are summed in FP32 over the whole K.
+template <class Put>
+__device__ __forceinline__ void emit_split(double xr, double xi, int e, int S, Put put) {
+  const double sc = ldexp(1.0, 7 - e);
+  double yr = xr * sc, yi = xi * sc;
+#pragma unroll 1
+  for (int s = 0; s < S; ++s) {
+    const float hr = __bfloat162float(__double2bfloat16(yr));
+    const float hi = __bfloat162float(__double2bfloat16(yi));
+    put(s, hr, hi);
+    yr -= (double)hr;
+    yi -= (double)hi;
+  }
+}
+
 // Y = round(x f 2^(7 + 8(S-1) - e)) for |x f| < 2^e and S <= 3 without an FP64
 // multiply: the product of the leading 31 bits of both
 // significands (relative error below 2^-29) is rounded to the at most 23-bit Y,
@@ -690,7 +708,7 @@ __global__ void chi0_rowmax_kernel(const void* A, int dtype, const int* order, i
 __global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, int n_vc, int n_g,
                                   int n_g_pad, long K, const double* sf,
                                   const unsigned long long* rowmax, int S,
-                                  __nv_bfloat162* planes, int* exps) {
+                                  __nv_bfloat162* planes, int* exps, int split) {
   __shared__ double2 t[32][33];
   __shared__ int es[32];
   const int vc0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
@@ -722,12 +740,15 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, in
     if ((long)2 * vc >= K) continue;
     double2 x = t[tx][r];
     __nv_bfloat162* p = planes + (long)(2 * g) * (K / 2) + vc;
-    emit_digits(digits_y(x.x, es[r], S), digits_y(x.y, es[r], S), S,
-                [&](int s, float fr, float fi) {
-                  __nv_bfloat162* p0 = p + s * plane;
-                  p0[0] = __floats2bfloat162_rn(fr, fi);
-                  p0[K / 2] = __floats2bfloat162_rn(fi, -fr);
-                });
+    auto put = [&](int s, float fr, float fi) {
+      __nv_bfloat162* p0 = p + s * plane;
+      p0[0] = __floats2bfloat162_rn(fr, fi);
+      p0[K / 2] = __floats2bfloat162_rn(fi, -fr);
+    };
+    if (split)
+      emit_split(x.x, x.y, es[r], S, put);
+    else
+      emit_digits(digits_y(x.x, es[r], S), digits_y(x.y, es[r], S), S, put);
   }
 }
 
@@ -761,7 +782,7 @@ __global__ void row_max_kernel(const void* src, int dtype, long ld, int n_rows, 
 __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_rows, int n_cplx,
                                   int rows_pad, long K, int S,
                                   const unsigned long long* rowmax, __nv_bfloat162* planes,
-                                  int* exps) {
+                                  int* exps, int split) {
   const int r = blockIdx.x;
   const int e = r < n_rows ? row_exponent(__longlong_as_double((long long)rowmax[r])) : 0;
   if (blockIdx.y == 0 && threadIdx.x == 0) exps[r] = e;
@@ -771,15 +792,18 @@ __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_row
     double2 x = make_double2(0.0, 0.0);
     if (r < n_rows && k < n_cplx) x = load_any(src, dtype, (long)r * ld + k);
     __nv_bfloat162* p = planes + (long)r * (K / 2) + k;
-    emit_digits(digits_y(x.x, e, S), digits_y(x.y, e, S), S,
-                [&](int s, float fr, float fi) { p[s * plane] = __floats2bfloat162_rn(fr, fi); });
+    auto put = [&](int s, float fr, float fi) { p[s * plane] = __floats2bfloat162_rn(fr, fi); };
+    if (split)
+      emit_split(x.x, x.y, e, S, put);
+    else
+      emit_digits(digits_y(x.x, e, S), digits_y(x.y, e, S), S, put);
   }
 }
 
 // Projection B operand from B[g][i] (= v^1/2 C): rows 2i = (b_r, -b_i) and
 // 2i+1 = (b_i, b_r) along K index 2g + part; one block per i.
 __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_eig_pad, long K,
-                                    int S, __nv_bfloat162* planes, int* exps) {
+                                    int S, __nv_bfloat162* planes, int* exps, int split) {
   __shared__ double red[32];
   const int i = blockIdx.x;
   double m = 0.0;
@@ -804,11 +828,15 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
     double2 b = make_double2(0.0, 0.0);
     if (i < n_eig && g < n_g) b = B[g * n_eig + i];
     __nv_bfloat162* p = planes + (long)(2 * i) * (K / 2) + g;
-    emit_digits(digits_y(b.x, e, S), digits_y(b.y, e, S), S, [&](int s, float fr, float fi) {
+    auto put = [&](int s, float fr, float fi) {
       __nv_bfloat162* p0 = p + s * plane;
       p0[0] = __floats2bfloat162_rn(fr, -fi);
       p0[K / 2] = __floats2bfloat162_rn(fi, fr);
-    });
+    };
+    if (split)
+      emit_split(b.x, b.y, e, S, put);
+    else
+      emit_digits(digits_y(b.x, e, S), digits_y(b.y, e, S), S, put);
   }
 }
 
@@ -873,7 +901,7 @@ __global__ void float_up_kernel(const double* f, long n, float* out) {
 __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
                                     long K, const double* f, int nb, int S,
                                     const unsigned long long* rowmax, __nv_bfloat162* planes,
-                                    int* exps, int eb_stride) {
+                                    int* exps, int eb_stride, int split) {
   const int j = blockIdx.x;
   __shared__ int e[MAX_GROUP];
   if (threadIdx.x < MAX_GROUP) {
@@ -893,6 +921,15 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
 #pragma unroll 1
     for (int b = 0; b < nb; ++b) {
       const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
+      __nv_bfloat162* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
+      if (split) {
+        emit_split(fv * x.x, fv * x.y, e[b], S, [&](int s, float fr, float fi) {
+          __nv_bfloat162* p0 = p + s * plane;
+          p0[0] = __floats2bfloat162_rn(fr, fi);
+          p0[K / 2] = __floats2bfloat162_rn(-fi, fr);
+        });
+        continue;
+      }
       long long yr, yi;
       if (S <= PROD_DIGITS_MAX_S) {
         yr = digits_y_prod(x.x, fv, e[b], S);
@@ -901,7 +938,6 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
         yr = digits_y(fv * x.x, e[b], S);
         yi = digits_y(fv * x.y, e[b], S);
       }
-      __nv_bfloat162* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
       emit_digits(yr, yi, S, [&](int s, float fr, float fi) {
         __nv_bfloat162* p0 = p + s * plane;
         p0[0] = __floats2bfloat162_rn(fr, fi);
@@ -1032,7 +1068,8 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   std::vector<int4> work;
   const int BN = pick_bn(a.S, a.nexact);
   const int tiles_n = cdiv(a.b_rows, BN);
-  const int kdt = drain_tiles(std::min(a.nexact, a.S));
+  // split precisions sum in FP32 over the whole K (one drain at the end)
+  const int kdt = w.split ? std::max(1, a.K / BK) : drain_tiles(std::min(a.nexact, a.S));
   const int kd = kdt * BK;
   int tiles = 0;
   for (int b = 0; b < batches; ++b)
@@ -1206,6 +1243,10 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
                         (size_t)s.proj * std::min<long>(vc_pad, w.proj_chunk) * k_g,
                         (size_t)2 * grp * s.chis * 2 * e_pad * k_vc});
   size_t p2 = std::max((size_t)s.proj * 2 * e_pad * k_g, (size_t)s.chis * e_pad * k_vc);
+  // the eigensolver's block products (chi~ times N_eig + p columns and smaller) run on
+  // the projection GEMM with EIG_SLICES planes
+  p1 = std::max(p1, (size_t)EIG_SLICES * g_pad * k_g);
+  p2 = std::max(p2, (size_t)EIG_SLICES * 2 * e_pad * k_g);
   w.plane_bytes = p1 * 2;
   w.plane2_bytes = p2 * 2;
   w.exp_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)e_pad}) +
@@ -1274,19 +1315,20 @@ static rpa_status side_fork(Workspace& w, cudaStream_t st, std::string& err) {
 
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
                 const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
-                std::string& err, int* launches) {
-  const int S = w.slices.chi0, Le = exact_levels_chi0(S);
+                std::string& err, int* launches, bool zero, int blocks) {
+  const int S = w.slices.chi0, Le = w.split ? 1 : exact_levels_chi0(S);
   const long g_pad = rup(n_g, BM);
   // K-blocks of the transitions in `order` (sorted by sqrt f(0)): each block has
   // its own per-row digit exponents, so rows keep more significant bits where
   // the transition weights of the block are smaller than the overall maximum.
-  const int nblk = std::max(1, std::min(w.chi0_blocks, cdiv(n_vc, 32)));
+  const int nblk =
+      std::max(1, std::min(blocks > 0 ? blocks : w.chi0_blocks, cdiv(n_vc, 32)));
   const long per = rup(cdiv(n_vc, nblk), 32);
   // Two plane buffers: block b is cut on the side stream while block b-1 is
   // multiplied on `st`; buffer b % 2 is reused once the GEMM of block b-2 is done.
   const size_t buf_elems = (size_t)S * 2 * g_pad * rup(2 * per, BK);  // BF16 pairs / 2
   w.proj_a.valid = false;
-  CK(cudaMemsetAsync(chi, 0, sizeof(cplx) * (size_t)n_g * n_g, st));
+  if (zero) CK(cudaMemsetAsync(chi, 0, sizeof(cplx) * (size_t)n_g * n_g, st));
   if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
   int b = 0;
   for (long r0 = 0; r0 < n_vc; r0 += per, ++b) {
@@ -1307,7 +1349,7 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
       dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
       chi0_slice_kernel<<<grid, dim3(32, 8), 0, w.side>>>(A, dtype, order + r0, nr, n_g,
                                                           (int)g_pad, K, sf, rowmax, S, planes,
-                                                          exps);
+                                                          exps, w.split);
       CK(cudaGetLastError());
     }
     CK(cudaEventRecord(w.ev_sliced[buf], w.side));
@@ -1366,7 +1408,7 @@ static const void* a_rows_at(const void* A, int dtype, long row, int n_g) {
 // rows [r0, r0 + nr) of A -> S digit planes of the projection's A operand and exponents ea
 static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, long r0, int nr, int n_g,
                                cudaStream_t s, std::string& err, int* launches) {
-  const int S = w.slices.proj;
+  const int S = w.proj_slices_override > 0 ? w.proj_slices_override : w.slices.proj;
   const long rpad = rup(nr, BM), K = rup(2L * n_g, BK);
   const void* a0 = a_rows_at(A, dtype, r0, n_g);
   CK(cudaMemsetAsync(w.rowmax, 0, rpad * sizeof(unsigned long long), s));
@@ -1374,7 +1416,8 @@ static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, long r0, 
                                                                       w.rowmax);
   CK(cudaGetLastError());
   slice_rows_kernel<<<dim3((unsigned)rpad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
-      a0, dtype, n_g, nr, n_g, (int)rpad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps);
+      a0, dtype, n_g, nr, n_g, (int)rpad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps,
+      w.split);
   CK(cudaGetLastError());
   if (launches) *launches += 2;
   return RPA_OK;
@@ -1398,10 +1441,19 @@ rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int
 }
 
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
-                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches) {
-  const int S = w.slices.proj;
-  const long chunk = proj_chunk_rows(w, n_vc);
+                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches,
+                   long ld_out) {
+  if (ld_out <= 0) ld_out = n_vc;
+  const int S = w.proj_slices_override > 0 ? w.proj_slices_override : w.slices.proj;
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_g, BK);
+  // rows of A cut at a time: the budgeted chunk, and no more than the plane buffer
+  // holds at this slice count
+  const long fit = (long)(w.plane_bytes / ((size_t)S * K * 2)) / BM * BM;
+  const long chunk = std::min(proj_chunk_rows(w, n_vc), fit);
+  if (chunk < BM || (size_t)S * 2 * e_pad * K * 2 > w.plane2_bytes) {
+    err = "projection: operand planes exceed the workspace";
+    return RPA_EINVAL;
+  }
   const bool chunked = chunk < n_vc;
   __nv_bfloat162* pb = (__nv_bfloat162*)w.planes2;
   int* ea = w.exps;
@@ -1412,13 +1464,15 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   w.hook(RPA_T_SLICE, 1);
   if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
   proj_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
-                                                       K, S, pb, eb);
+                                                       K, S, pb, eb, w.split);
   CK(cudaGetLastError());
   if (launches) *launches += 1;
   // chunks of the output's columns are added with FP64 atomics into a zeroed M~
-  if (chunked) CK(cudaMemsetAsync(mt, 0, sizeof(cplx) * (size_t)n_eig * n_vc, st));
+  if (chunked)
+    CK(cudaMemset2DAsync(mt, sizeof(cplx) * (size_t)ld_out, 0, sizeof(cplx) * (size_t)n_vc,
+                         (size_t)n_eig, st));
   w.hook(RPA_T_SLICE, 0);
-  const int Le = exact_levels_proj(S);
+  const int Le = w.split ? 1 : exact_levels_proj(S);
   CUtensorMap tb;
   if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le), err))
     return RPA_ECUDA;
@@ -1446,7 +1500,7 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
     a.out = (double2*)(mt + r0);
     a.out_bstride = 0;
     a.ld_row = 1;
-    a.ld_col = n_vc;
+    a.ld_col = ld_out;
     a.conj = 1;
     a.atomic = 0;
     a.accumulate = chunked ? 1 : 0;
@@ -1462,7 +1516,7 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
                 int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
                 int* launches) {
-  const int S = w.slices.chis, Le = exact_levels_chis(S);
+  const int S = w.slices.chis, Le = w.split ? 1 : exact_levels_chis(S);
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_vc, BK);
   const int grp = w.freq_group;
   __nv_bfloat162* pa = (__nv_bfloat162*)w.planes2;
@@ -1475,7 +1529,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
                                                                             n_eig, n_vc, w.rowmax);
   CK(cudaGetLastError());
   slice_rows_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
-      mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea);
+      mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea, w.split);
   CK(cudaGetLastError());
   float_up_kernel<<<std::min(cdiv((long)n_freq * n_vc, 256), 4096), 256, 0, st>>>(
       f, (long)n_freq * n_vc, w.fweights);
@@ -1505,7 +1559,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
     CK(cudaGetLastError());
     chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, (int)e_pad, n_vc, K, f + (size_t)k0 * n_vc, nb, S, rowmax, pb,
-        eb, (int)e_pad);
+        eb, (int)e_pad, w.split);
     CK(cudaGetLastError());
     CK(cudaEventRecord(w.ev_sliced[buf], cut));
     CK(cudaEventRecord(w.ev_side_last, cut));

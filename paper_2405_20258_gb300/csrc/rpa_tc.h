@@ -25,6 +25,10 @@ namespace rpa {
 namespace tc {
 
 constexpr int MAX_SLICES = 8;
+// Digit planes of the eigensolver's block products on the projection GEMM: products
+// exact to ~2^-55 of the row and column scales (its Rayleigh quotient resolves
+// eigenvalues 1e-4 of the largest to FP64-class accuracy).
+constexpr int EIG_SLICES = 7;
 
 struct Slices {
   int chi0 = 4, proj = 6, chis = 3;
@@ -60,6 +64,8 @@ struct Workspace {
   long proj_chunk = 0;        // rows of A whose projection planes are cut at a time
   bool chis_overlap = true;   // cut the chi_s B planes on the side stream
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
+  int split = 0;              // 1: round-to-nearest BF16 hi/lo split planes, FP32 sums over K
+  int proj_slices_override = 0;  // > 0: slice count of project() (the eigensolver's products)
   int debug_stall = 0;
   Hook hook;
   // Side stream for digit slicing that overlaps the GEMMs and the eigensolve
@@ -82,10 +88,12 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
 void free_workspace(Workspace& w);
 
 // chi~(0) from the transitions in `order` (a permutation of 0..n_vc-1, device),
-// processed in w.chi0_blocks K-blocks with their own digit exponents.
+// processed in K-blocks with their own digit exponents (w.chi0_blocks, or `blocks`
+// when > 0).  zero: chi is set to zero first; else the contributions are added
+// (a q-point whose transitions arrive in chunks).
 rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
                 const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
-                std::string& err, int* launches);
+                std::string& err, int* launches, bool zero = true, int blocks = 0);
 // The caller's stream `st` waits for all side-stream work queued so far.
 rpa_status join_side(Workspace& w, cudaStream_t st, std::string& err);
 
@@ -97,8 +105,11 @@ rpa_status join_side(Workspace& w, cudaStream_t st, std::string& err);
 // them again.
 rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
                            cudaStream_t st, std::string& err, int* launches);
+// mt[i][r] (row stride ld_out, n_vc when <= 0) = conj(sum_g A[r][g] B[g][i]) for the
+// n_vc rows r of A.
 rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
-                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches);
+                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches,
+                   long ld_out = 0);
 // chi_s(i omega_k) for all k from M~ and the transition weights f[k][vc] of every
 // frequency (FP64, device).
 rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librpa.so")
 
 RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_EEIG, RPA_ENUMERIC, RPA_ETIMEOUT, RPA_ESTATE = range(8)
-RPA_FP64, RPA_MIXED = 0, 1
+RPA_FP64, RPA_MIXED, RPA_MIXED_BF16X3, RPA_MIXED_BF16X6 = 0, 1, 2, 3
 RPA_ROUTE_CHOLESKY, RPA_ROUTE_EIG = 0, 1
 RPA_C128, RPA_C64 = 0, 1
 RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
@@ -46,7 +46,7 @@ class rpa_options(ctypes.Structure):
                 ("omega_scale", ctypes.c_double), ("timing", ctypes.c_int),
                 ("slices_chi0", ctypes.c_int), ("slices_proj", ctypes.c_int),
                 ("slices_chis", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("vc_chunk", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class RPAError(RuntimeError):
@@ -176,12 +176,12 @@ class Plan:
     """Owner of an ``rpa_plan_t``; methods mirror the C entry points."""
 
     def __init__(self, qpoints, precision=RPA_FP64, energy_route=RPA_ROUTE_CHOLESKY, omega_scale=0.5,
-                 stream=None, timing=False, slices=(0, 0, 0), debug_stall=0):
+                 stream=None, timing=False, slices=(0, 0, 0), debug_stall=0, vc_chunk=0):
         lib = load()
         self.qpoints = list(qpoints)
         self._structs = (rpa_qpoint * len(self.qpoints))(*[q.struct() for q in self.qpoints])
         opt = rpa_options(precision, energy_route, omega_scale, int(bool(timing)), *slices,
-                          int(debug_stall))
+                          int(debug_stall), int(vc_chunk))
         self._stream = _stream(stream)
         h = ctypes.c_void_p()
         st = lib.rpa_plan_create(ctypes.byref(h), self._structs, len(self.qpoints), ctypes.byref(opt),

@@ -9,7 +9,8 @@ subspace polarizability with its scratch in a fixed library array.
 This test calls that entry point through the C ABI twice in a row on the same
 inputs and checks both results against the trace rpa_chi_freq computes with
 its plan-owned workspace, within the 1e-12 relative tolerance of the FP64
-parity tests; then once more on a smaller problem (the fixed scratch still
+parity tests, and against the oracle's trace term on the same M~; then once
+more on a smaller problem (the fixed scratch still
 holds the larger problem's values), and checks that sizes beyond the fixed
 scratch are refused.  The file is named so that pytest collects it last.
 """
@@ -50,11 +51,16 @@ def static_trace(dq, mt, omega):
 
 def test_static_trace_matches_plan_trace():
     from paper_2405_20258_gb300 import rpa
+    import oracle.rpa_oracle as orc
     dq, mt, ref, omega = plan_trace(160, 6, 50, 30, 7)
+    delta = orc.transition_energies(dq.e_v.cpu().numpy(), dq.e_c.cpu().numpy())
+    mt_h, om_h = mt.cpu().numpy(), omega.cpu().numpy()
+    ref_orc = np.array([orc.trace_term(mt_h, delta, w, dq.omega_cell) for w in om_h])
     for _ in range(2):
         got = static_trace(dq, mt, omega)
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12
+        assert np.max(np.abs(got - ref_orc) / np.abs(ref_orc)) < 1e-12
     # a smaller problem after the larger one: stale scratch entries are never read
     dq2, mt2, ref2, omega2 = plan_trace(90, 2, 30, 12, 3)
     got2 = static_trace(dq2, mt2, omega2)
