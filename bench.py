@@ -37,7 +37,13 @@ WORKLOADS = {
     "qpoint-4000-neig800": dict(n_g=4000, n_v=128, n_c=2000, n_eig=800, n_freq=32),
     # the interface-sized q-point with complex64 matrix elements drawn on the device (50 GB)
     "qpoint-12000": dict(n_g=12000, n_v=256, n_c=2048, n_eig=1200, n_freq=48, m_dtype="c64"),
+    # the same q-point with A never held whole: drawn again per chunk of 16 valence bands
+    "qpoint-12000-streamed": dict(n_g=12000, n_v=256, n_c=2048, n_eig=1200, n_freq=48,
+                                  m_dtype="c64", vc_chunk=16 * 2048),
 }
+# the uneven 4x4x4 q-grid: N_G in [1500, 6000], N_v = 96, N_c in [800, 2400], N_eig = N_G/10,
+# 48 frequencies, every q-point's A drawn on the device; one step = all 64 q-points
+BATCH_WORKLOADS = {"batch-64": dict(n_q=64, n_freq=48)}
 # FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
 PRECISIONS = {"fp64": "RPA_FP64", "mixed": "RPA_MIXED", "bf16x3": "RPA_MIXED_BF16X3",
@@ -272,6 +278,54 @@ def run_steps(plan, n):
     return [plan.run(0) for _ in range(n)]
 
 
+def batch_bench(args):
+    """The uneven 64-q workload in one plan (rpa_ecorr over every q-point, inputs drawn
+    on the device): q-points/s over `steps` passes, after `warmup` passes."""
+    import torch
+    from paper_2405_20258_gb300 import inputs, rpa
+    w = BATCH_WORKLOADS["batch-64"]
+    sizes = inputs.batched_workload()[:w["n_q"]]
+    dqs = []
+    for s in sizes:
+        qp = inputs.make_qpoint(s["n_g"], s["n_v"], s["n_c"], iq=s["iq"],
+                                q_twentieths=s["q_twentieths"])
+        dqs.append(rpa.device_qpoint(qp, max(1, s["n_g"] // 10), w["n_freq"]))
+    precision = getattr(rpa, PRECISIONS[args.precision])
+    stream = torch.cuda.Stream()
+    work = sum(sum(flops(dict(n_g=s["n_g"], n_v=s["n_v"], n_c=s["n_c"], n_eig=max(1, s["n_g"] // 10),
+                              n_freq=w["n_freq"])).values()) for s in sizes)
+    with rpa.Plan(dqs, precision=precision, stream=stream, timing=True) as p:
+        for _ in range(args.warmup):
+            p.ecorr(-1)
+        p.timings()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler() as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                ecs = p.ecorr(-1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        st, launches = p.timings()
+    line = {"metric": METRIC, "value": len(sizes) * args.steps / t, "unit": "q-points/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.precision != "fp64" else "f64",
+            "data": "synthetic (splitmix64 matrix elements drawn on the device)",
+            "config": {"workload": "batch-64", "n_q": len(sizes), "n_v": 96,
+                       "n_g_range": [1500, 6000], "n_c_range": [800, 2400],
+                       "n_eig": "N_G/10", "n_freq": w["n_freq"], "precision": args.precision,
+                       "l2": "inputs larger than L2", "parallelism": "single GPU"},
+            "contraction_tflops": work / (sum(st[k] for k in ("chi0", "proj", "chis")) / 1e3
+                                          / args.steps) / 1e12,
+            "stage_ms_per_step": {k: v / args.steps for k, v in st.items()},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+            "ec_ha_per_q": ecs}
+    print(json.dumps(line), flush=True)
+
+
 def plan_slices(precision, slices):
     """Digit planes per stage (chi~, projection, chi_s) the plan multiplies."""
     if precision == "bf16x3":
@@ -341,7 +395,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qpoint-4000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="qpoint-4000",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=sorted(PRECISIONS))
     ap.add_argument("--route", default="cholesky", choices=["eig", "cholesky"])
     ap.add_argument("--slices", default="4,6,3", help="digit slices of chi0, projection, chi_s")
@@ -364,6 +419,13 @@ def main():
         return
     if args.precision_study:
         precision_study(WORKLOADS[args.workload])
+        return
+    if args.workload in BATCH_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's reference arm "
+                              "times single q-point workloads"}))
+            return
+        batch_bench(args)
         return
     w = WORKLOADS[args.workload]
     if args.eig == "cusolver":
@@ -407,8 +469,13 @@ def main():
         rpa.rpa_generate_m(dq, 0, w["n_v"], 0, w["n_c"], A, stream=stream)
     stream.synchronize()
     dq.m = A
+    if w.get("vc_chunk"):
+        args.no_e2e = True  # no host inputs to copy: A is drawn on the device per chunk
+        dq.m = None  # drawn again per chunk by the library; A is never held whole
+        del A
+        A = torch.empty((0, w["n_g"]), dtype=torch.complex64, device=dev)
     plan = rpa.Plan([dq], precision=precision, energy_route=route, stream=stream, timing=True,
-                    slices=slices if mixed else (0, 0, 0))
+                    slices=slices if mixed else (0, 0, 0), vc_chunk=w.get("vc_chunk", 0))
     fl = flops(w)
     fl_total = sum(fl.values())
 
@@ -607,7 +674,10 @@ def main():
                    "slices": list(slices) if mixed else None, "energy_route": args.route,
                    "eigensolver": args.eig,
                    "chi0_fp64_diagonal": (not args.no_chi0_diag) if mixed else None,
-                   "l2": "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9),
+                   "l2": ("inputs larger than L2 (A is %.1f GB, drawn per chunk of %d transitions, "
+                          "never whole)" % (n_vc * w["n_g"] * (8 if c64 else 16) / 1e9, w["vc_chunk"])
+                          if w.get("vc_chunk") else
+                          "inputs larger than L2 (A is %.1f GB)" % (A.numel() * A.element_size() / 1e9)),
                    "parallelism": "one q-point per GPU" if world > 1 else "single GPU"},
         "contraction_tflops": contraction_tflops,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},

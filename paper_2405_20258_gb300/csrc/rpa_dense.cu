@@ -139,7 +139,7 @@ constexpr int PNB = 32;             // panel width
 constexpr int HT = 512;             // threads per CTA
 constexpr int HW = HT / 32;         // warps per CTA
 constexpr int PL = 2 * PNB + 1;     // partial sums per CTA
-constexpr int SEG = 8;              // segments of the cross-CTA sums
+constexpr int MAXG = 160;           // largest persistent grid (the sums' staging)
 constexpr int MAXOWN = 128;         // rows a CTA may own (n <= MAXOWN * grid)
 constexpr int RJ = 32;              // rows per chunk of the trailing update
 
@@ -156,10 +156,18 @@ struct HetrdArgs {
   int* status;
 };
 
+// The reflector v of the current column is staged in shared memory when it has at
+// most VCAP elements (96 KB); longer ones are read from L2.
+template <typename T>
+__host__ __device__ constexpr int vcap() {
+  return (int)(96 * 1024 / sizeof(typename CxT<T>::C));
+}
+
 template <typename T>
 size_t hetrd_smem() {
   using C = typename CxT<T>::C;
-  return sizeof(C) * (MAXOWN + PL * SEG + PL + 4 * PNB + 2 * RJ * (PNB + 1) + 2 * HW * PNB + 4);
+  return sizeof(C) *
+         (MAXOWN + PL * (MAXG / 4) + PL + 4 * PNB + 2 * RJ * (PNB + 1) + 2 * HW * PNB + 4 + vcap<T>());
 }
 
 template <typename T>
@@ -167,8 +175,8 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
   using C = typename CxT<T>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* xs = (C*)smraw;            // [MAXOWN] this CTA's x
-  C* red = xs + MAXOWN;         // [PL * SEG]
-  C* tot = red + PL * SEG;      // [PL]
+  C* red = xs + MAXOWN;         // [PL * MAXG/4] (>= HW * PL)
+  C* tot = red + PL * (MAXG / 4);  // [PL]
   C* vk = tot + PL;             // [PNB] V(k, :)
   C* wk = vk + PNB;             // [PNB] W(k, :)
   C* s1 = wk + PNB;             // [PNB] W^H v
@@ -178,6 +186,7 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
   C* wb = Ws + RJ * (PNB + 1);  // [HW][PNB] conj W(i, :)
   C* vb = wb + HW * PNB;        // [HW][PNB] conj V(i, :)
   C* scal = vb + HW * PNB;      // tau, sc, alpha2, W(k+1, c)
+  C* vsm = scal + 4;            // [vcap] v(k+1 : n) when it fits
   const int n = p.n, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5,
             lane = tid & 31;
   const int rend = n > b ? (n - b + G - 1) / G : 0;  // local r < rend: i = b + G r < n
@@ -193,51 +202,71 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
       wk[tid] = tid == c - 1 ? scal[3] : __ldcg(&p.wp[(size_t)k * PNB + tid]);
     }
     __syncthreads();
-    if (tid < nown) {
-      const int i = b + G * (rbeg + tid);
-      C x = __ldcg(&p.a[(size_t)k * n + i]);
-      for (int j = 0; j < c; ++j) {
-        const C vij = __ldcg(&p.vp[(size_t)i * PNB + j]);
-        const C wij = __ldcg(&p.wp[(size_t)i * PNB + j]);
-        x = csub(x, cadd(cmul_cb(vij, wk[j]), cmul_cb(wij, vk[j])));
+    // a warp per owned row, lanes over the panel's columns
+    for (int q = warp; q < nown; q += HW) {
+      const int i = b + G * (rbeg + q);
+      C term = {0, 0};
+      if (lane < c)
+        term = cadd(cmul_cb(__ldcg(&p.vp[(size_t)i * PNB + lane]), wk[lane]),
+                    cmul_cb(__ldcg(&p.wp[(size_t)i * PNB + lane]), vk[lane]));
+      term = warp_csum(term);
+      if (lane == 0) {
+        const C x = csub(__ldcg(&p.a[(size_t)k * n + i]), term);
+        xs[q] = x;
+        if (i == k)
+          p.d[k] = x.x;
+        else
+          p.xcol[i] = x;
       }
-      xs[tid] = x;
-      if (i == k)
-        p.d[k] = x.x;
-      else
-        p.xcol[i] = x;
     }
     if (k == n - 1) break;
     __syncthreads();
-    if (tid <= 2 * c) {
-      C acc = {0, 0};
-      for (int q = 0; q < nown; ++q) {
+    {
+      // partial sums over this CTA's rows >= k+2 (per warp in row order, then warps
+      // in order): ||x||^2, W^H x, V^H x
+      C a1 = {0, 0}, a2 = {0, 0};
+      T nrm = T(0);
+      for (int q = warp; q < nown; q += HW) {
         const int i = b + G * (rbeg + q);
         if (i < k + 2) continue;
         const C x = xs[q];
-        if (tid == 0)
-          acc.x += x.x * x.x + x.y * x.y;
-        else if (tid <= c)
-          acc = cadd(acc, cmul_ca(__ldcg(&p.wp[(size_t)i * PNB + tid - 1]), x));
-        else
-          acc = cadd(acc, cmul_ca(__ldcg(&p.vp[(size_t)i * PNB + tid - 1 - c]), x));
+        nrm += x.x * x.x + x.y * x.y;
+        if (lane < c) {
+          a1 = cadd(a1, cmul_ca(__ldcg(&p.wp[(size_t)i * PNB + lane]), x));
+          a2 = cadd(a2, cmul_ca(__ldcg(&p.vp[(size_t)i * PNB + lane]), x));
+        }
       }
-      p.part[(size_t)b * PL + tid] = acc;
+      if (lane == 0) red[warp * PL] = C{nrm, T(0)};
+      if (lane < c) {
+        red[warp * PL + 1 + lane] = a1;
+        red[warp * PL + 1 + c + lane] = a2;
+      }
+      __syncthreads();
+      if (tid <= 2 * c) {
+        C acc = {0, 0};
+        for (int w = 0; w < HW; ++w) acc = cadd(acc, red[w * PL + tid]);
+        p.part[(size_t)b * PL + tid] = acc;
+      }
     }
     if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
 
     // ---- B: reflector and A_eff v over this CTA's columns
     const int L = 2 * c + 1;
-    for (int w = tid; w < L * SEG; w += HT) {
-      const int q = w / SEG, sg = w % SEG;
-      C acc = {0, 0};
-      for (int g = sg; g < G; g += SEG) acc = cadd(acc, __ldcg(&p.part[(size_t)g * PL + q]));
-      red[w] = acc;
+    // every entry's G partials in nsg segments of at most four (one round of loads)
+    const int nsg = (G + 3) / 4;
+    for (int w = tid; w < L * nsg; w += HT) {
+      const int q = w / nsg, sg = w % nsg;
+      const int g0 = sg * 4;
+      C a0 = __ldcg(&p.part[(size_t)g0 * PL + q]);
+      const C a1 = g0 + 1 < G ? __ldcg(&p.part[(size_t)(g0 + 1) * PL + q]) : C{0, 0};
+      const C a2 = g0 + 2 < G ? __ldcg(&p.part[(size_t)(g0 + 2) * PL + q]) : C{0, 0};
+      const C a3 = g0 + 3 < G ? __ldcg(&p.part[(size_t)(g0 + 3) * PL + q]) : C{0, 0};
+      red[w] = cadd(cadd(a0, a1), cadd(a2, a3));
     }
     __syncthreads();
     if (tid < L) {
       C t = {0, 0};
-      for (int sg = 0; sg < SEG; ++sg) t = cadd(t, red[tid * SEG + sg]);
+      for (int sg = 0; sg < nsg; ++sg) t = cadd(t, red[tid * nsg + sg]);
       tot[tid] = t;
     }
     __syncthreads();
@@ -273,17 +302,21 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     __syncthreads();
     const int cbeg = k + 1 > b ? (k + 1 - b + G - 1) / G : 0;
     const int ncol = max(0, rend - cbeg);
+    const int j0 = k + 1, len = n - j0;
+    const bool staged = len <= vcap<T>();
+    if (staged) {
+      for (int t = tid; t < len; t += HT)
+        vsm[t] = t == 0 ? C{1, 0} : cmul(__ldcg(&p.xcol[j0 + t]), sc);
+      __syncthreads();
+    }
     C yvp = {0, 0};
-    for (int q = warp; q < ncol; q += HW) {
+    // Work items (column q, segment sg): when a CTA has fewer columns than warps,
+    // each column's dot product is cut into nseg segments so that every warp streams
+    // A; eight loads in flight per lane; segment sums are added in segment order.
+    const int nseg = ncol > 0 ? max(1, HW / ncol) : 1;
+    const int seglen = ((len + nseg - 1) / nseg + 31) / 32 * 32;
+    auto finish = [&](int q, C acc) {
       const int i = b + G * (cbeg + q);
-      const C* col = p.a + (size_t)i * n;
-      C acc = {0, 0};
-      for (int j = k + 1 + lane; j < n; j += 32) {
-        const C aji = __ldcg(&col[j]);
-        const C vj = j == k + 1 ? C{1, 0} : cmul(__ldcg(&p.xcol[j]), sc);
-        acc = cadd(acc, cmul_ca(aji, vj));
-      }
-      acc = warp_csum(acc);
       C corr = {0, 0};
       if (lane < c)
         corr = cadd(cmul(__ldcg(&p.vp[(size_t)i * PNB + lane]), s1[lane]),
@@ -296,6 +329,45 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
         p.vp[(size_t)i * PNB + c] = vi;
         p.a[(size_t)k * n + i] = vi;
         yvp = cadd(yvp, cmul_ca(y, vi));
+      }
+    };
+    for (int it = warp; it < ncol * nseg; it += HW) {
+      const int q = it / nseg, sg = it % nseg;
+      const int i = b + G * (cbeg + q);
+      const C* col = p.a + (size_t)i * n + j0;
+      const int t0 = sg * seglen, t1 = min(len, t0 + seglen);
+      C acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = C{0, 0};
+      int t = t0 + lane;
+      if (staged) {
+        for (; t + 224 < t1; t += 256) {
+          C av[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) av[u] = __ldcg(&col[t + 32 * u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = cadd(acc[u], cmul_ca(av[u], vsm[t + 32 * u]));
+        }
+        for (; t < t1; t += 32) acc[0] = cadd(acc[0], cmul_ca(__ldcg(&col[t]), vsm[t]));
+      } else {
+        for (; t < t1; t += 32) {
+          const C vj = t == 0 ? C{1, 0} : cmul(__ldcg(&p.xcol[j0 + t]), sc);
+          acc[0] = cadd(acc[0], cmul_ca(__ldcg(&col[t]), vj));
+        }
+      }
+      const C sum = warp_csum(cadd(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])),
+                                   cadd(cadd(acc[4], acc[5]), cadd(acc[6], acc[7]))));
+      if (nseg == 1)
+        finish(q, sum);
+      else if (lane == 0)
+        red[it] = sum;
+    }
+    if (nseg > 1) {
+      __syncthreads();
+      for (int q = warp; q < ncol; q += HW) {
+        C sum = {0, 0};
+        for (int sg = 0; sg < nseg; ++sg) sum = cadd(sum, red[q * nseg + sg]);
+        finish(q, sum);
       }
     }
     __syncthreads();
@@ -421,38 +493,54 @@ __global__ void __launch_bounds__(256) wy_t_kernel(const typename CxT<T>::C* a,
 }
 
 // X <- Q X: CTA owns CT columns of X (n x m, column-major) and applies the blocks
-// from the last to the first: X -= V (T (V^H X)).
-constexpr int CT = 8;
+// from the last to the first: X -= V (T (V^H X)); 32 x CT threads.  The CTA's
+// n x CT tile of X stays in shared memory for the whole product when it fits
+// (`resident`), so only the reflectors stream from L2; V is staged in chunks of
+// RCH rows.
+constexpr int CT = 4;
+constexpr int AQ_THREADS = 32 * CT;
+constexpr int RCH = 64;
 template <typename T>
-__global__ void __launch_bounds__(256) apply_q_kernel(const typename CxT<T>::C* a, int n,
-                                                      const typename CxT<T>::C* tfac,
-                                                      typename CxT<T>::C* x, int m) {
+__global__ void __launch_bounds__(AQ_THREADS) apply_q_kernel(const typename CxT<T>::C* a, int n,
+                                                             const typename CxT<T>::C* tfac,
+                                                             typename CxT<T>::C* x, int m,
+                                                             int resident) {
   using C = typename CxT<T>::C;
-  __shared__ C Vc[32][PNB + 1];
-  __shared__ C Xc[32][CT + 1];
+  extern __shared__ __align__(16) unsigned char aq_raw[];
+  C* xr = (C*)aq_raw;  // [n][CT] when resident
+  __shared__ C Vc[RCH][PNB + 1];
   __shared__ C W1[PNB][CT + 1];
   __shared__ C W2[PNB][CT + 1];
   __shared__ C Tt[PNB][PNB + 1];
   const int tid = threadIdx.x, c0 = blockIdx.x * CT;
   const int nr = n - 1, nblk = (nr + PNB - 1) / PNB;
-  const int r_own = tid / CT, cc_own = tid % CT;  // 32 x 8 = 256
+  const int r_own = tid / CT, cc_own = tid % CT;  // 32 x CT
+  auto xat = [&](int j, int cc) -> C& { return resident ? xr[(size_t)j * CT + cc]
+                                                        : x[(size_t)(c0 + cc) * n + j]; };
+  if (resident)
+    for (int e = tid; e < n * CT; e += AQ_THREADS) {
+      const int cc = e / n, j = e % n;
+      xr[(size_t)j * CT + cc] = c0 + cc < m ? x[(size_t)(c0 + cc) * n + j] : C{0, 0};
+    }
   for (int blk = nblk - 1; blk >= 0; --blk) {
     const int b0 = blk * PNB, nb = min(PNB, nr - b0);
     __syncthreads();
-    for (int e = tid; e < PNB * PNB; e += 256) Tt[e / PNB][e % PNB] = tfac[(size_t)blk * PNB * PNB + e];
+    for (int e = tid; e < PNB * PNB; e += AQ_THREADS)
+      Tt[e / PNB][e % PNB] = tfac[(size_t)blk * PNB * PNB + e];
     C acc = {0, 0};
-    for (int j0 = b0 + 1; j0 < n; j0 += 32) {
+    for (int j0 = b0 + 1; j0 < n; j0 += RCH) {
       __syncthreads();
-      for (int e = tid; e < 32 * PNB; e += 256) {
-        const int r = e / 32, jj = e % 32, j = j0 + jj;
+      for (int e = tid; e < RCH * PNB; e += AQ_THREADS) {
+        const int r = e / RCH, jj = e % RCH, j = j0 + jj;
         Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
       }
-      {
-        const int jj = tid % 32, cc = tid / 32, j = j0 + jj;  // 32 x 8
-        Xc[jj][cc] = (j < n && c0 + cc < m) ? x[(size_t)(c0 + cc) * n + j] : C{0, 0};
-      }
       __syncthreads();
-      for (int jj = 0; jj < 32; ++jj) acc = cadd(acc, cmul_ca(Vc[jj][r_own], Xc[jj][cc_own]));
+      const bool in_c = c0 + cc_own < m;
+      const int jmax = min(RCH, n - j0);
+      for (int jj = 0; jj < jmax; ++jj) {
+        const C xv = in_c ? xat(j0 + jj, cc_own) : C{0, 0};
+        acc = cadd(acc, cmul_ca(Vc[jj][r_own], xv));
+      }
     }
     W1[r_own][cc_own] = acc;
     __syncthreads();
@@ -461,22 +549,30 @@ __global__ void __launch_bounds__(256) apply_q_kernel(const typename CxT<T>::C* 
       for (int s = r_own; s < PNB; ++s) t = cadd(t, cmul(Tt[r_own][s], W1[s][cc_own]));
       W2[r_own][cc_own] = t;
     }
-    for (int j0 = b0 + 1; j0 < n; j0 += 32) {
+    for (int j0 = b0 + 1; j0 < n; j0 += RCH) {
       __syncthreads();
-      for (int e = tid; e < 32 * PNB; e += 256) {
-        const int r = e / 32, jj = e % 32, j = j0 + jj;
+      for (int e = tid; e < RCH * PNB; e += AQ_THREADS) {
+        const int r = e / RCH, jj = e % RCH, j = j0 + jj;
         Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
       }
       __syncthreads();
-      const int jj = tid % 32, cc = tid / 32, j = j0 + jj;
-      if (j < n && c0 + cc < m) {
-        C t = {0, 0};
-        for (int r = 0; r < PNB; ++r) t = cadd(t, cmul(Vc[jj][r], W2[r][cc]));
-        C* xp = &x[(size_t)(c0 + cc) * n + j];
-        *xp = csub(*xp, t);
+      for (int e = tid; e < RCH * CT; e += AQ_THREADS) {
+        const int jj = e % RCH, cc = e / RCH, j = j0 + jj;
+        if (j < n && c0 + cc < m) {
+          C t = {0, 0};
+          for (int r = 0; r < PNB; ++r) t = cadd(t, cmul(Vc[jj][r], W2[r][cc]));
+          C& xv = xat(j, cc);
+          xv = csub(xv, t);
+        }
       }
     }
   }
+  __syncthreads();
+  if (resident)
+    for (int e = tid; e < n * CT; e += AQ_THREADS) {
+      const int cc = e / n, j = e % n;
+      if (c0 + cc < m) x[(size_t)(c0 + cc) * n + j] = xr[(size_t)j * CT + cc];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -526,7 +622,11 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
   const int tid = threadIdx.x;
   unsigned gen = 0;
   const double eps = 2.220446049250313e-16;
-  int rotated = 0;  // rotations this CTA applied in the current sweep
+  // largest relative off-diagonal |g_pq| / sqrt(|g_pp g_qq|) this thread rotated away in
+  // the current sweep: Jacobi converges quadratically, so once a whole sweep needed
+  // only rotations below kConverged the matrix it leaves is diagonal to ~kConverged^2
+  double offmax = 0.0;
+  constexpr double kConverged = 1e-8;
   for (int sweep = 0; sweep < p.max_sweeps; ++sweep) {
     for (int r = 0; r < M - 1; ++r) {
       // 1. rotation parameters of this CTA's pairs
@@ -539,14 +639,15 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
           const double c = ldcg_c(&p.g[(size_t)qq * m + qq]).re;
           const cplx gpq = ldcg_c(&p.g[(size_t)qq * m + pp]);
           const double beta = hypot(gpq.re, gpq.im);
-          if (beta > 1e-300 && beta > eps * sqrt(fabs(a * c))) {
+          const double ref = sqrt(fabs(a * c));
+          if (beta > 1e-300 && beta > eps * ref) {
+            offmax = fmax(offmax, ref > 0.0 ? beta / ref : 1.0);
             const double zeta = (c - a) / (2.0 * beta);
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             cs = 1.0 / sqrt(1.0 + t * t);
             sn = t * cs;
             er = gpq.re / beta;
             ei = -gpq.im / beta;
-            ++rotated;
           }
         }
         double* o = p.prm + 4 * (size_t)k;
@@ -605,26 +706,26 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
       }
       if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
     }
-    // stop when no CTA rotated in this sweep
+    // stop once the sweep needed no rotation above kConverged (in any CTA)
     __syncthreads();
     {
-      __shared__ int cnt[JT / 32];
-      int v = rotated;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((tid & 31) == 0) cnt[tid >> 5] = v;
+      __shared__ double cmax[JT / 32];
+      double v = offmax;
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((tid & 31) == 0) cmax[tid >> 5] = v;
       __syncthreads();
       if (tid == 0) {
-        int s = 0;
-        for (int w = 0; w < JT / 32; ++w) s += cnt[w];
-        p.part[b] = (double)s;
+        double s = 0.0;
+        for (int w = 0; w < JT / 32; ++w) s = fmax(s, cmax[w]);
+        p.part[b] = s;
       }
     }
-    rotated = 0;
+    offmax = 0.0;
     if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
     if (tid == 0) {
       double s = 0.0;
-      for (int g = 0; g < G; ++g) s += __ldcg(&p.part[g]);
-      stop_s = s == 0.0;
+      for (int g = 0; g < G; ++g) s = fmax(s, __ldcg(&p.part[g]));
+      stop_s = s < kConverged;
     }
     __syncthreads();
     if (stop_s) break;
@@ -812,8 +913,8 @@ rpa_status hetrd_alloc(HetrdWork& w, int n_max, size_t elem, std::string& err) {
   if (s != RPA_OK) return s;
   w.n_max = n_max;
   w.elem = elem;
-  w.grid = sms;
-  if ((long)MAXOWN * sms < n_max) {
+  w.grid = std::min(sms, MAXG);
+  if ((long)MAXOWN * w.grid < n_max) {
     err = "dense eigensolver: matrix too large for the persistent grid";
     return RPA_EINVAL;
   }
@@ -860,7 +961,7 @@ rpa_status hetrd(HetrdWork& w, void* a, int n, T* d, T* e, void* tau, cudaStream
   int sms = 0;
   rpa_status s = coop_setup(sms, err);
   if (s != RPA_OK) return s;
-  const int G = hetrd_grid<T>(n, std::min(sms, w.grid));
+  const int G = hetrd_grid<T>(n, std::min(std::min(sms, w.grid), MAXG));
   if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
     err = "dense eigensolver: barrier reset failed";
     return RPA_ECUDA;
@@ -891,7 +992,18 @@ rpa_status apply_q(const void* a, const void* tau, int n, void* x, int m, void* 
   if (n < 2 || m < 1) return RPA_OK;
   const int nblk = (n - 1 + PNB - 1) / PNB;
   wy_t_kernel<T><<<nblk, 256, 0, st>>>((const C*)a, (const C*)tau, n, (C*)tfac);
-  apply_q_kernel<T><<<(m + CT - 1) / CT, 256, 0, st>>>((const C*)a, n, (const C*)tfac, (C*)x, m);
+  // the X tile resident in shared memory when it fits beside the static arrays
+  const size_t res_bytes = (size_t)n * CT * sizeof(C);
+  const bool resident = res_bytes <= 160 * 1024;
+  if (resident &&
+      cudaFuncSetAttribute(apply_q_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(160 * 1024)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    err = "apply_q: shared memory attribute";
+    return RPA_ECUDA;
+  }
+  apply_q_kernel<T><<<(m + CT - 1) / CT, AQ_THREADS, resident ? res_bytes : 0, st>>>(
+      (const C*)a, n, (const C*)tfac, (C*)x, m, resident ? 1 : 0);
   const cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) {
     err = std::string("apply_q launch: ") + cudaGetErrorString(ce);
@@ -949,7 +1061,7 @@ rpa_status jacobi(JacobiWork& w, cplx* g, int m, double* theta, cplx* y, cplx* y
   rpa_status s = coop_setup(sms, err);
   if (s != RPA_OK) return s;
   const int M = m + (m & 1), np = M / 2;
-  const int G = std::max(1, std::min(std::min(sms, w.grid), np / 4));
+  const int G = std::max(1, std::min(std::min(sms, w.grid), np / 2));
   identity_kernel<<<std::min(4096, (m * m + 255) / 256), 256, 0, st>>>(ywork, m);
   if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
     err = "Jacobi eigensolver: barrier reset failed";

@@ -93,17 +93,25 @@ __global__ void promote_tri_kernel(const float* d32, const float* e32, int n, do
   }
 }
 
-// w[j] for j < k: eigenvalue j (ascending) of T by Sturm bisection, a thread each;
-// FP32 bisection finished in FP64 (use32) or FP64 throughout
+// w[j] for j < k: eigenvalue j (ascending) of T by Sturm bisection, a thread each.
+// mode 0: FP64 throughout; 1: FP32 bisection finished in FP64; 2: FP32 only (to 4
+// FP32 ulps of the eigenvalue: the FP32 reduction's T is itself an FP32 object, and
+// the refinement that follows restores FP64 accuracy).
 __global__ void bisect_kernel(const double* d, const double* e, const double* e2, const float* d32,
-                              const float* e2f, int n, int k, int use32, double* w) {
+                              const float* e2f, int n, int k, int mode, double* w) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
   double lo, hi, pivmin;
   tri::bounds(d, e, n, &lo, &hi, &pivmin);
+  if (mode == 2) {
+    float flo = (float)lo, fhi = (float)hi;
+    tri::bisect_f(d32, e2f, n, j, &flo, &fhi);
+    w[j] = 0.5 * ((double)flo + (double)fhi);
+    return;
+  }
   const double abstol = 1e-8 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
-  w[j] = use32 ? tri::bisect_mixed(d, e2, d32, e2f, n, j, lo, hi, pivmin, abstol)
-               : tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
+  w[j] = mode == 1 ? tri::bisect_mixed(d, e2, d32, e2f, n, j, lo, hi, pivmin, abstol)
+                   : tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
 }
 
 // Eigenvectors of T for the clusters c < nc of w (cluster c = w[first[c] ..
@@ -383,12 +391,16 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   //    (RPA_EIG_BISECT32=0: without the FP32 phase; RPA_EIG_BISECT_BLOCK threads a
   //    block, 32 by default, a multiple of 32 at most 256)
   const int nval = mp < n ? mp + 1 : mp;
+  //    The FP32 start takes FP32 bisection only (RPA_EIG_BISECT64=1: finished in FP64);
+  //    the FP64 start FP32 bisection finished in FP64 (RPA_EIG_BISECT32=0: FP64 only).
   const char* b32_env = getenv("RPA_EIG_BISECT32");
+  const char* b64_env = getenv("RPA_EIG_BISECT64");
   const char* blk_env = getenv("RPA_EIG_BISECT_BLOCK");
-  const int use32 = !(b32_env && b32_env[0] == '0');
-  const int bb = std::max(32, std::min(256, (blk_env ? atoi(blk_env) : 32) / 32 * 32));
+  int mode = (b32_env && b32_env[0] == '0') ? 0 : 1;
+  if (s32 && !(b64_env && b64_env[0] == '1')) mode = 2;
+  const int bb = std::max(1, std::min(256, blk_env ? atoi(blk_env) : 32));
   bisect_kernel<<<(nval + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, s32 ? d32 : d32b, e2f, n, nval,
-                                                     use32, wt);
+                                                     mode, wt);
   CU_E(cudaGetLastError());
   nl += 1;
   std::vector<double> w(nval);
@@ -419,7 +431,18 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
     return RPA_ENUMERIC;
   }
   std::vector<int> fh(mp + 1);
-  const int nc = tri::clusters(w.data(), mp, 1e-10 * tnorm, fh.data());
+  int nc = 0;
+  if (mode == 2) {
+    // FP32 eigenvalues: a new cluster where the gap exceeds 1e-5 of the eigenvalue,
+    // well above the bisection's 4 FP32 ulps (inverse iteration with shifts closer
+    // than their errors would return one vector twice)
+    for (int j = 0; j < mp; ++j)
+      if (j == 0 || w[j] - w[j - 1] > 1e-5 * std::max(std::fabs(w[j]), std::fabs(w[j - 1])))
+        fh[nc++] = j;
+    fh[nc] = mp;
+  } else {
+    nc = tri::clusters(w.data(), mp, 1e-10 * tnorm, fh.data());
+  }
   int widest = 0;
   for (int c = 0; c < nc; ++c) widest = std::max(widest, fh[c + 1] - fh[c]);
   if (widest > kMaxCluster) {
@@ -427,7 +450,9 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
     return RPA_ENUMERIC;
   }
   CU_E(cudaMemcpyAsync(first, fh.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  invit_kernel<<<(nc + 31) / 32, 32, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
+  const char* ib_env = getenv("RPA_EIG_INVIT_BLOCK");
+  const int ib = std::max(1, std::min(256, ib_env ? atoi(ib_env) : 32));
+  invit_kernel<<<(nc + ib - 1) / ib, ib, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
   CU_E(cudaGetLastError());
   if (s32) {
     z_to_c64_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, c32);

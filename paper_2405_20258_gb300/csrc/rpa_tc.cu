@@ -1467,8 +1467,11 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
                                                        K, S, pb, eb, w.split);
   CK(cudaGetLastError());
   if (launches) *launches += 1;
-  // chunks of the output's columns are added with FP64 atomics into a zeroed M~
-  if (chunked)
+  // chunks of the output's columns, and a strided output (ld_out != n_vc, whose
+  // split-K tiles must not zero a contiguous range), are added with FP64 atomics
+  // into a zeroed M~
+  const bool strided = ld_out != n_vc;
+  if (chunked || strided)
     CK(cudaMemset2DAsync(mt, sizeof(cplx) * (size_t)ld_out, 0, sizeof(cplx) * (size_t)n_vc,
                          (size_t)n_eig, st));
   w.hook(RPA_T_SLICE, 0);
@@ -1503,7 +1506,7 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
     a.ld_col = ld_out;
     a.conj = 1;
     a.atomic = 0;
-    a.accumulate = chunked ? 1 : 0;
+    a.accumulate = (chunked || strided) ? 1 : 0;
     w.hook(RPA_T_PROJ, 1);
     rpa_status r = run_gemm(w, ta, tb, a, cdiv(nr, BM), 1, false, mt,
                             sizeof(cplx) * (size_t)n_eig * n_vc, st, err, launches);

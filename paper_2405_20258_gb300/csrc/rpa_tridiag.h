@@ -206,31 +206,68 @@ RPA_HD void lu_factor(const double* d, const double* e, int n, double lambda, do
 }
 
 // Solve M x = y in place (y becomes x) with the factors of lu_factor.  Returns the
-// factor by which the result was scaled down to stay finite (1 if none).
+// factor by which the result was scaled down to stay finite (1 if none).  Both
+// sweeps are recurrences; their operands are fetched PF steps ahead (the lanes
+// live in global memory on the device, where a fetch takes hundreds of cycles),
+// with the arithmetic in the same order as one step at a time.
+constexpr int PF = 8;
 RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane y) {
-  for (int k = 0; k + 1 < n; ++k) {
-    if (piv[k] != 0.0) {
-      const double yk = y[k], yk1 = y[k + 1];
-      y[k] = yk1;
-      y[k + 1] = yk - l[k] * yk1;
-    } else {
-      y[k + 1] -= l[k] * y[k];
+  // forward: row exchanges and multipliers; cur = y[k] as updated so far
+  double cur = n > 0 ? y[0] : 0.0;
+  for (int k0 = 0; k0 + 1 < n; k0 += PF) {
+    const int cnt = (n - 1 - k0) < PF ? (n - 1 - k0) : PF;
+    double bp[PF], bl[PF], by[PF];
+    for (int t = 0; t < cnt; ++t) {
+      bp[t] = piv[k0 + t];
+      bl[t] = l[k0 + t];
+      by[t] = y[k0 + t + 1];
+    }
+    for (int t = 0; t < cnt; ++t) {
+      const int k = k0 + t;
+      if (bp[t] != 0.0) {
+        const double yk = cur, yk1 = by[t];
+        y[k] = yk1;
+        cur = yk - bl[t] * yk1;
+      } else {
+        y[k] = cur;
+        cur = by[t] - bl[t] * cur;
+      }
     }
   }
+  if (n > 0) y[n - 1] = cur;
   double scale = 1.0;
   const double big = 1e150;
-  for (int k = n - 1; k >= 0; --k) {
-    double s = y[k];
-    if (k + 1 < n) s -= u1[k] * y[k + 1];
-    if (k + 2 < n) s -= u2[k] * y[k + 2];
-    s /= u0[k];
-    if (fabs(s) > big) {
-      // rescale the solved tail (and the rest of the right-hand side) by 1/big
-      for (int i = 0; i < n; ++i) y[i] *= 1.0 / big;
-      s *= 1.0 / big;
-      scale *= 1.0 / big;
+  // backward: s_k = (y_k - u1_k s_{k+1} - u2_k s_{k+2}) / u0_k
+  double s1 = 0.0, s2 = 0.0;  // s_{k+1}, s_{k+2}
+  for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
+    const int cnt = (k0 + 1) < PF ? (k0 + 1) : PF;
+    double by[PF], b0[PF], b1[PF], b2[PF];
+    for (int t = 0; t < cnt; ++t) {
+      const int k = k0 - t;
+      by[t] = y[k];
+      b0[t] = u0[k];
+      b1[t] = u1[k];
+      b2[t] = u2[k];
     }
-    y[k] = s;
+    for (int t = 0; t < cnt; ++t) {
+      const int k = k0 - t;
+      double s = by[t];
+      if (k + 1 < n) s -= b1[t] * s1;
+      if (k + 2 < n) s -= b2[t] * s2;
+      s /= b0[t];
+      if (fabs(s) > big) {
+        // rescale the solved tail (and the rest of the right-hand side) by 1/big
+        for (int i = 0; i < n; ++i) y[i] *= 1.0 / big;
+        for (int t2 = t + 1; t2 < cnt; ++t2) by[t2] *= 1.0 / big;
+        s1 *= 1.0 / big;
+        s2 *= 1.0 / big;
+        s *= 1.0 / big;
+        scale *= 1.0 / big;
+      }
+      y[k] = s;
+      s2 = s1;
+      s1 = s;
+    }
   }
   return scale;
 }

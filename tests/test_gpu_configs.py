@@ -82,3 +82,20 @@ def test_large_qpoint_subsample_against_oracle():
     ref = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, 150, 48)["ec"]
     got = run_gpu(qp, A, 150, 48, precision=1, keep=False)["ec"]
     assert abs(got - ref) <= 1e-6
+
+
+def test_uneven_batch_smallest_qpoints_against_oracle():
+    """The two smallest q-points of the uneven 64-q grid (by N_G N_vc), each in a plan of
+    its own on the mixed path, against the oracle within 1e-6 Ha."""
+    from paper_2405_20258_gb300 import rpa
+    sizes = inputs.batched_workload()
+    small = sorted(range(len(sizes)), key=lambda i: sizes[i]["n_g"] ** 2 * sizes[i]["n_c"])[:2]
+    for i in small:
+        s = sizes[i]
+        qp = inputs.make_qpoint(s["n_g"], s["n_v"], s["n_c"], iq=s["iq"],
+                                q_twentieths=s["q_twentieths"])
+        A = inputs.matrix_elements(qp)
+        n_eig = max(1, s["n_g"] // 10)
+        ref = orc.ecorr(A, qp.qg2, qp.e_v, qp.e_c, qp.omega_cell, n_eig, 48)["ec"]
+        got = run_gpu(qp, A, n_eig, 48, precision=1, keep=False)["ec"]
+        assert abs(got - ref) <= 1e-6, (i, got, ref)
