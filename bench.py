@@ -47,7 +47,7 @@ BATCH_WORKLOADS = {"batch-64": dict(n_q=64, n_freq=48)}
 # FP64 tensor/SIMT rate relative to dense BF16 (nominal 1.25 vs 2250 TFLOP/s)
 FP64_OVER_BF16 = 1.25 / 2250.0
 PRECISIONS = {"fp64": "RPA_FP64", "mixed": "RPA_MIXED", "bf16x3": "RPA_MIXED_BF16X3",
-              "bf16x6": "RPA_MIXED_BF16X6"}
+              "bf16x6": "RPA_MIXED_BF16X6", "tf32x3": "RPA_MIXED_TF32X3"}
 
 
 def flops(w):
@@ -244,9 +244,13 @@ def gpu_local_cpus(index):
 #         RPA_TC_CHI0_BLOCKS=1 for one K-block of K = 32,000); chi0_static three times.
 #   chis: the chi_s stage of a 1000-plane-wave q-point with 32,000 transitions, N_eig 400
 #         and 4 frequencies; the whole chain twice.
+#   eig:  the subspace stage (the library's eigensolver, FP32 start) of a 4000-plane-wave
+#         q-point with 4,000 transitions (chi~ is the bench workload's size, A 0.26 GB);
+#         chi0_static once, subspace_basis three times.
 PROFILE_CASES = {
     "chi0": dict(n_g=4000, n_v=16, n_c=1000, n_eig=400, n_freq=8),
     "chis": dict(n_g=1000, n_v=16, n_c=2000, n_eig=400, n_freq=4),
+    "eig": dict(n_g=4000, n_v=8, n_c=500, n_eig=400, n_freq=8),
 }
 
 
@@ -262,11 +266,15 @@ def profile_case(name, slices):
     dq.m = A
     sl = tuple(int(x) for x in slices.split(","))
     with rpa.Plan([dq], precision=rpa.RPA_MIXED, slices=sl, timing=True) as p:
-        reps = 3 if name == "chi0" else 2
-        for _ in range(reps):
+        reps = 3 if name in ("chi0", "eig") else 2
+        if name == "eig":
             p.chi0_static(0)
-            if name == "chis":
+        for _ in range(reps):
+            if name != "eig":
+                p.chi0_static(0)
+            if name in ("chis", "eig"):
                 p.subspace_basis(0)
+            if name == "chis":
                 p.chi_freq(0)
         torch.cuda.synchronize()
         st, _ = p.timings()
@@ -328,7 +336,7 @@ def batch_bench(args):
 
 def plan_slices(precision, slices):
     """Digit planes per stage (chi~, projection, chi_s) the plan multiplies."""
-    if precision == "bf16x3":
+    if precision in ("bf16x3", "tf32x3"):
         return (2, 2, 2)
     if precision == "bf16x6":
         return (3, 3, 3)
@@ -373,7 +381,7 @@ def precision_study(w):
         dq = rpa.device_qpoint(qp, n_eig, w["n_freq"])
         with rpa.Plan([dq], precision=rpa.RPA_FP64) as p:
             e64 = p.run(0)
-        for name in ("mixed", "bf16x6", "bf16x3"):
+        for name in ("mixed", "bf16x6", "bf16x3", "tf32x3"):
             with rpa.Plan([dq], precision=getattr(rpa, PRECISIONS[name]), timing=True) as p:
                 ec = p.run(0)
                 t0 = time.perf_counter()
@@ -448,7 +456,7 @@ def main():
     rpa.load()
     mixed = args.precision != "fp64"
     precision = getattr(rpa, PRECISIONS[args.precision])
-    if args.precision in ("bf16x3", "bf16x6"):
+    if args.precision in ("bf16x3", "bf16x6", "tf32x3"):
         args.slices = "0,0,0"  # the split precisions fix their planes
     route = rpa.RPA_ROUTE_CHOLESKY if args.route == "cholesky" else rpa.RPA_ROUTE_EIG
     slices = tuple(int(x) for x in args.slices.split(","))

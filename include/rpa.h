@@ -72,7 +72,9 @@ typedef enum {
   RPA_MIXED_BF16X3 = 2, /* every contraction on round-to-nearest BF16 hi/lo planes, 3
                            products (hi.hi + hi.lo + lo.hi), FP32 sums over K: the
                            classic split; does not reach 1e-6 Ha (for comparison)      */
-  RPA_MIXED_BF16X6 = 3  /* the same with hi/mid/lo planes, 6 products                  */
+  RPA_MIXED_BF16X6 = 3, /* the same with hi/mid/lo planes, 6 products                  */
+  RPA_MIXED_TF32X3 = 4  /* every contraction on TF32 hi/lo planes (kind::tf32 tensor cores),
+                           3 products, FP32 sums over K (for comparison)                */
 } rpa_precision;
 
 typedef enum {

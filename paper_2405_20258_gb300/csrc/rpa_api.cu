@@ -488,7 +488,7 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
   o.omega_scale = 0.5;
   if (opt) o = *opt;
   if (!(o.omega_scale > 0.0)) o.omega_scale = 0.5;
-  if (o.precision < RPA_FP64 || o.precision > RPA_MIXED_BF16X6)
+  if (o.precision < RPA_FP64 || o.precision > RPA_MIXED_TF32X3)
     return fail(nullptr, RPA_EINVAL, "unknown precision %d", o.precision);
   if (o.energy_route != RPA_ROUTE_EIG && o.energy_route != RPA_ROUTE_CHOLESKY)
     return fail(nullptr, RPA_EINVAL, "unknown energy route %d", o.energy_route);
@@ -565,25 +565,23 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     rpa::tc::Slices sl;
     // the split precisions: every contraction on round-to-nearest BF16 hi/lo planes
     // (2 planes, 3 products; or 3 planes, 6 products) summed in FP32
-    const bool split = o.precision == RPA_MIXED_BF16X3 || o.precision == RPA_MIXED_BF16X6;
-    if (split) sl.chi0 = sl.proj = sl.chis = o.precision == RPA_MIXED_BF16X3 ? 2 : 3;
+    const bool tf32 = o.precision == RPA_MIXED_TF32X3;
+    const bool split = o.precision == RPA_MIXED_BF16X3 || o.precision == RPA_MIXED_BF16X6 || tf32;
+    // TF32 planes take 4 bytes an element: the workspace is sized for twice the planes
+    if (split) sl.chi0 = sl.proj = sl.chis = o.precision == RPA_MIXED_BF16X6 ? 3 : (tf32 ? 4 : 2);
     if (o.slices_chi0 > 0) sl.chi0 = o.slices_chi0;
     if (o.slices_proj > 0) sl.proj = o.slices_proj;
     if (o.slices_chis > 0) sl.chis = o.slices_chis;
     std::string e;
-    // the eigensolver's FP32 start multiplies chi~ by N_eig + p columns on the
-    // projection GEMM: size its B operand for them
-    size_t E_tc = E;
-    for (int i = 0; i < n_q; ++i)
-      if (rpa::eig::start32(q[i].n_g, q[i].n_eig))
-        E_tc = std::max(E_tc, (size_t)rpa::eig::block_size(q[i].n_g, q[i].n_eig));
-    s = rpa::tc::alloc_workspace(p->tcw, G, E_tc, V, F, sl, e);
+    s = rpa::tc::alloc_workspace(p->tcw, G, E, V, F, sl, e);
     if (s != RPA_OK) {
       free_plan(p);
       return fail(nullptr, s, "tensor-core workspace: %s", e.c_str());
     }
     p->tcw.debug_stall = o.debug_stall;
     p->tcw.split = split ? 1 : 0;
+    p->tcw.tf32 = tf32 ? 1 : 0;
+    if (tf32) p->tcw.slices.chi0 = p->tcw.slices.proj = p->tcw.slices.chis = 2;
     if (dalloc(nullptr, &p->fall, F * V) != RPA_OK || dalloc(nullptr, &p->order, V) != RPA_OK) {
       free_plan(p);
       return RPA_ENOMEM;
@@ -765,11 +763,9 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
   const int n = q.n_g;
   const bool mixed = p->opt.precision != RPA_FP64;
   const bool refine_here = p->refine_ready && !rpa::eig::use_library();
-  const bool tc_products = mixed && refine_here && rpa::eig::start32(n, q.n_eig) &&
-                           rpa::eig::products_on_tc();
-  // the projection's A planes are cut on the side stream during the eigensolve,
-  // unless the eigensolver's tensor-core products take the planes then
-  if (mixed && !tc_products && !streamed(p, iq)) {
+  // the projection's A planes are cut on the side stream during the eigensolve (whose
+  // own tensor-core products use a workspace of their own)
+  if (mixed && !streamed(p, iq)) {
     const void* A;
     int dt, nl = 0;
     if ((s = matrix_a(p, iq, &A, &dt)) != RPA_OK) return s;
@@ -785,8 +781,8 @@ rpa_status rpa_subspace_basis(rpa_plan_t p, int iq, double* lambda_out, void* c_
     // start, FP64 tridiagonal eigenpairs, Cholesky-QR2 and Rayleigh-Ritz; the
     // eigenvectors land where the library solver would leave them, for the gauge kernel
     int nl = 0;
-    s = p->refine.subspace(p->chi, n, q.n_eig, p->lam_all, p->chi_work, p->chi_work,
-                           mixed ? &p->tcw : nullptr, mixed, p->st, p->err, &nl);
+    s = p->refine.subspace(p->chi, n, q.n_eig, p->lam_all, p->chi_work, p->chi_work, mixed,
+                           p->st, p->err, &nl);
     p->launches += nl;
     if (s != RPA_OK && s != RPA_ENUMERIC) return s;
     refined = s == RPA_OK;  // RPA_ENUMERIC: a degenerate spectrum, the library solver takes it

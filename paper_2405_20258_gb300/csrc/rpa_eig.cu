@@ -323,6 +323,15 @@ rpa_status Refine::alloc(int n_max, int mp_max, bool with32, std::string& err) {
   }
   rpa_status s = RPA_OK;
   if (with32) s = dense::hetrd_alloc(hw32, n_max, sizeof(float2), err);
+  if (s == RPA_OK && with32 && products_on_tc()) {
+    tc::Slices sl;
+    sl.chi0 = 1;
+    sl.proj = tc::EIG_SLICES;
+    sl.chis = 1;
+    // rows up to n (chi~ and the blocks), K up to 2n, columns up to m'
+    s = tc::alloc_workspace(tw, n, mp, n, 1, sl, err);
+    has_tw = s == RPA_OK;
+  }
   if (s == RPA_OK) s = dense::hetrd_alloc(hw64, n_max, sizeof(cplx), err);
   if (s == RPA_OK) s = dense::jacobi_alloc(jw, mp_max, err);
   if (s != RPA_OK) {
@@ -341,6 +350,7 @@ void Refine::release() {
   dense::hetrd_free(hw32);
   dense::hetrd_free(hw64);
   dense::jacobi_free(jw);
+  if (has_tw) tc::free_workspace(tw);
   *this = Refine{};
 }
 
@@ -359,8 +369,8 @@ void Refine::release() {
   } while (0)
 
 rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, cplx* vec_out,
-                            cplx* a64, tc::Workspace* tcw, bool mixed, cudaStream_t st,
-                            std::string& err, int* launches) {
+                            cplx* a64, bool mixed, cudaStream_t st, std::string& err,
+                            int* launches) {
   const int mp = block_size(n, n_eig);
   const bool s32 = mixed && has32 && start32(n, n_eig);
   if (n > max_n || mp > max_mp) {
@@ -474,7 +484,7 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   // default: products exact to ~2^-47 of the row and column scales); a column-major
   // X enters as the row-major conj(X) through a conjugate transpose.  Otherwise
   // they run on the FP64 pipe (dense::gemm_z).
-  const bool on_tc = s32 && tcw != nullptr && products_on_tc();
+  const bool on_tc = s32 && has_tw && products_on_tc();
   const cplx one = {1.0, 0.0}, zero = {0.0, 0.0};
   auto ctrans = [&](const cplx* x, int rows, int cols, cplx* out) -> rpa_status {
     ctrans_kernel<<<dim3((rows + 31) / 32, (cols + 31) / 32), dim3(32, 8), 0, st>>>(x, rows, cols,
@@ -485,17 +495,9 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   };
   auto tc_gemm = [&](const cplx* a_rm, int rows, int k, const cplx* b_rm, int cols,
                      cplx* out) -> rpa_status {
-    // exact digits (whatever the plan's precision) with EIG_SLICES planes
-    const tc::Hook saved = tcw->hook;
-    const int saved_split = tcw->split;
-    tcw->hook = tc::Hook{};
-    tcw->split = 0;
-    tcw->proj_slices_override = tc::EIG_SLICES;
+    // exact digits with EIG_SLICES planes, in the eigensolver's own workspace
     int l = 0;
-    const rpa_status r = tc::project(*tcw, a_rm, RPA_C128, rows, k, b_rm, cols, out, st, err, &l);
-    tcw->hook = saved;
-    tcw->split = saved_split;
-    tcw->proj_slices_override = 0;
+    const rpa_status r = tc::project(tw, a_rm, RPA_C128, rows, k, b_rm, cols, out, st, err, &l);
     nl += l;
     return r;
   };

@@ -52,6 +52,10 @@ struct Refine {
   unsigned long long* absmax = nullptr;
   dense::HetrdWork hw32, hw64;
   dense::JacobiWork jw;
+  // tensor-core workspace of the FP32 start's block products (planes of its own, so
+  // that the projection's operand planes can be cut on the side stream meanwhile)
+  tc::Workspace tw;
+  bool has_tw = false;
   int max_n = 0, max_mp = 0;
   bool has32 = false;
   rpa_status alloc(int n_max, int mp_max, bool with32, std::string& err);
@@ -59,13 +63,12 @@ struct Refine {
   // lam_out[0 .. n_eig) and the column-major n x n_eig vec_out: the N_eig most
   // negative eigenpairs of the column-major view hc (n x n, Hermitian, not
   // modified).  a64: n x n complex128 scratch (may be vec_out).  mixed: a
-  // mixed-precision plan (FP32 start where start32(); products on tcw where
-  // products_on_tc()).  RPA_ENUMERIC: a degenerate spectrum (a cluster of more than
+  // mixed-precision plan (FP32 start where start32(); its block products on the
+  // tensor cores where products_on_tc(), in the workspace tw).  RPA_ENUMERIC: a degenerate spectrum (a cluster of more than
   // 64 eigenvalues of T within 1e-10 of the largest, or no interval to filter):
   // the caller takes the library solver.
   rpa_status subspace(const cplx* hc, int n, int n_eig, double* lam_out, cplx* vec_out,
-                      cplx* a64, tc::Workspace* tcw, bool mixed, cudaStream_t st,
-                      std::string& err, int* launches);
+                      cplx* a64, bool mixed, cudaStream_t st, std::string& err, int* launches);
 };
 
 }  // namespace eig

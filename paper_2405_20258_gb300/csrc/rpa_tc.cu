@@ -81,12 +81,18 @@ constexpr int MMA_N_MAX = 256;  // largest N of a cta_group::1 kind::f16 MMA wit
 constexpr uint32_t A_TILE = BM * BK * 2;  // 16 KB
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 
-// kind::f16 instruction descriptor: D = F32 (bits 4-5), A = B = BF16 (bits 7-9,
-// 10-12), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
-__host__ __device__ constexpr uint32_t idesc_n(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor of kind::f16 (A = B = BF16, code 1) or kind::tf32 (A = B =
+// TF32, code 2): D = F32 (bits 4-5), A and B formats at bits 7-9 and 10-12, both K-major
+// (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t idesc_n(int n, bool tf32 = false) {
+  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+
+// K elements per 128-byte row of a tile: 64 BF16 or 32 TF32 (FP32 storage).
+__host__ __device__ constexpr int bk_elems(bool tf32) { return tf32 ? 32 : 64; }
+constexpr int ROWB = 128;   // bytes per K-major tile row (one 128-byte swizzle row)
+constexpr int KSTEPS = 4;   // MMAs per K-tile: 32 bytes of K each (16 BF16 or 8 TF32)
 
 enum : int {
   ERR_WAIT_PRODUCER = 1,
@@ -202,15 +208,25 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+template <bool TF>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  if constexpr (TF)
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -258,11 +274,12 @@ __device__ __forceinline__ void dfloat_add(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, err);
 }
 
-template <int BN>
+template <int BN, bool TF>
 __global__ void __launch_bounds__(threads_for<BN>(), 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
-  constexpr uint32_t B_TILE = BN * BK * 2;
+  constexpr uint32_t B_TILE = BN * ROWB;
+  constexpr int BKE = bk_elems(TF);  // K elements per tile
   constexpr int CPT = 32;           // accumulator columns per epilogue thread
   constexpr int EPI = BN / 8;       // epilogue warps: 4 lane quadrants x BN/32 column blocks
   constexpr int TS = tmem_stride<BN>();
@@ -325,11 +342,11 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
       const int4 wk = p.work[wi];
       const int tm = wk.x, tn = wk.y, batch = wk.z;
       const int k_begin = wk.w * p.k_per_split;
-      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
+      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BKE;
       const int total = nkt * S;
       int i = 0;
       for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
-        const int k0 = k_begin + kt * BK;
+        const int k0 = k_begin + kt * BKE;
         if (!mbar_wait(&empty_b[bb], bphase ^ 1, &abort_flag, p.status, ERR_WAIT_PRODUCER)) {
           ok = false;
           break;
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
       bool alive = true;
       for (int wi = blockIdx.x; wi < p.n_work && alive; wi += gridDim.x) {
       const int k_begin = p.work[wi].w * p.k_per_split;
-      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
+      const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BKE;
       const int total = nkt * S;
       int i = 0, kin = 0;
       alive = false;
@@ -406,20 +423,20 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           const int rows = s < Le ? BN * (min(S, Le) - s) : 0;
           for (int c0 = 0; c0 < rows; c0 += MMA_N_MAX) {
             const int n = min(MMA_N_MAX, rows - c0);
-            const uint32_t id = idesc_n(n);
-            const uint64_t bd = bd0 + (uint64_t)((c0 * BK * 2) >> 4);
+            const uint32_t id = idesc_n(n, TF);
+            const uint64_t bd = bd0 + (uint64_t)((c0 * ROWB) >> 4);
             const uint32_t d = acc_base + s * TS + c0;
-            mma_bf16(d, ad, bd, id, (s == 0 && first) ? 0u : 1u);
+            mma_issue<TF>(d, ad, bd, id, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
-            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
+            for (int kk = 1; kk < KSTEPS; ++kk) mma_issue<TF>(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
           }
           for (int t = max(0, Le - s); t <= S - 1 - s; ++t) {
-            const uint32_t id = idesc_n(BN);
-            const uint64_t bd = bd0 + (uint64_t)((t * BN * BK * 2) >> 4);
+            const uint32_t id = idesc_n(BN, TF);
+            const uint64_t bd = bd0 + (uint64_t)((t * BN * ROWB) >> 4);
             const uint32_t d = acc_base + Le * TS;
-            mma_bf16(d, ad, bd, id, tail_first ? 0u : 1u);
+            mma_issue<TF>(d, ad, bd, id, tail_first ? 0u : 1u);
 #pragma unroll
-            for (int kk = 1; kk < BK / 16; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
+            for (int kk = 1; kk < KSTEPS; ++kk) mma_issue<TF>(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
             tail_first = false;
           }
           if (s == 0) first = 0;
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
     const int4 wk = p.work[wi];
     const int tm = wk.x, tn = wk.y, batch = wk.z;
     const int k_begin = wk.w * p.k_per_split;
-    const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BK;
+    const int nkt = (min(p.K, k_begin + p.k_per_split) - k_begin) / BKE;
     const int niv = (nkt + kdt - 1) / kdt;
     float hi[CPT], lo[NLO];
 #pragma unroll
@@ -625,18 +642,42 @@ __device__ __forceinline__ void emit_digits(long long yr, long long yi, int S, P
   }
 }
 
-// Round-to-nearest BF16 split of the row-scaled value y = x 2^(7 - e), |y| < 128:
-// hi = bf16(y), then each further plane the BF16 rounding of what the earlier
-// planes leave (the classic hi/lo split).  Used by the split precisions
-// (RPA_MIXED_BF16X3 / X6), whose products are summed in FP32 over the whole K.
-template <class Put>
+// Digit planes hold (re, im) pairs of BF16 (kind::f16) or of TF32 values in FP32
+// storage (kind::tf32, the split precision RPA_MIXED_TF32X3).
+template <typename P>
+struct PlaneT;
+template <>
+struct PlaneT<__nv_bfloat162> {
+  __device__ static void put(__nv_bfloat162* p, float a, float b) {
+    *p = __floats2bfloat162_rn(a, b);
+  }
+  // round-to-nearest BF16
+  __device__ static float round(double y) { return __bfloat162float(__double2bfloat16(y)); }
+};
+template <>
+struct PlaneT<float2> {
+  __device__ static void put(float2* p, float a, float b) { *p = make_float2(a, b); }
+  // round to nearest FP32, then to TF32 (10 stored mantissa bits, ties away)
+  __device__ static float round(double y) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)y));
+    return __uint_as_float(r);
+  }
+};
+
+// Round-to-nearest split of the row-scaled value y = x 2^(7 - e), |y| < 128: the first
+// plane the plane type's rounding of y, each further plane the rounding of what the
+// earlier planes leave (the classic hi/lo split).  Used by the split precisions
+// (RPA_MIXED_BF16X3 / X6, RPA_MIXED_TF32X3), whose products are summed in FP32 over
+// the whole K.
+template <typename P, class Put>
 __device__ __forceinline__ void emit_split(double xr, double xi, int e, int S, Put put) {
   const double sc = ldexp(1.0, 7 - e);
   double yr = xr * sc, yi = xi * sc;
 #pragma unroll 1
   for (int s = 0; s < S; ++s) {
-    const float hr = __bfloat162float(__double2bfloat16(yr));
-    const float hi = __bfloat162float(__double2bfloat16(yi));
+    const float hr = PlaneT<P>::round(yr);
+    const float hi = PlaneT<P>::round(yi);
     put(s, hr, hi);
     yr -= (double)hr;
     yi -= (double)hi;
@@ -705,10 +746,11 @@ __global__ void chi0_rowmax_kernel(const void* A, int dtype, const int* order, i
 // (x_r, x_i), row 2g+1 holds (x_i, -x_r), so that Re chi = X_g . X_h and
 // Im chi = X_g . Y_h.  One 32 x 32 (vc, g) tile per block, transposed through
 // shared memory so that the plane rows are written contiguously.
+template <typename P>
 __global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, int n_vc, int n_g,
                                   int n_g_pad, long K, const double* sf,
-                                  const unsigned long long* rowmax, int S,
-                                  __nv_bfloat162* planes, int* exps, int split) {
+                                  const unsigned long long* rowmax, int S, P* planes, int* exps,
+                                  int split) {
   __shared__ double2 t[32][33];
   __shared__ int es[32];
   const int vc0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
@@ -739,14 +781,14 @@ __global__ void chi0_slice_kernel(const void* A, int dtype, const int* order, in
     const int vc = vc0 + tx;  // K pair index
     if ((long)2 * vc >= K) continue;
     double2 x = t[tx][r];
-    __nv_bfloat162* p = planes + (long)(2 * g) * (K / 2) + vc;
+    P* p = planes + (long)(2 * g) * (K / 2) + vc;
     auto put = [&](int s, float fr, float fi) {
-      __nv_bfloat162* p0 = p + s * plane;
-      p0[0] = __floats2bfloat162_rn(fr, fi);
-      p0[K / 2] = __floats2bfloat162_rn(fi, -fr);
+      P* p0 = p + s * plane;
+      PlaneT<P>::put(p0, fr, fi);
+      PlaneT<P>::put(p0 + K / 2, fi, -fr);
     };
     if (split)
-      emit_split(x.x, x.y, es[r], S, put);
+      emit_split<P>(x.x, x.y, es[r], S, put);
     else
       emit_digits(digits_y(x.x, es[r], S), digits_y(x.y, es[r], S), S, put);
   }
@@ -779,10 +821,11 @@ __global__ void row_max_kernel(const void* src, int dtype, long ld, int n_rows, 
 
 // Row slicing: planes [S][rows_pad][K] with K index 2 k + part, from the row
 // maxima; grid (rows_pad, K/2 chunks).
+template <typename P>
 __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_rows, int n_cplx,
                                   int rows_pad, long K, int S,
-                                  const unsigned long long* rowmax, __nv_bfloat162* planes,
-                                  int* exps, int split) {
+                                  const unsigned long long* rowmax, P* planes, int* exps,
+                                  int split) {
   const int r = blockIdx.x;
   const int e = r < n_rows ? row_exponent(__longlong_as_double((long long)rowmax[r])) : 0;
   if (blockIdx.y == 0 && threadIdx.x == 0) exps[r] = e;
@@ -791,10 +834,10 @@ __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_row
   for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     double2 x = make_double2(0.0, 0.0);
     if (r < n_rows && k < n_cplx) x = load_any(src, dtype, (long)r * ld + k);
-    __nv_bfloat162* p = planes + (long)r * (K / 2) + k;
-    auto put = [&](int s, float fr, float fi) { p[s * plane] = __floats2bfloat162_rn(fr, fi); };
+    P* p = planes + (long)r * (K / 2) + k;
+    auto put = [&](int s, float fr, float fi) { PlaneT<P>::put(p + s * plane, fr, fi); };
     if (split)
-      emit_split(x.x, x.y, e, S, put);
+      emit_split<P>(x.x, x.y, e, S, put);
     else
       emit_digits(digits_y(x.x, e, S), digits_y(x.y, e, S), S, put);
   }
@@ -802,8 +845,9 @@ __global__ void slice_rows_kernel(const void* src, int dtype, long ld, int n_row
 
 // Projection B operand from B[g][i] (= v^1/2 C): rows 2i = (b_r, -b_i) and
 // 2i+1 = (b_i, b_r) along K index 2g + part; one block per i.
+template <typename P>
 __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_eig_pad, long K,
-                                    int S, __nv_bfloat162* planes, int* exps, int split) {
+                                    int S, P* planes, int* exps, int split) {
   __shared__ double red[32];
   const int i = blockIdx.x;
   double m = 0.0;
@@ -827,14 +871,14 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
   for (long g = threadIdx.x; g < K / 2; g += blockDim.x) {
     double2 b = make_double2(0.0, 0.0);
     if (i < n_eig && g < n_g) b = B[g * n_eig + i];
-    __nv_bfloat162* p = planes + (long)(2 * i) * (K / 2) + g;
+    P* p = planes + (long)(2 * i) * (K / 2) + g;
     auto put = [&](int s, float fr, float fi) {
-      __nv_bfloat162* p0 = p + s * plane;
-      p0[0] = __floats2bfloat162_rn(fr, -fi);
-      p0[K / 2] = __floats2bfloat162_rn(fi, fr);
+      P* p0 = p + s * plane;
+      PlaneT<P>::put(p0, fr, -fi);
+      PlaneT<P>::put(p0 + K / 2, fi, fr);
     };
     if (split)
-      emit_split(b.x, b.y, e, S, put);
+      emit_split<P>(b.x, b.y, e, S, put);
     else
       emit_digits(digits_y(b.x, e, S), digits_y(b.y, e, S), S, put);
   }
@@ -898,10 +942,11 @@ __global__ void float_up_kernel(const double* f, long n, float* out) {
 
 // chi_s B operand of the group's frequencies: for row j, f_b(vc) M~[j][vc] as
 // rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); grid (n_eig_pad, chunks).
+template <typename P>
 __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
                                     long K, const double* f, int nb, int S,
-                                    const unsigned long long* rowmax, __nv_bfloat162* planes,
-                                    int* exps, int eb_stride, int split) {
+                                    const unsigned long long* rowmax, P* planes, int* exps,
+                                    int eb_stride, int split) {
   const int j = blockIdx.x;
   __shared__ int e[MAX_GROUP];
   if (threadIdx.x < MAX_GROUP) {
@@ -921,12 +966,12 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
 #pragma unroll 1
     for (int b = 0; b < nb; ++b) {
       const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
-      __nv_bfloat162* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
+      P* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
       if (split) {
-        emit_split(fv * x.x, fv * x.y, e[b], S, [&](int s, float fr, float fi) {
-          __nv_bfloat162* p0 = p + s * plane;
-          p0[0] = __floats2bfloat162_rn(fr, fi);
-          p0[K / 2] = __floats2bfloat162_rn(-fi, fr);
+        emit_split<P>(fv * x.x, fv * x.y, e[b], S, [&](int s, float fr, float fi) {
+          P* p0 = p + s * plane;
+          PlaneT<P>::put(p0, fr, fi);
+          PlaneT<P>::put(p0 + K / 2, -fi, fr);
         });
         continue;
       }
@@ -939,9 +984,9 @@ __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad,
         yi = digits_y(fv * x.y, e[b], S);
       }
       emit_digits(yr, yi, S, [&](int s, float fr, float fi) {
-        __nv_bfloat162* p0 = p + s * plane;
-        p0[0] = __floats2bfloat162_rn(fr, fi);
-        p0[K / 2] = __floats2bfloat162_rn(-fi, fr);
+        P* p0 = p + s * plane;
+        PlaneT<P>::put(p0, fr, fi);
+        PlaneT<P>::put(p0 + K / 2, -fi, fr);
       });
     }
   }
@@ -992,10 +1037,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D map over BF16 planes: dim0 = K (contiguous), dim1 = rows (row_bytes apart),
-// dim2 = plane (plane_bytes apart); box K 64 x box_rows x 1, 128-byte swizzle.
+// 3-D map over digit planes (BF16, or TF32 in FP32 storage when tf32): dim0 = K
+// (contiguous), dim1 = rows (row_bytes apart), dim2 = plane (plane_bytes apart); box
+// 128 bytes of K x box_rows x 1, 128-byte swizzle.
 bool make_map(CUtensorMap* m, void* base, long K, long rows, long planes, long row_bytes,
-              long plane_bytes, int box_rows, std::string& err) {
+              long plane_bytes, int box_rows, std::string& err, bool tf32 = false) {
   auto fn = encode_fn();
   if (!fn) {
     err = "cuTensorMapEncodeTiled unavailable";
@@ -1003,11 +1049,12 @@ bool make_map(CUtensorMap* m, void* base, long K, long rows, long planes, long r
   }
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)plane_bytes};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bk_elems(tf32), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                  base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char b[160];
     snprintf(b, sizeof b, "cuTensorMapEncodeTiled failed (%d): K=%ld rows=%ld planes=%ld", (int)r,
@@ -1069,8 +1116,9 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   const int BN = pick_bn(a.S, a.nexact);
   const int tiles_n = cdiv(a.b_rows, BN);
   // split precisions sum in FP32 over the whole K (one drain at the end)
-  const int kdt = w.split ? std::max(1, a.K / BK) : drain_tiles(std::min(a.nexact, a.S));
-  const int kd = kdt * BK;
+  const int bke = bk_elems(w.tf32 != 0);
+  const int kdt = w.split ? std::max(1, a.K / bke) : drain_tiles(std::min(a.nexact, a.S));
+  const int kd = kdt * bke;
   int tiles = 0;
   for (int b = 0; b < batches; ++b)
     for (int m = 0; m < tiles_m; ++m)
@@ -1152,21 +1200,28 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   if (!lim_dev.smem) {
     // opt-in shared memory per block minus the kernels' static shared memory
     int optin = 0, sms = 0;
-    cudaFuncAttributes fa64{}, fa128{};
+    cudaFuncAttributes fa[4]{};
+    const void* kern[4] = {(const void*)slice_gemm_kernel<64, false>,
+                           (const void*)slice_gemm_kernel<128, false>,
+                           (const void*)slice_gemm_kernel<64, true>,
+                           (const void*)slice_gemm_kernel<128, true>};
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
-            cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa64, slice_gemm_kernel<64>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa128, slice_gemm_kernel<128>)) != cudaSuccess) {
+        cudaSuccess) {
       err = std::string("querying shared memory limits: ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
-    size_t lim = (size_t)optin - std::max(fa64.sharedSizeBytes, fa128.sharedSizeBytes);
-    if ((e = cudaFuncSetAttribute(slice_gemm_kernel<64>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
-            cudaSuccess ||
-        (e = cudaFuncSetAttribute(slice_gemm_kernel<128>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim)) !=
-            cudaSuccess) {
+    size_t stat = 0;
+    for (int i = 0; i < 4; ++i) {
+      if ((e = cudaFuncGetAttributes(&fa[i], kern[i])) != cudaSuccess) {
+        err = std::string("querying shared memory limits: ") + cudaGetErrorString(e);
+        return RPA_ECUDA;
+      }
+      stat = std::max(stat, fa[i].sharedSizeBytes);
+    }
+    size_t lim = (size_t)optin - stat;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaFuncSetAttribute(kern[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if (e != cudaSuccess) {
       err = std::string("cudaFuncSetAttribute(max dynamic smem): ") + cudaGetErrorString(e);
       return RPA_ECUDA;
     }
@@ -1190,10 +1245,17 @@ rpa_status run_gemm(Workspace& w, const CUtensorMap& ta, const CUtensorMap& tb, 
   a.n_work = (int)work.size();
   const unsigned grid = (unsigned)std::min<long>(
       a.n_work, std::max(1, env_int("RPA_TC_GRID", limits.sms > 0 ? limits.sms : a.n_work)));
-  if (BN == 128)
-    slice_gemm_kernel<128><<<grid, threads_for<128>(), smem, st>>>(ta, tb, a);
-  else
-    slice_gemm_kernel<64><<<grid, threads_for<64>(), smem, st>>>(ta, tb, a);
+  if (w.tf32) {
+    if (BN == 128)
+      slice_gemm_kernel<128, true><<<grid, threads_for<128>(), smem, st>>>(ta, tb, a);
+    else
+      slice_gemm_kernel<64, true><<<grid, threads_for<64>(), smem, st>>>(ta, tb, a);
+  } else {
+    if (BN == 128)
+      slice_gemm_kernel<128, false><<<grid, threads_for<128>(), smem, st>>>(ta, tb, a);
+    else
+      slice_gemm_kernel<64, false><<<grid, threads_for<64>(), smem, st>>>(ta, tb, a);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("slice GEMM launch: ") + cudaGetErrorString(e);
@@ -1313,9 +1375,12 @@ static rpa_status side_fork(Workspace& w, cudaStream_t st, std::string& err) {
   return RPA_OK;
 }
 
-rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
+template <typename P>
+rpa_status chi0_t(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
                 const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
                 std::string& err, int* launches, bool zero, int blocks) {
+  constexpr int EB = (int)sizeof(P) / 2;  // bytes of one plane element
+  constexpr bool TFP = sizeof(P) == 8;
   const int S = w.slices.chi0, Le = w.split ? 1 : exact_levels_chi0(S);
   const long g_pad = rup(n_g, BM);
   // K-blocks of the transitions in `order` (sorted by sqrt f(0)): each block has
@@ -1335,7 +1400,7 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
     const int buf = b & 1;
     const int nr = (int)std::min<long>(per, n_vc - r0);
     const long K = rup(2L * nr, BK);
-    __nv_bfloat162* planes = (__nv_bfloat162*)w.planes + buf * (buf_elems / 2);
+    P* planes = (P*)w.planes + buf * (buf_elems / 2);
     int* exps = w.exps + buf * g_pad;
     unsigned long long* rowmax = w.rowmax + buf * g_pad;
     if (b >= 2) CK(cudaStreamWaitEvent(w.side, w.ev_gemm[buf], 0));
@@ -1347,7 +1412,7 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
     }
     {
       dim3 grid(cdiv(K / 2, 32), cdiv(g_pad, 32));
-      chi0_slice_kernel<<<grid, dim3(32, 8), 0, w.side>>>(A, dtype, order + r0, nr, n_g,
+      chi0_slice_kernel<P><<<grid, dim3(32, 8), 0, w.side>>>(A, dtype, order + r0, nr, n_g,
                                                           (int)g_pad, K, sf, rowmax, S, planes,
                                                           exps, w.split);
       CK(cudaGetLastError());
@@ -1360,10 +1425,10 @@ rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const
     CK(cudaStreamWaitEvent(st, w.ev_sliced[buf], 0));
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap ta, tb;
-    const long plane_bytes = 2 * g_pad * K * 2;
+    const long plane_bytes = 2 * g_pad * K * EB;
     // A view: even rows of the planes (X_g); B: all rows (X_h, Y_h interleaved)
-    if (!make_map(&ta, planes, K, g_pad, S, 2 * K * 2, plane_bytes, BM, err)) return RPA_ECUDA;
-    if (!make_map(&tb, planes, K, 2 * g_pad, S, K * 2, plane_bytes, pick_bn(S, Le), err))
+    if (!make_map(&ta, planes, K, g_pad, S, 2 * K * EB, plane_bytes, BM, err, TFP)) return RPA_ECUDA;
+    if (!make_map(&tb, planes, K, 2 * g_pad, S, K * EB, plane_bytes, pick_bn(S, Le), err, TFP))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
@@ -1406,6 +1471,7 @@ static const void* a_rows_at(const void* A, int dtype, long row, int n_g) {
 }
 
 // rows [r0, r0 + nr) of A -> S digit planes of the projection's A operand and exponents ea
+template <typename P>
 static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, long r0, int nr, int n_g,
                                cudaStream_t s, std::string& err, int* launches) {
   const int S = w.proj_slices_override > 0 ? w.proj_slices_override : w.slices.proj;
@@ -1415,20 +1481,21 @@ static rpa_status slice_proj_a(Workspace& w, const void* A, int dtype, long r0, 
   row_max_kernel<<<dim3((unsigned)nr, cdiv(n_g, CHUNK)), 256, 0, s>>>(a0, dtype, n_g, nr, n_g,
                                                                       w.rowmax);
   CK(cudaGetLastError());
-  slice_rows_kernel<<<dim3((unsigned)rpad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
-      a0, dtype, n_g, nr, n_g, (int)rpad, K, S, w.rowmax, (__nv_bfloat162*)w.planes, w.exps,
+  slice_rows_kernel<P><<<dim3((unsigned)rpad, cdiv(K / 2, CHUNK)), 256, 0, s>>>(
+      a0, dtype, n_g, nr, n_g, (int)rpad, K, S, w.rowmax, (P*)w.planes, w.exps,
       w.split);
   CK(cudaGetLastError());
   if (launches) *launches += 2;
   return RPA_OK;
 }
 
-rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+template <typename P>
+rpa_status project_prepare_t(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
                            cudaStream_t st, std::string& err, int* launches) {
   w.proj_a.valid = false;
   if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
   const int nr = (int)std::min<long>(n_vc, proj_chunk_rows(w, n_vc));  // the first chunk
-  rpa_status r = slice_proj_a(w, A, dtype, 0, nr, n_g, w.side, err, launches);
+  rpa_status r = slice_proj_a<P>(w, A, dtype, 0, nr, n_g, w.side, err, launches);
   if (r != RPA_OK) return r;
   CK(cudaEventRecord(w.ev_side_last, w.side));
   w.proj_a.valid = true;
@@ -1440,22 +1507,25 @@ rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int
   return RPA_OK;
 }
 
-rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
+template <typename P>
+rpa_status project_t(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
                    int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches,
                    long ld_out) {
+  constexpr int EB = (int)sizeof(P) / 2;  // bytes of one plane element
+  constexpr bool TFP = sizeof(P) == 8;
   if (ld_out <= 0) ld_out = n_vc;
   const int S = w.proj_slices_override > 0 ? w.proj_slices_override : w.slices.proj;
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_g, BK);
   // rows of A cut at a time: the budgeted chunk, and no more than the plane buffer
   // holds at this slice count
-  const long fit = (long)(w.plane_bytes / ((size_t)S * K * 2)) / BM * BM;
+  const long fit = (long)(w.plane_bytes / ((size_t)S * K * EB)) / BM * BM;
   const long chunk = std::min(proj_chunk_rows(w, n_vc), fit);
-  if (chunk < BM || (size_t)S * 2 * e_pad * K * 2 > w.plane2_bytes) {
+  if (chunk < BM || (size_t)S * 2 * e_pad * K * EB > w.plane2_bytes) {
     err = "projection: operand planes exceed the workspace";
     return RPA_EINVAL;
   }
   const bool chunked = chunk < n_vc;
-  __nv_bfloat162* pb = (__nv_bfloat162*)w.planes2;
+  P* pb = (P*)w.planes2;
   int* ea = w.exps;
   int* eb = w.exps + std::max({rup(n_g, BM), rup(std::min<long>(chunk, n_vc), BM), e_pad});
   const bool ready = w.proj_a.valid && w.proj_a.a == A && w.proj_a.dtype == dtype &&
@@ -1463,7 +1533,7 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   w.proj_a.valid = false;  // the chi_s stage reuses the planes next
   w.hook(RPA_T_SLICE, 1);
   if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
-  proj_b_slice_kernel<<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
+  proj_b_slice_kernel<P><<<(unsigned)e_pad, 256, 0, st>>>((const double2*)B, n_g, n_eig, (int)e_pad,
                                                        K, S, pb, eb, w.split);
   CK(cudaGetLastError());
   if (launches) *launches += 1;
@@ -1477,19 +1547,20 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   w.hook(RPA_T_SLICE, 0);
   const int Le = w.split ? 1 : exact_levels_proj(S);
   CUtensorMap tb;
-  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le), err))
+  if (!make_map(&tb, w.planes2, K, 2 * e_pad, S, K * EB, 2 * e_pad * K * EB, pick_bn(S, Le), err,
+                TFP))
     return RPA_ECUDA;
   for (long r0 = 0; r0 < n_vc; r0 += chunk) {
     const int nr = (int)std::min<long>(chunk, n_vc - r0);
     const long rpad = rup(nr, BM);
     if (r0 > 0 || !ready) {
       w.hook(RPA_T_SLICE, 1);
-      rpa_status r = slice_proj_a(w, A, dtype, r0, nr, n_g, st, err, launches);
+      rpa_status r = slice_proj_a<P>(w, A, dtype, r0, nr, n_g, st, err, launches);
       w.hook(RPA_T_SLICE, 0);
       if (r != RPA_OK) return r;
     }
     CUtensorMap ta;
-    if (!make_map(&ta, w.planes, K, rpad, S, K * 2, rpad * K * 2, BM, err)) return RPA_ECUDA;
+    if (!make_map(&ta, w.planes, K, rpad, S, K * EB, rpad * K * EB, BM, err, TFP)) return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
     a.nexact = Le;
@@ -1516,13 +1587,16 @@ rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, co
   return RPA_OK;
 }
 
-rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
+template <typename P>
+rpa_status chis_t(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
                 int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
                 int* launches) {
+  constexpr int EB = (int)sizeof(P) / 2;  // bytes of one plane element
+  constexpr bool TFP = sizeof(P) == 8;
   const int S = w.slices.chis, Le = w.split ? 1 : exact_levels_chis(S);
   const long e_pad = rup(n_eig, BM), K = rup(2L * n_vc, BK);
   const int grp = w.freq_group;
-  __nv_bfloat162* pa = (__nv_bfloat162*)w.planes2;
+  P* pa = (P*)w.planes2;
   int* ea = w.exps;
   w.proj_a.valid = false;
   w.hook(RPA_T_SLICE, 1);
@@ -1531,7 +1605,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   row_max_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(mt, RPA_C128, n_vc,
                                                                             n_eig, n_vc, w.rowmax);
   CK(cudaGetLastError());
-  slice_rows_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
+  slice_rows_kernel<P><<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
       mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea, w.split);
   CK(cudaGetLastError());
   float_up_kernel<<<std::min(cdiv((long)n_freq * n_vc, 256), 4096), 256, 0, st>>>(
@@ -1540,7 +1614,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   if (launches) *launches += 3;
   w.hook(RPA_T_SLICE, 0);
   CUtensorMap ta;
-  if (!make_map(&ta, w.planes2, K, e_pad, S, K * 2, e_pad * K * 2, BM, err)) return RPA_ECUDA;
+  if (!make_map(&ta, w.planes2, K, e_pad, S, K * EB, e_pad * K * EB, BM, err, TFP)) return RPA_ECUDA;
   const int tiles_m = cdiv(n_eig, BM);
   // B planes of frequency groups in two alternating buffers: group g + 1 is cut
   // on the side stream while group g is multiplied on `st`.
@@ -1550,7 +1624,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
   int g = 0;
   for (int k0 = 0; k0 < n_freq; k0 += grp, ++g) {
     const int nb = std::min(grp, n_freq - k0), buf = g & 1;
-    __nv_bfloat162* pb = (__nv_bfloat162*)w.planes + buf * buf_pairs;
+    P* pb = (P*)w.planes + buf * buf_pairs;
     int* eb = w.exps + e_pad + (size_t)buf * grp * e_pad;
     unsigned long long* rowmax = w.rowmax + (size_t)buf * grp * e_pad;
     if (g >= 2) CK(cudaStreamWaitEvent(cut, w.ev_gemm[buf], 0));
@@ -1560,7 +1634,7 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
         (const double2*)mt, n_eig, n_vc, w.fweights + (size_t)k0 * n_vc, f + (size_t)k0 * n_vc,
         nb, rowmax, (int)e_pad);
     CK(cudaGetLastError());
-    chis_b_slice_kernel<<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
+    chis_b_slice_kernel<P><<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, (int)e_pad, n_vc, K, f + (size_t)k0 * n_vc, nb, S, rowmax, pb,
         eb, (int)e_pad, w.split);
     CK(cudaGetLastError());
@@ -1571,8 +1645,8 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
     CK(cudaStreamWaitEvent(st, w.ev_sliced[buf], 0));
     w.hook(RPA_T_SLICE, 0);
     CUtensorMap tb;
-    if (!make_map(&tb, pb, K, 2 * e_pad, (long)nb * S, K * 2, 2 * e_pad * K * 2, pick_bn(S, Le),
-                  err))
+    if (!make_map(&tb, pb, K, 2 * e_pad, (long)nb * S, K * EB, 2 * e_pad * K * EB, pick_bn(S, Le),
+                  err, TFP))
       return RPA_ECUDA;
     GemmArgs a{};
     a.S = S;
@@ -1597,6 +1671,39 @@ rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double*
     CK(cudaEventRecord(w.ev_gemm[buf], st));
   }
   return RPA_OK;
+}
+
+
+rpa_status chi0(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const double* sf,
+                const int* order, const double* sv, double scale, cplx* chi, cudaStream_t st,
+                std::string& err, int* launches, bool zero, int blocks) {
+  return w.tf32 ? chi0_t<float2>(w, A, dtype, n_vc, n_g, sf, order, sv, scale, chi, st, err,
+                                 launches, zero, blocks)
+                : chi0_t<__nv_bfloat162>(w, A, dtype, n_vc, n_g, sf, order, sv, scale, chi, st,
+                                         err, launches, zero, blocks);
+}
+
+rpa_status project_prepare(Workspace& w, const void* A, int dtype, int n_vc, int n_g,
+                           cudaStream_t st, std::string& err, int* launches) {
+  return w.tf32 ? project_prepare_t<float2>(w, A, dtype, n_vc, n_g, st, err, launches)
+                : project_prepare_t<__nv_bfloat162>(w, A, dtype, n_vc, n_g, st, err, launches);
+}
+
+rpa_status project(Workspace& w, const void* A, int dtype, int n_vc, int n_g, const cplx* B,
+                   int n_eig, cplx* mt, cudaStream_t st, std::string& err, int* launches,
+                   long ld_out) {
+  return w.tf32 ? project_t<float2>(w, A, dtype, n_vc, n_g, B, n_eig, mt, st, err, launches,
+                                    ld_out)
+                : project_t<__nv_bfloat162>(w, A, dtype, n_vc, n_g, B, n_eig, mt, st, err,
+                                            launches, ld_out);
+}
+
+rpa_status chis(Workspace& w, const cplx* mt, int n_eig, int n_vc, const double* f,
+                int n_freq, double scale, cplx* out, cudaStream_t st, std::string& err,
+                int* launches) {
+  return w.tf32 ? chis_t<float2>(w, mt, n_eig, n_vc, f, n_freq, scale, out, st, err, launches)
+                : chis_t<__nv_bfloat162>(w, mt, n_eig, n_vc, f, n_freq, scale, out, st, err,
+                                         launches);
 }
 
 }  // namespace tc

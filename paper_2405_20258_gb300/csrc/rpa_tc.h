@@ -66,6 +66,7 @@ struct Workspace {
   int chi0_blocks = 32;       // K-blocks of chi~(0) (transitions sorted by sqrt f(0))
   int split = 0;              // 1: round-to-nearest BF16 hi/lo split planes, FP32 sums over K
   int proj_slices_override = 0;  // > 0: slice count of project() (the eigensolver's products)
+  int tf32 = 0;               // 1: planes of TF32 values (FP32 storage), kind::tf32 MMAs
   int debug_stall = 0;
   Hook hook;
   // Side stream for digit slicing that overlaps the GEMMs and the eigensolve

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librpa.so")
 
 RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_EEIG, RPA_ENUMERIC, RPA_ETIMEOUT, RPA_ESTATE = range(8)
-RPA_FP64, RPA_MIXED, RPA_MIXED_BF16X3, RPA_MIXED_BF16X6 = 0, 1, 2, 3
+RPA_FP64, RPA_MIXED, RPA_MIXED_BF16X3, RPA_MIXED_BF16X6, RPA_MIXED_TF32X3 = 0, 1, 2, 3, 4
 RPA_ROUTE_CHOLESKY, RPA_ROUTE_EIG = 0, 1
 RPA_C128, RPA_C64 = 0, 1
 RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
