@@ -241,6 +241,25 @@ rpa_status rpa_trace_term_static(const void* mtilde, int n_eig, int n_v, int n_c
                                  const double* e_v, const double* e_c, const double* omega,
                                  int n_freq, double omega_cell, double* trace_out, void* stream);
 
+/* Building blocks of the subspace step (a3), for checking each on its own.  Both
+ * allocate their scratch per call and synchronise `stream` (a cudaStream_t, NULL:
+ * the legacy default stream).  Errors: RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA,
+ * RPA_ETIMEOUT (a grid barrier gave up waiting); message in rpa_last_error(NULL).
+ *
+ * rpa_tridiagonalize: the Householder reduction that starts the eigensolver,
+ * T = Q^H A Q real symmetric tridiagonal, in FP32 (bits = 32: a is complex64) or
+ * FP64 (bits = 64: complex128).  a: device, n x n Hermitian, column-major, full
+ * storage; overwritten with the reflectors.  d: device, n reals (float or double
+ * as bits), the diagonal of T; e: device, n-1 reals, its off-diagonal.
+ *
+ * rpa_hermitian_eig_jacobi: all eigenpairs of a Hermitian m x m matrix (m <=
+ * 4096) by the cyclic two-sided Jacobi solver of the Rayleigh-Ritz step, in FP64.
+ * g: device, complex128 column-major, destroyed; theta: device, m doubles,
+ * ascending; y: device, complex128 m x m column-major, the eigenvectors in the
+ * same order. */
+rpa_status rpa_tridiagonalize(int n, int bits, void* a, void* d, void* e, void* stream);
+rpa_status rpa_hermitian_eig_jacobi(int m, void* g, double* theta, void* y, void* stream);
+
 /* Library version string. */
 const char* rpa_version(void);
 

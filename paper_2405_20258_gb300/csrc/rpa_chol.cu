@@ -56,15 +56,19 @@ __global__ void __launch_bounds__(THREADS) potrf_tile_kernel(cplx* a, int n, int
                                                              int* bad) {
   __shared__ cplx t[NB][NB + 1];
   __shared__ cplx u[NB][NB + 1];
-  __shared__ double piv;
+  __shared__ double piv[NB];
+  __shared__ double rpiv;
   const int b = blockIdx.x, tid = threadIdx.x;
   cplx* m = a + (size_t)b * n * n;
   for (int e = tid; e < NB * NB; e += THREADS) {
     const int i = e / NB, j = e % NB;
     t[i][j] = (i < kb && j <= i) ? m[(size_t)(k0 + i) * n + k0 + j] : cplx{0.0, 0.0};
+    u[i][j] = cplx{(i == j && i < kb) ? 1.0 : 0.0, 0.0};
   }
   __syncthreads();
-  double ld = 0.0;
+  // Column j: the pivot, then column j of L and row j of X = L^-1 scaled by 1 / L_jj,
+  // then the trailing update of the tile and X(j+1:, 0:j] -= L(j+1:, j) X(j, 0:j]
+  // (forward elimination of the identity: X is final when the loop ends).
   for (int j = 0; j < kb; ++j) {
     if (tid == 0) {
       double d = t[j][j].re;
@@ -72,15 +76,20 @@ __global__ void __launch_bounds__(THREADS) potrf_tile_kernel(cplx* a, int n, int
         atomicOr(bad, 16);
         d = 1.0;
       }
-      piv = sqrt(d);
-      t[j][j] = cplx{piv, 0.0};
-      ld += 2.0 * log(piv);
+      const double pj = sqrt(d);
+      piv[j] = pj;
+      rpiv = 1.0 / pj;
+      t[j][j] = cplx{pj, 0.0};
     }
     __syncthreads();
-    const double p = piv;
-    for (int i = j + 1 + tid; i < kb; i += THREADS) {
-      t[i][j].re /= p;
-      t[i][j].im /= p;
+    const double rp = rpiv;
+    if (tid > j && tid < kb) {
+      t[tid][j].re *= rp;
+      t[tid][j].im *= rp;
+    } else if (tid >= NB && tid - NB <= j) {
+      const int c = tid - NB;
+      u[j][c].re *= rp;
+      u[j][c].im *= rp;
     }
     __syncthreads();
     const int rem = kb - j - 1;
@@ -92,34 +101,25 @@ __global__ void __launch_bounds__(THREADS) potrf_tile_kernel(cplx* a, int n, int
       t[i][c].re -= li.re * lc.re + li.im * lc.im;
       t[i][c].im -= li.im * lc.re - li.re * lc.im;
     }
+    for (int e = tid; e < rem * (j + 1); e += THREADS) {
+      const int i = j + 1 + e / (j + 1), c = e % (j + 1);
+      const cplx l = t[i][j], x = u[j][c];
+      u[i][c].re -= l.re * x.re - l.im * x.im;
+      u[i][c].im -= l.re * x.im + l.im * x.re;
+    }
     __syncthreads();
   }
-  // inverse X of the lower-triangular L by forward substitution, one column per thread:
-  // X[i][c] = (delta_ic - sum_{c <= q < i} L[i][q] X[q][c]) / L[i][i]
-  if (tid < NB) {
-    const int c = tid;
-    for (int i = 0; i < NB; ++i) {
-      if (i < c || c >= kb || i >= kb) {
-        u[i][c] = cplx{0.0, 0.0};
-        continue;
-      }
-      cplx s = cplx{i == c ? 1.0 : 0.0, 0.0};
-      for (int q = c; q < i; ++q) {
-        const cplx l = t[i][q], x = u[q][c];
-        s.re -= l.re * x.re - l.im * x.im;
-        s.im -= l.re * x.im + l.im * x.re;
-      }
-      const double dinv = 1.0 / t[i][i].re;
-      u[i][c] = cplx{s.re * dinv, s.im * dinv};
-    }
-  }
-  __syncthreads();
   for (int e = tid; e < NB * NB; e += THREADS) {
     const int i = e / NB, j = e % NB;
     if (i < kb && j <= i) m[(size_t)(k0 + i) * n + k0 + j] = t[i][j];
     inv[(size_t)b * NB * NB + e] = u[i][j];
   }
-  if (tid == 0 && logdet) logdet[b] += ld;
+  // 2 sum_j ln L_jj of this tile (the logarithms in parallel, summed in a fixed order)
+  if (logdet && tid < 32) {
+    double l = tid < kb ? 2.0 * log(piv[tid]) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (tid == 0) logdet[b] += l;
+  }
 }
 
 // L_ik = A_ik L_kk^-H for the tiles below the diagonal tile: blockIdx.x = tile row

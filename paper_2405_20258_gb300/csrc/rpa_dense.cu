@@ -76,45 +76,75 @@ __device__ __forceinline__ cplx ldcg_c(const cplx* p) {
   return cplx{v.x, v.y};
 }
 
-// Grid-wide barrier: bar[0] arrivals, bar[1] generation, bar[2] abort.  gen is the
-// generation this CTA last passed (kept by thread 0).  false: a wait ran out here
-// or in another CTA; the caller returns.
+// Grid-wide barrier among the nblocks CTAs of a cooperative launch.  bar[2] is the
+// abort word.  CTA g publishes the generation it has reached in a 64-byte line of
+// its own, bar[BAR_FLAGS + BAR_STRIDE g] (a release store after a CTA barrier), and
+// warp 0 of every CTA polls the lines of all CTAs until each has reached the
+// generation (then an acquire fence): no read-modify-write on one shared word, so
+// the arrivals do not queue at one L2 address.  gen is the generation this CTA last
+// passed (kept by the lanes of warp 0).  false: a wait ran out here or in another
+// CTA; the caller returns.
+constexpr int BAR_FLAGS = 32;   // words before the first flag line (bar[2]: abort)
+constexpr int BAR_STRIDE = 16;  // words per flag line
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* status,
                              int code) {
   __shared__ int ok_s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned target = gen + 1;
-    __threadfence();
-    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-      atomicExch(&bar[0], 0u);
+  if (threadIdx.x < 32) {
+    const unsigned lane = threadIdx.x, target = gen + 1;
+    if (lane == 0) {
       __threadfence();
-      atomicExch(&bar[1], target);
-    } else {
-      const long long t0 = clock64();
-      while (true) {
-        if (*(volatile unsigned*)&bar[1] == target) break;
-        if (*(volatile unsigned*)&bar[2]) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > kWaitCycles) {
+      st_release_u32(&bar[BAR_FLAGS + BAR_STRIDE * blockIdx.x], target);
+    }
+    // lane l watches the flags of CTAs l, l + 32, ...
+    const unsigned nu = (nblocks + 31) / 32;
+    unsigned need = 0, seen = 0;
+    for (unsigned u = 0; u < nu; ++u)
+      if (lane + 32 * u < nblocks) need |= 1u << u;
+    int ok = 1;
+    const long long t0 = clock64();
+    while (true) {
+      for (unsigned u = 0; u < nu; ++u)
+        if (((need & ~seen) >> u) & 1u)
+          if (ld_relaxed_u32(&bar[BAR_FLAGS + BAR_STRIDE * (lane + 32 * u)]) >= target)
+            seen |= 1u << u;
+      if (__all_sync(0xffffffffu, seen == need)) break;
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_relaxed_u32(&bar[2])) {
+          stop = 1;
+        } else if (clock64() - t0 > kWaitCycles) {
           atomicExch(&bar[2], 1u);
           atomicOr(status, code);
-          ok = 0;
-          break;
+          stop = 1;
         }
-        __nanosleep(32);
       }
+      if (__shfl_sync(0xffffffffu, stop, 0)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(16);
     }
     __threadfence();
     gen = target;
-    ok_s = ok;
+    if (lane == 0) ok_s = ok;
   }
   __syncthreads();
   return ok_s != 0;
 }
+
+// Words of barrier state for a grid of `grid` CTAs.
+size_t bar_words(int grid) { return BAR_FLAGS + (size_t)BAR_STRIDE * (size_t)grid; }
 
 // ---------------------------------------------------------------------------
 // Householder tridiagonalisation (lower), blocked, persistent.
@@ -493,28 +523,46 @@ __global__ void __launch_bounds__(256) wy_t_kernel(const typename CxT<T>::C* a,
 }
 
 // X <- Q X: CTA owns CT columns of X (n x m, column-major) and applies the blocks
-// from the last to the first: X -= V (T (V^H X)); 32 x CT threads.  The CTA's
-// n x CT tile of X stays in shared memory for the whole product when it fits
-// (`resident`), so only the reflectors stream from L2; V is staged in chunks of
-// RCH rows.
+// from the last to the first: X -= V (T (V^H X)), 512 threads.  The CTA's n x CT tile
+// of X stays in shared memory for the whole product when it fits (`resident`), so
+// only the reflectors stream from L2.  V is staged in chunks of AR rows, double
+// buffered: each thread loads its part of chunk c+1 into registers while chunk c is
+// used.  V^H X: thread (part, r, cc) sums the rows part, part + AQP, ... of a chunk;
+// the AQP parts are added at the end of the block.  X -= V W: an element per thread.
 constexpr int CT = 4;
-constexpr int AQ_THREADS = 32 * CT;
-constexpr int RCH = 64;
+constexpr int AQ_THREADS = 512;
+constexpr int AQP = AQ_THREADS / (PNB * CT);  // row parts of the V^H X sums
+
+template <typename T>
+__host__ __device__ constexpr int aq_rows() {
+  return sizeof(T) == 4 ? 128 : 64;
+}
+
+template <typename T>
+size_t aq_smem(int n, bool resident) {
+  using C = typename CxT<T>::C;
+  return sizeof(C) * (2 * (size_t)aq_rows<T>() * (PNB + 1) + PNB * (PNB + 1) +
+                      (size_t)AQP * PNB * CT + PNB * CT + (resident ? (size_t)n * CT : 0));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(AQ_THREADS) apply_q_kernel(const typename CxT<T>::C* a, int n,
                                                              const typename CxT<T>::C* tfac,
                                                              typename CxT<T>::C* x, int m,
                                                              int resident) {
   using C = typename CxT<T>::C;
+  constexpr int AR = aq_rows<T>();
+  constexpr int PER = AR * PNB / AQ_THREADS;  // staged V elements per thread and chunk
   extern __shared__ __align__(16) unsigned char aq_raw[];
-  C* xr = (C*)aq_raw;  // [n][CT] when resident
-  __shared__ C Vc[RCH][PNB + 1];
-  __shared__ C W1[PNB][CT + 1];
-  __shared__ C W2[PNB][CT + 1];
-  __shared__ C Tt[PNB][PNB + 1];
+  C* Vb = (C*)aq_raw;               // [2][AR][PNB + 1]
+  C* Tt = Vb + 2 * AR * (PNB + 1);  // [PNB][PNB + 1]
+  C* Wp = Tt + PNB * (PNB + 1);     // [AQP][PNB][CT]
+  C* W2 = Wp + AQP * PNB * CT;      // [PNB][CT]
+  C* xr = W2 + PNB * CT;            // [n][CT] when resident
   const int tid = threadIdx.x, c0 = blockIdx.x * CT;
   const int nr = n - 1, nblk = (nr + PNB - 1) / PNB;
-  const int r_own = tid / CT, cc_own = tid % CT;  // 32 x CT
+  const int cc1 = tid % CT, r1 = (tid / CT) % PNB, part1 = tid / (CT * PNB);
+  const bool in1 = c0 + cc1 < m;
   auto xat = [&](int j, int cc) -> C& { return resident ? xr[(size_t)j * CT + cc]
                                                         : x[(size_t)(c0 + cc) * n + j]; };
   if (resident)
@@ -524,46 +572,81 @@ __global__ void __launch_bounds__(AQ_THREADS) apply_q_kernel(const typename CxT<
     }
   for (int blk = nblk - 1; blk >= 0; --blk) {
     const int b0 = blk * PNB, nb = min(PNB, nr - b0);
+    const int jb = b0 + 1, nch = (n - jb + AR - 1) / AR;
+    // V(j, r) of chunk ch for this thread's element u (r = e / AR, jj = e % AR)
+    auto vload = [&](int ch, int u) -> C {
+      const int e = tid + AQ_THREADS * u, r = e / AR, j = jb + ch * AR + e % AR;
+      return (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+    };
+    auto vstore = [&](int buf, int u, C v) {
+      const int e = tid + AQ_THREADS * u;
+      Vb[((size_t)buf * AR + e % AR) * (PNB + 1) + e / AR] = v;
+    };
     __syncthreads();
     for (int e = tid; e < PNB * PNB; e += AQ_THREADS)
-      Tt[e / PNB][e % PNB] = tfac[(size_t)blk * PNB * PNB + e];
+      Tt[(e / PNB) * (PNB + 1) + e % PNB] = tfac[(size_t)blk * PNB * PNB + e];
+    // ---- W = V^H X
     C acc = {0, 0};
-    for (int j0 = b0 + 1; j0 < n; j0 += RCH) {
-      __syncthreads();
-      for (int e = tid; e < RCH * PNB; e += AQ_THREADS) {
-        const int r = e / RCH, jj = e % RCH, j = j0 + jj;
-        Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+    C pf[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) vstore(0, u, vload(0, u));
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) pf[u] = vload(ch + 1, u);
       }
       __syncthreads();
-      const bool in_c = c0 + cc_own < m;
-      const int jmax = min(RCH, n - j0);
-      for (int jj = 0; jj < jmax; ++jj) {
-        const C xv = in_c ? xat(j0 + jj, cc_own) : C{0, 0};
-        acc = cadd(acc, cmul_ca(Vc[jj][r_own], xv));
+      const C* V = Vb + (size_t)buf * AR * (PNB + 1);
+      const int j0 = jb + ch * AR, jmax = min(AR, n - j0);
+      if (in1)
+        for (int jj = part1; jj < jmax; jj += AQP)
+          acc = cadd(acc, cmul_ca(V[jj * (PNB + 1) + r1], xat(j0 + jj, cc1)));
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) vstore(buf ^ 1, u, pf[u]);
       }
     }
-    W1[r_own][cc_own] = acc;
+    Wp[(part1 * PNB + r1) * CT + cc1] = acc;
     __syncthreads();
-    {
-      C t = {0, 0};
-      for (int s = r_own; s < PNB; ++s) t = cadd(t, cmul(Tt[r_own][s], W1[s][cc_own]));
-      W2[r_own][cc_own] = t;
+    if (tid < PNB * CT) {
+      C t = Wp[tid];
+      for (int q = 1; q < AQP; ++q) t = cadd(t, Wp[q * PNB * CT + tid]);
+      W2[tid] = t;  // V^H X, replaced by T (V^H X) below
     }
-    for (int j0 = b0 + 1; j0 < n; j0 += RCH) {
-      __syncthreads();
-      for (int e = tid; e < RCH * PNB; e += AQ_THREADS) {
-        const int r = e / RCH, jj = e % RCH, j = j0 + jj;
-        Vc[jj][r] = (r < nb && j < n && j >= b0 + r + 1) ? a[(size_t)(b0 + r) * n + j] : C{0, 0};
+    __syncthreads();
+    C tw = {0, 0};
+    if (tid < PNB * CT) {
+      const int r = tid / CT, cc = tid % CT;
+      for (int q = r; q < PNB; ++q) tw = cadd(tw, cmul(Tt[r * (PNB + 1) + q], W2[q * CT + cc]));
+    }
+    __syncthreads();
+    if (tid < PNB * CT) W2[tid] = tw;
+    // ---- X -= V (T W)
+#pragma unroll
+    for (int u = 0; u < PER; ++u) vstore(0, u, vload(0, u));
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) pf[u] = vload(ch + 1, u);
       }
       __syncthreads();
-      for (int e = tid; e < RCH * CT; e += AQ_THREADS) {
-        const int jj = e % RCH, cc = e / RCH, j = j0 + jj;
+      const C* V = Vb + (size_t)buf * AR * (PNB + 1);
+      const int j0 = jb + ch * AR;
+      for (int e = tid; e < AR * CT; e += AQ_THREADS) {
+        const int jj = e % AR, cc = e / AR, j = j0 + jj;
         if (j < n && c0 + cc < m) {
           C t = {0, 0};
-          for (int r = 0; r < PNB; ++r) t = cadd(t, cmul(Vc[jj][r], W2[r][cc]));
+#pragma unroll 8
+          for (int r = 0; r < PNB; ++r) t = cadd(t, cmul(V[jj * (PNB + 1) + r], W2[r * CT + cc]));
           C& xv = xat(j, cc);
           xv = csub(xv, t);
         }
+      }
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) vstore(buf ^ 1, u, pf[u]);
       }
     }
   }
@@ -578,13 +661,18 @@ __global__ void __launch_bounds__(AQ_THREADS) apply_q_kernel(const typename CxT<
 // ---------------------------------------------------------------------------
 // Cyclic two-sided Jacobi (FP64) with round-robin pairs of M = m + (m & 1)
 // players: round r pairs (M-1, r) and ((r + k) mod (M-1), (r - k) mod (M-1)),
-// k = 1 .. M/2 - 1; a pair with the padding index m is skipped.  Per round:
-//   1. the CTA owning pair k (k = b, b + G, ...) computes its rotation from
-//      a = G_pp, c = G_qq, g = G_pq = |g| e^{i phi}: zeta = (c - a) / (2 |g|),
-//      t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1 + t^2),
-//      sn = t cs; J = diag(1, e^{-i phi}) [[cs, sn], [-sn, cs]];      barrier
-//   2. it rotates its columns p, q of G and Y (G J, Y J), then applies every
-//      pair's row rotation (J^H) to those two columns, and zeroes G_pq;  barrier
+// k = 1 .. M/2 - 1.  With m odd, the player paired with the padding index m takes
+// no rotation that round (its column still takes the other pairs' row rotations).
+// Per round:
+//   1. every CTA computes every pair's rotation from a = G_pp, c = G_qq,
+//      g = G_pq = |g| e^{i phi}, read from a buffer of their own (below):
+//      zeta = (c - a) / (2 |g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+//      cs = 1/sqrt(1 + t^2), sn = t cs; J = diag(1, e^{-i phi}) [[cs, sn], [-sn, cs]];
+//   2. the CTA owning pair k (k = b, b + G, ...) rotates its columns p, q of G and
+//      Y (G J, Y J), applies every pair's row rotation (J^H) to those two columns,
+//      zeroes G_pq, and writes the entries of its columns that the next round's
+//      rotations need into the other buffer (double-buffered by round);  barrier
+//   One grid barrier per round, and no CTA reads G while another rotates it.
 // Rotations with |g| <= 1e-300 or |g| <= eps sqrt(|a c|) are skipped.  A sweep
 // is M - 1 rounds; sweeps stop when no pair of a sweep needed a rotation.
 // ---------------------------------------------------------------------------
@@ -608,7 +696,7 @@ struct JacArgs {
   cplx* g;
   int m;
   cplx* y;
-  double* prm;   // [M/2][4]: cs, sn, Re e^{-i phi}, Im e^{-i phi}
+  double* prm;   // [2][M/2][4]: G_pp, G_qq, Re G_pq, Im G_pq of each pair of a round
   double* part;  // [grid]: rotations needed in the sweep
   unsigned* bar;
   int* status;
@@ -627,17 +715,33 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
   // only rotations below kConverged the matrix it leaves is diagonal to ~kConverged^2
   double offmax = 0.0;
   constexpr double kConverged = 1e-8;
+  // the entries a rotation needs, round 0
+  for (int k = b + G * tid; k < np; k += G * JT) {
+    int pp, qq;
+    pair_of(M, 0, k, pp, qq);
+    if (qq >= m) continue;
+    const cplx gpq = p.g[(size_t)qq * m + pp];
+    double* o = p.prm + 4 * (size_t)k;
+    o[0] = p.g[(size_t)pp * m + pp].re;
+    o[1] = p.g[(size_t)qq * m + qq].re;
+    o[2] = gpq.re;
+    o[3] = gpq.im;
+  }
+  if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+  int R = 0;  // rounds done: the inputs of round R are in prm[R & 1]
   for (int sweep = 0; sweep < p.max_sweeps; ++sweep) {
-    for (int r = 0; r < M - 1; ++r) {
-      // 1. rotation parameters of this CTA's pairs
-      for (int k = b + G * tid; k < np; k += G * JT) {
+    for (int r = 0; r < M - 1; ++r, ++R) {
+      const double* in = p.prm + (size_t)(R & 1) * 4 * np;
+      double* nx = p.prm + (size_t)((R + 1) & 1) * 4 * np;
+      // 1. rotation parameters of every pair, computed by every CTA (the same
+      //    arithmetic on the same entries, so the same values) into shared memory
+      for (int k = tid; k < np; k += JT) {
         int pp, qq;
         pair_of(M, r, k, pp, qq);
         double cs = 1.0, sn = 0.0, er = 1.0, ei = 0.0;
         if (qq < m) {
-          const double a = ldcg_c(&p.g[(size_t)pp * m + pp]).re;
-          const double c = ldcg_c(&p.g[(size_t)qq * m + qq]).re;
-          const cplx gpq = ldcg_c(&p.g[(size_t)qq * m + pp]);
+          const double a = __ldcg(&in[4 * k]), c = __ldcg(&in[4 * k + 1]);
+          const cplx gpq = {__ldcg(&in[4 * k + 2]), __ldcg(&in[4 * k + 3])};
           const double beta = hypot(gpq.re, gpq.im);
           const double ref = sqrt(fabs(a * c));
           if (beta > 1e-300 && beta > eps * ref) {
@@ -650,22 +754,21 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
             ei = -gpq.im / beta;
           }
         }
-        double* o = p.prm + 4 * (size_t)k;
-        o[0] = cs;
-        o[1] = sn;
-        o[2] = er;
-        o[3] = ei;
+        jsm[4 * k] = cs;
+        jsm[4 * k + 1] = sn;
+        jsm[4 * k + 2] = er;
+        jsm[4 * k + 3] = ei;
       }
-      if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
-      for (int e = tid; e < 4 * np; e += JT) jsm[e] = __ldcg(&p.prm[e]);
       __syncthreads();
       // 2. columns p, q of this CTA's pairs: G J and Y J, then J^H on those columns
       for (int k = b; k < np; k += G) {
         int pp, qq;
         pair_of(M, r, k, pp, qq);
-        if (qq >= m) continue;
+        // with m odd, the player paired with the padding index m idles this round: its
+        // column takes no column rotation but still every pair's row rotation
+        const bool idle = qq >= m;
         const double cs = jsm[4 * k], sn = jsm[4 * k + 1], er = jsm[4 * k + 2], ei = jsm[4 * k + 3];
-        if (sn == 0.0 && er == 1.0 && ei == 0.0) {
+        if (idle || (sn == 0.0 && er == 1.0 && ei == 0.0)) {
           // no rotation of these columns; their rows still rotate below
         } else {
           for (int mat = 0; mat < 2; ++mat) {
@@ -681,7 +784,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
         }
         __syncthreads();
         // rows: (J^H X)[p'] = cs X[p'] - sn e^{i phi'} X[q'], (J^H X)[q'] = sn X[p'] + cs e^{i phi'} X[q']
-        for (int col = 0; col < 2; ++col) {
+        for (int col = 0; col < (idle ? 1 : 2); ++col) {
           cplx* X = p.g + (size_t)(col == 0 ? pp : qq) * m;
           for (int k2 = tid; k2 < np; k2 += JT) {
             int p2, q2;
@@ -697,11 +800,39 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
           }
         }
         __syncthreads();
-        if (tid == 0 && !(sn == 0.0 && er == 1.0 && ei == 0.0)) {
+        if (tid == 0 && !idle && !(sn == 0.0 && er == 1.0 && ei == 0.0)) {
           p.g[(size_t)qq * m + pp] = cplx{0.0, 0.0};
           p.g[(size_t)pp * m + qq] = cplx{0.0, 0.0};
           p.g[(size_t)pp * m + pp].im = 0.0;
           p.g[(size_t)qq * m + qq].im = 0.0;
+        }
+        __syncthreads();
+        // columns pp and qq are final for this round: their entries that the next
+        // round's rotations need (its diagonal entries, and G_p'q' from the column
+        // of the larger index q') go to the other buffer, so that no CTA reads G while
+        // another rotates it
+        if (tid < (idle ? 1 : 2)) {
+          const int cix = tid == 0 ? pp : qq;
+          const int rn = r + 1 < M - 1 ? r + 1 : 0;
+          int kn;
+          if (cix == M - 1 || cix == rn) {
+            kn = 0;
+          } else {
+            const int dd = ((cix - rn) % (M - 1) + (M - 1)) % (M - 1);
+            kn = dd < np ? dd : (M - 1) - dd;
+          }
+          int p2, q2;
+          pair_of(M, rn, kn, p2, q2);
+          if (q2 < m) {
+            if (cix == p2) {
+              nx[4 * kn] = p.g[(size_t)cix * m + cix].re;
+            } else {
+              const cplx gv = p.g[(size_t)cix * m + p2];
+              nx[4 * kn + 1] = p.g[(size_t)cix * m + cix].re;
+              nx[4 * kn + 2] = gv.re;
+              nx[4 * kn + 3] = gv.im;
+            }
+          }
         }
       }
       if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
@@ -773,43 +904,51 @@ __device__ __forceinline__ cplx load_op(const cplx* a, int lda, char op, int i, 
   return op == 'C' ? cplx{v.re, -v.im} : v;
 }
 
+// C tile (TILE x TILE; TILE = 32: 2 x 2 outputs per thread, 16: one) of
+// alpha op(A) op(B) + beta C.  tri bit 0: op(B) upper triangular (its rows k > j are
+// zero), bit 1: op(A) upper triangular (its columns k < i are zero); the K range of a
+// tile is cut to where both are nonzero.
+template <int TILE>
 __global__ void __launch_bounds__(256) gemm_z_kernel(char opa, char opb, int m, int n, int k,
                                                      cplx alpha, const cplx* a, int lda,
                                                      const cplx* b, int ldb, cplx beta, cplx* c,
-                                                     int ldc) {
-  __shared__ cplx As[32][17];  // As[i][kk]
-  __shared__ cplx Bs[16][33];  // Bs[kk][j]
+                                                     int ldc, int tri) {
+  constexpr int R = TILE / 16;
+  __shared__ cplx As[TILE][17];      // As[i][kk]
+  __shared__ cplx Bs[16][TILE + 1];  // Bs[kk][j]
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-  cplx acc[2][2] = {};
-  for (int k0 = 0; k0 < k; k0 += 16) {
-    for (int e = tid; e < 32 * 16; e += 256) {
-      const int ii = e % 32, kk = e / 32;
+  const int i0 = blockIdx.x * TILE, j0 = blockIdx.y * TILE;
+  const int kbeg = (tri & 2) ? (i0 / 16) * 16 : 0;
+  const int kend = (tri & 1) ? min(k, j0 + TILE) : k;
+  cplx acc[R][R] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    for (int e = tid; e < TILE * 16; e += 256) {
+      const int ii = e % TILE, kk = e / TILE;
       As[ii][kk] = load_op(a, lda, opa, i0 + ii, k0 + kk, m, k);
     }
-    for (int e = tid; e < 16 * 32; e += 256) {
+    for (int e = tid; e < 16 * TILE; e += 256) {
       const int kk = e % 16, jj = e / 16;
       Bs[kk][jj] = load_op(b, ldb, opb, k0 + kk, j0 + jj, k, n);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < 16; ++kk) {
-      const cplx a0 = As[2 * ty][kk], a1 = As[2 * ty + 1][kk];
-      const cplx b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
-      acc[0][0].re = fma(a0.re, b0.re, fma(-a0.im, b0.im, acc[0][0].re));
-      acc[0][0].im = fma(a0.re, b0.im, fma(a0.im, b0.re, acc[0][0].im));
-      acc[0][1].re = fma(a0.re, b1.re, fma(-a0.im, b1.im, acc[0][1].re));
-      acc[0][1].im = fma(a0.re, b1.im, fma(a0.im, b1.re, acc[0][1].im));
-      acc[1][0].re = fma(a1.re, b0.re, fma(-a1.im, b0.im, acc[1][0].re));
-      acc[1][0].im = fma(a1.re, b0.im, fma(a1.im, b0.re, acc[1][0].im));
-      acc[1][1].re = fma(a1.re, b1.re, fma(-a1.im, b1.im, acc[1][1].re));
-      acc[1][1].im = fma(a1.re, b1.im, fma(a1.im, b1.re, acc[1][1].im));
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+        const cplx av = As[R * ty + y][kk];
+#pragma unroll
+        for (int x = 0; x < R; ++x) {
+          const cplx bv = Bs[kk][R * tx + x];
+          acc[y][x].re = fma(av.re, bv.re, fma(-av.im, bv.im, acc[y][x].re));
+          acc[y][x].im = fma(av.re, bv.im, fma(av.im, bv.re, acc[y][x].im));
+        }
+      }
     }
     __syncthreads();
   }
-  for (int y = 0; y < 2; ++y)
-    for (int x = 0; x < 2; ++x) {
-      const int i = i0 + 2 * ty + y, j = j0 + 2 * tx + x;
+  for (int y = 0; y < R; ++y)
+    for (int x = 0; x < R; ++x) {
+      const int i = i0 + R * ty + y, j = j0 + R * tx + x;
       if (i >= m || j >= n) continue;
       const cplx v = acc[y][x];
       cplx out = {alpha.re * v.re - alpha.im * v.im, alpha.re * v.im + alpha.im * v.re};
@@ -822,37 +961,45 @@ __global__ void __launch_bounds__(256) gemm_z_kernel(char opa, char opb, int m, 
     }
 }
 
-// In-place inverse of an upper-triangular n x n (n <= 32) block of a column-major
-// matrix (ld), zeroing the block's strictly lower part; one thread per column.
-__global__ void trinv_tile_kernel(cplx* r, int n, int ld) {
+// Inverse of each 32 x 32 diagonal tile (the last one ragged) of the upper-triangular
+// n x n R (column-major, leading dimension ld), in place, zero below the diagonal:
+// blockIdx.x = tile.  Backward elimination of the identity: for j from the last row
+// up, row j of X = R^-1 is scaled by 1 / R_jj and eliminated from the rows above.
+__global__ void __launch_bounds__(256) trinv_tiles_kernel(cplx* r, int n, int ld) {
   __shared__ cplx t[32][33];
   __shared__ cplx u[32][33];
-  const int tid = threadIdx.x;
+  __shared__ cplx rd;
+  const int tid = threadIdx.x, o = 32 * blockIdx.x, kb = min(32, n - o);
   for (int e = tid; e < 32 * 32; e += blockDim.x) {
     const int i = e % 32, j = e / 32;
-    t[i][j] = (i < n && j < n && i <= j) ? r[(size_t)j * ld + i] : cplx{0.0, 0.0};
+    t[i][j] = (i < kb && j < kb && i <= j) ? r[(size_t)(o + j) * ld + o + i] : cplx{0.0, 0.0};
+    u[i][j] = cplx{(i == j && i < kb) ? 1.0 : 0.0, 0.0};
   }
   __syncthreads();
-  if (tid < n) {
-    const int c = tid;
-    // X[c][c] = 1 / R[c][c]; X[i][c] = -(sum_{i < q <= c} R[i][q] X[q][c]) / R[i][i]
-    for (int i = 31; i >= 0; --i) u[i][c] = cplx{0.0, 0.0};
-    for (int i = c; i >= 0; --i) {
-      cplx s = {i == c ? 1.0 : 0.0, 0.0};
-      for (int q = i + 1; q <= c; ++q) {
-        const cplx a = t[i][q], x = u[q][c];
-        s.re -= a.re * x.re - a.im * x.im;
-        s.im -= a.re * x.im + a.im * x.re;
-      }
-      const cplx d = t[i][i];
+  for (int j = kb - 1; j >= 0; --j) {
+    if (tid == 0) {
+      const cplx d = t[j][j];
       const double dd = d.re * d.re + d.im * d.im;
-      u[i][c] = cplx{(s.re * d.re + s.im * d.im) / dd, (s.im * d.re - s.re * d.im) / dd};
+      rd = cplx{d.re / dd, -d.im / dd};
     }
+    __syncthreads();
+    if (tid >= j && tid < kb) {
+      const cplx x = u[j][tid], q = rd;
+      u[j][tid] = cplx{x.re * q.re - x.im * q.im, x.re * q.im + x.im * q.re};
+    }
+    __syncthreads();
+    const int w = kb - j;  // columns c = j .. kb-1 of the rows i < j
+    for (int e = tid; e < j * w; e += blockDim.x) {
+      const int i = e / w, c = j + e % w;
+      const cplx a = t[i][j], x = u[j][c];
+      u[i][c].re -= a.re * x.re - a.im * x.im;
+      u[i][c].im -= a.re * x.im + a.im * x.re;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    r[(size_t)j * ld + i] = i <= j ? u[i][j] : cplx{0.0, 0.0};
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e % kb, j = e / kb;
+    r[(size_t)(o + j) * ld + o + i] = i <= j ? u[i][j] : cplx{0.0, 0.0};
   }
 }
 
@@ -928,7 +1075,8 @@ rpa_status hetrd_alloc(HetrdWork& w, int n_max, size_t elem, std::string& err) {
   const size_t n = n_max;
   if (!al(&w.vp, n * PNB * elem) || !al(&w.wp, n * PNB * elem) || !al(&w.xcol, n * elem) ||
       !al(&w.ycol, n * elem) || !al(&w.part, (size_t)sms * PL * elem) ||
-      !al(&w.part2, (size_t)sms * elem) || !al((void**)&w.bar, 4 * sizeof(unsigned)) ||
+      !al(&w.part2, (size_t)sms * elem) ||
+      !al((void**)&w.bar, bar_words(w.grid) * sizeof(unsigned)) ||
       !al((void**)&w.status, sizeof(int))) {
     hetrd_free(w);
     err = "dense eigensolver: cudaMalloc failed";
@@ -962,7 +1110,7 @@ rpa_status hetrd(HetrdWork& w, void* a, int n, T* d, T* e, void* tau, cudaStream
   rpa_status s = coop_setup(sms, err);
   if (s != RPA_OK) return s;
   const int G = hetrd_grid<T>(n, std::min(std::min(sms, w.grid), MAXG));
-  if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
+  if (cudaMemsetAsync(w.bar, 0, bar_words(w.grid) * sizeof(unsigned), st) != cudaSuccess) {
     err = "dense eigensolver: barrier reset failed";
     return RPA_ECUDA;
   }
@@ -992,17 +1140,16 @@ rpa_status apply_q(const void* a, const void* tau, int n, void* x, int m, void* 
   if (n < 2 || m < 1) return RPA_OK;
   const int nblk = (n - 1 + PNB - 1) / PNB;
   wy_t_kernel<T><<<nblk, 256, 0, st>>>((const C*)a, (const C*)tau, n, (C*)tfac);
-  // the X tile resident in shared memory when it fits beside the static arrays
-  const size_t res_bytes = (size_t)n * CT * sizeof(C);
-  const bool resident = res_bytes <= 160 * 1024;
-  if (resident &&
-      cudaFuncSetAttribute(apply_q_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(160 * 1024)) != cudaSuccess) {
+  // the X tile resident in shared memory when everything fits in 227 KB
+  const bool resident = aq_smem<T>(n, true) <= 227 * 1024;
+  const size_t smem = aq_smem<T>(n, resident);
+  if (cudaFuncSetAttribute(apply_q_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
     (void)cudaGetLastError();
     err = "apply_q: shared memory attribute";
     return RPA_ECUDA;
   }
-  apply_q_kernel<T><<<(m + CT - 1) / CT, AQ_THREADS, resident ? res_bytes : 0, st>>>(
+  apply_q_kernel<T><<<(m + CT - 1) / CT, AQ_THREADS, smem, st>>>(
       (const C*)a, n, (const C*)tfac, (C*)x, m, resident ? 1 : 0);
   const cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) {
@@ -1029,9 +1176,9 @@ rpa_status jacobi_alloc(JacobiWork& w, int m_max, std::string& err) {
   w.m_max = m_max;
   w.grid = sms;
   const size_t M = (size_t)m_max + 1;
-  if (cudaMalloc(&w.prm, 4 * (M / 2 + 1) * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc(&w.prm, 8 * (M / 2 + 1) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&w.part, (size_t)sms * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&w.bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&w.bar, bar_words(w.grid) * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&w.status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&w.perm, M * sizeof(int)) != cudaSuccess ||
       cudaMemset(w.status, 0, sizeof(int)) != cudaSuccess) {
@@ -1063,7 +1210,7 @@ rpa_status jacobi(JacobiWork& w, cplx* g, int m, double* theta, cplx* y, cplx* y
   const int M = m + (m & 1), np = M / 2;
   const int G = std::max(1, std::min(std::min(sms, w.grid), np / 2));
   identity_kernel<<<std::min(4096, (m * m + 255) / 256), 256, 0, st>>>(ywork, m);
-  if (cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess) {
+  if (cudaMemsetAsync(w.bar, 0, bar_words(w.grid) * sizeof(unsigned), st) != cudaSuccess) {
     err = "Jacobi eigensolver: barrier reset failed";
     return RPA_ECUDA;
   }
@@ -1087,16 +1234,25 @@ rpa_status jacobi(JacobiWork& w, cplx* g, int m, double* theta, cplx* y, cplx* y
   return RPA_OK;
 }
 
-rpa_status gemm_z(char opa, char opb, int m, int n, int k, cplx alpha, const cplx* a, int lda,
-                  const cplx* b, int ldb, cplx beta, cplx* c, int ldc, cudaStream_t st,
-                  std::string& err, int* launches) {
+static rpa_status gemm_z_tri(char opa, char opb, int m, int n, int k, cplx alpha,
+                             const cplx* a, int lda, const cplx* b, int ldb, cplx beta, cplx* c,
+                             int ldc, int tri, cudaStream_t st, std::string& err,
+                             int* launches) {
   if (m < 1 || n < 1) return RPA_OK;
-  const dim3 grid((m + 31) / 32, (n + 31) / 32);
+  // 16 x 16 tiles when 32 x 32 ones would leave SMs idle (the FP64 pipe is narrow)
+  const bool small = (long)((m + 31) / 32) * ((n + 31) / 32) < 152;
+  const int tile = small ? 16 : 32;
+  const dim3 grid((m + tile - 1) / tile, (n + tile - 1) / tile);
   if (grid.y > 65535) {
     err = "gemm_z: n too large";
     return RPA_EINVAL;
   }
-  gemm_z_kernel<<<grid, 256, 0, st>>>(opa, opb, m, n, k, alpha, a, lda, b, ldb, beta, c, ldc);
+  if (small)
+    gemm_z_kernel<16><<<grid, 256, 0, st>>>(opa, opb, m, n, k, alpha, a, lda, b, ldb, beta, c,
+                                            ldc, tri);
+  else
+    gemm_z_kernel<32><<<grid, 256, 0, st>>>(opa, opb, m, n, k, alpha, a, lda, b, ldb, beta, c,
+                                            ldc, tri);
   const cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) {
     err = std::string("gemm_z launch: ") + cudaGetErrorString(ce);
@@ -1106,32 +1262,44 @@ rpa_status gemm_z(char opa, char opb, int m, int n, int k, cplx alpha, const cpl
   return RPA_OK;
 }
 
-// Recursive doubling: [R11 R12; 0 R22]^-1 = [X11, -X11 R12 X22; 0, X22].
+rpa_status gemm_z(char opa, char opb, int m, int n, int k, cplx alpha, const cplx* a, int lda,
+                  const cplx* b, int ldb, cplx beta, cplx* c, int ldc, cudaStream_t st,
+                  std::string& err, int* launches) {
+  return gemm_z_tri(opa, opb, m, n, k, alpha, a, lda, b, ldb, beta, c, ldc, 0, st, err,
+                    launches);
+}
+
+// Off-diagonal blocks of R^-1 by recursive doubling, the diagonal 32 x 32 tiles
+// already inverted: [R11 R12; 0 R22]^-1 = [X11, -X11 R12 X22; 0, X22].  Splits fall
+// on multiples of 32, so the leaves are the inverted tiles.
+static rpa_status trinv_blocks(cplx* r, int n, int ld, cplx* work, cudaStream_t st,
+                               std::string& err, int* launches) {
+  if (n <= 32) return RPA_OK;
+  const int n1 = ((n / 2 + 31) / 32) * 32, n2 = n - n1;
+  rpa_status s;
+  if ((s = trinv_blocks(r, n1, ld, work, st, err, launches)) != RPA_OK) return s;
+  if ((s = trinv_blocks(r + (size_t)n1 * ld + n1, n2, ld, work, st, err, launches)) != RPA_OK)
+    return s;
+  // work (n1 x n2) = R12 X22 (X22 upper triangular); X12 = -X11 work (X11 upper)
+  cplx* r12 = r + (size_t)n1 * ld;
+  if ((s = gemm_z_tri('N', 'N', n1, n2, n2, cplx{1.0, 0.0}, r12, ld, r + (size_t)n1 * ld + n1,
+                      ld, cplx{0.0, 0.0}, work, n1, 1, st, err, launches)) != RPA_OK)
+    return s;
+  return gemm_z_tri('N', 'N', n1, n2, n1, cplx{-1.0, 0.0}, r, ld, work, n1, cplx{0.0, 0.0}, r12,
+                    ld, 2, st, err, launches);
+}
+
 rpa_status trinv_upper(cplx* r, int n, int ld, cplx* work, cudaStream_t st, std::string& err,
                        int* launches) {
   if (n < 1) return RPA_OK;
-  if (n <= 32) {
-    trinv_tile_kernel<<<1, 64, 0, st>>>(r, n, ld);
-    const cudaError_t ce = cudaGetLastError();
-    if (ce != cudaSuccess) {
-      err = std::string("trinv launch: ") + cudaGetErrorString(ce);
-      return RPA_ECUDA;
-    }
-    if (launches) *launches += 1;
-    return RPA_OK;
+  trinv_tiles_kernel<<<(n + 31) / 32, 256, 0, st>>>(r, n, ld);
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    err = std::string("trinv launch: ") + cudaGetErrorString(ce);
+    return RPA_ECUDA;
   }
-  const int n1 = ((n / 2 + 31) / 32) * 32, n2 = n - n1;
-  rpa_status s;
-  if ((s = trinv_upper(r, n1, ld, work, st, err, launches)) != RPA_OK) return s;
-  if ((s = trinv_upper(r + (size_t)n1 * ld + n1, n2, ld, work, st, err, launches)) != RPA_OK)
-    return s;
-  // work (n1 x n2) = R12 X22; X12 = -X11 work
-  cplx* r12 = r + (size_t)n1 * ld;
-  if ((s = gemm_z('N', 'N', n1, n2, n2, cplx{1.0, 0.0}, r12, ld, r + (size_t)n1 * ld + n1, ld,
-                  cplx{0.0, 0.0}, work, n1, st, err, launches)) != RPA_OK)
-    return s;
-  return gemm_z('N', 'N', n1, n2, n1, cplx{-1.0, 0.0}, r, ld, work, n1, cplx{0.0, 0.0}, r12, ld,
-                st, err, launches);
+  if (launches) *launches += 1;
+  return trinv_blocks(r, n, ld, work, st, err, launches);
 }
 
 }  // namespace dense

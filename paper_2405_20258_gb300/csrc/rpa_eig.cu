@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -114,6 +115,53 @@ __global__ void bisect_kernel(const double* d, const double* e, const double* e2
                    : tri::bisect(d, e2, n, j, lo, hi, pivmin, abstol);
 }
 
+// The k most negative eigenvalues of T for the FP32 start, to 4 FP32 ulps of each: a
+// warp per eigenvalue, whose lanes place 32 shifts evenly inside its bracket and take
+// FP32 Sturm counts at all of them at once (multisection: five bits of the bracket per
+// pass over T instead of one).  The first lane whose count exceeds j closes the
+// bracket from above, the lane before it from below.  The Gershgorin bracket comes from
+// the FP64 T, computed by the warp.
+__global__ void bisect32_warp_kernel(const double* d, const double* e, const float* d32,
+                                     const float* e2f, int n, int k, double* w) {
+  const int j = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= k) return;  // whole warps
+  double l = d[0], h = d[0];
+  for (int i = lane; i < n; i += 32) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    l = fmin(l, d[i] - r);
+    h = fmax(h, d[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+    h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+  }
+  const double wd = fmax(h - l, DBL_MIN);
+  float flo = __double2float_rd(l - 2.0 * DBL_EPSILON * wd * n - DBL_MIN);
+  float fhi = __double2float_ru(h + 2.0 * DBL_EPSILON * wd * n + DBL_MIN);
+  const float fpiv = 1.1754944e-38f;  // FLT_MIN
+  for (int it = 0; it < 32; ++it) {
+    if (fhi - flo <= 4.0f * 1.1920929e-7f * fmaxf(fabsf(flo), fabsf(fhi))) break;
+    const float x =
+        fminf(fmaxf(flo + (fhi - flo) * ((float)(lane + 1) * (1.0f / 33.0f)), flo), fhi);
+    const int cnt = tri::sturm_count_f(d32, e2f, n, x, fpiv);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > j);
+    float nlo = flo, nhi = fhi;
+    if (above == 0u) {
+      nlo = __shfl_sync(0xffffffffu, x, 31);
+    } else {
+      const int f = __ffs(above) - 1;
+      nhi = __shfl_sync(0xffffffffu, x, f);
+      const float prev = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+      if (f > 0) nlo = prev;
+    }
+    if (!(nhi - nlo < fhi - flo)) break;  // no progress at FP32 resolution
+    flo = nlo;
+    fhi = nhi;
+  }
+  if (lane == 0) w[j] = 0.5 * ((double)flo + (double)fhi);
+}
+
 // Eigenvectors of T for the clusters c < nc of w (cluster c = w[first[c] ..
 // first[c+1])), a thread each; z is n x ldz row-major; lanes holds 6 n nc doubles,
 // element i of a thread's lane q at q n nc + i nc + c.
@@ -130,6 +178,23 @@ __global__ void invit_kernel(const double* d, const double* e, int n, const doub
                        tri::Lane{b, nc}, tri::Lane{b + plane, nc}, tri::Lane{b + 2 * plane, nc},
                        tri::Lane{b + 3 * plane, nc}, tri::Lane{b + 4 * plane, nc},
                        tri::Lane{b + 5 * plane, nc});
+}
+
+// The same in FP32 arithmetic for the FP32 start, whose T (d32, e32) is itself an FP32
+// object: its eigenvectors are wanted to FP32 accuracy only (the filtered
+// Rayleigh-Ritz refinement restores FP64).  tiny: the pivot floor, FLT_EPSILON |T|;
+// lanes holds 6 n nc floats.
+__global__ void invit32_kernel(const float* d, const float* e, int n, const double* w,
+                               const int* first, int nc, float tiny, double* z, int ldz,
+                               float* lanes) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const long plane = (long)n * nc;
+  float* b = lanes + c;
+  using LF = tri::LaneT<float>;
+  tri::cluster_vectors<float>(d, e, n, w, first[c], first[c + 1], tiny, z, ldz, LF{b, nc},
+                              LF{b + plane, nc}, LF{b + 2 * plane, nc}, LF{b + 3 * plane, nc},
+                              LF{b + 4 * plane, nc}, LF{b + 5 * plane, nc});
 }
 
 // c[i + n j] = z[i k + j] as complex64 (column-major n x k from row-major FP64)
@@ -409,8 +474,11 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   int mode = (b32_env && b32_env[0] == '0') ? 0 : 1;
   if (s32 && !(b64_env && b64_env[0] == '1')) mode = 2;
   const int bb = std::max(1, std::min(256, blk_env ? atoi(blk_env) : 32));
-  bisect_kernel<<<(nval + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, s32 ? d32 : d32b, e2f, n, nval,
-                                                     mode, wt);
+  if (mode == 2)
+    bisect32_warp_kernel<<<(nval + 3) / 4, 128, 0, st>>>(d64, e64, d32, e2f, n, nval, wt);
+  else
+    bisect_kernel<<<(nval + bb - 1) / bb, bb, 0, st>>>(d64, e64, e2, s32 ? d32 : d32b, e2f, n,
+                                                       nval, mode, wt);
   CU_E(cudaGetLastError());
   nl += 1;
   std::vector<double> w(nval);
@@ -462,7 +530,12 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   CU_E(cudaMemcpyAsync(first, fh.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   const char* ib_env = getenv("RPA_EIG_INVIT_BLOCK");
   const int ib = std::max(1, std::min(256, ib_env ? atoi(ib_env) : 32));
-  invit_kernel<<<(nc + ib - 1) / ib, ib, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
+  if (mode == 2)
+    invit32_kernel<<<(nc + ib - 1) / ib, ib, 0, st>>>(d32, e32, n, wt, first, nc,
+                                                      (float)(FLT_EPSILON * tnorm), zt, mp,
+                                                      (float*)lanes);
+  else
+    invit_kernel<<<(nc + ib - 1) / ib, ib, 0, st>>>(d64, e64, n, wt, first, nc, zt, mp, lanes);
   CU_E(cudaGetLastError());
   if (s32) {
     z_to_c64_kernel<<<grid_for((long)n * mp, 256), 256, 0, st>>>(zt, n, mp, c32);

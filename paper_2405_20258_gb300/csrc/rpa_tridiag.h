@@ -162,46 +162,54 @@ inline int clusters(const double* w, int k, double cluster_tol, int* first) {
 
 // Strided view of one thread's scratch: element i lives at p[i * stride], so that
 // the threads of a warp, each at the same i, touch consecutive addresses.
-struct Lane {
-  double* p;
+template <typename R>
+struct LaneT {
+  R* p;
   long stride;
-  RPA_HD double& operator[](long i) const { return p[i * stride]; }
+  RPA_HD R& operator[](long i) const { return p[i * stride]; }
 };
+using Lane = LaneT<double>;
+
+template <typename R>
+RPA_HD R rabs(R x) {
+  return x < R(0) ? -x : x;
+}
 
 // Gaussian elimination with partial pivoting of M = T - lambda I.  U (upper, two
 // super-diagonals) in u0 (diagonal), u1, u2; multipliers in l; piv[i] = 1 when
 // rows i and i+1 were exchanged at step i.  Pivots smaller than tiny are replaced
 // by +-tiny, so that the solve stays finite at an exact eigenvalue.
-RPA_HD void lu_factor(const double* d, const double* e, int n, double lambda, double tiny,
-                      Lane u0, Lane u1, Lane u2, Lane l, Lane piv) {
+template <typename R>
+RPA_HD void lu_factor(const R* d, const R* e, int n, R lambda, R tiny, LaneT<R> u0, LaneT<R> u1,
+                      LaneT<R> u2, LaneT<R> l, LaneT<R> piv) {
   // current row k: a at column k, b at column k+1
-  double a = d[0] - lambda, b = n > 1 ? e[0] : 0.0;
+  R a = d[0] - lambda, b = n > 1 ? e[0] : R(0);
   for (int k = 0; k + 1 < n; ++k) {
-    const double g = e[k];                      // M[k+1][k]
-    const double al = d[k + 1] - lambda;        // M[k+1][k+1]
-    const double be = k + 2 < n ? e[k + 1] : 0.0;  // M[k+1][k+2]
-    if (fabs(a) >= fabs(g)) {
-      if (fabs(a) < tiny) a = a < 0.0 ? -tiny : tiny;
-      const double m = g / a;
+    const R g = e[k];                          // M[k+1][k]
+    const R al = d[k + 1] - lambda;            // M[k+1][k+1]
+    const R be = k + 2 < n ? e[k + 1] : R(0);  // M[k+1][k+2]
+    if (rabs(a) >= rabs(g)) {
+      if (rabs(a) < tiny) a = a < R(0) ? -tiny : tiny;
+      const R m = g / a;
       u0[k] = a;
       u1[k] = b;
-      u2[k] = 0.0;
+      u2[k] = R(0);
       l[k] = m;
-      piv[k] = 0.0;
+      piv[k] = R(0);
       a = al - m * b;
       b = be;
     } else {
-      const double m = a / g;
+      const R m = a / g;
       u0[k] = g;
       u1[k] = al;
       u2[k] = be;
       l[k] = m;
-      piv[k] = 1.0;
+      piv[k] = R(1);
       a = b - m * al;
       b = -m * be;
     }
   }
-  if (fabs(a) < tiny) a = a < 0.0 ? -tiny : tiny;
+  if (rabs(a) < tiny) a = a < R(0) ? -tiny : tiny;
   u0[n - 1] = a;
 }
 
@@ -211,12 +219,14 @@ RPA_HD void lu_factor(const double* d, const double* e, int n, double lambda, do
 // live in global memory on the device, where a fetch takes hundreds of cycles),
 // with the arithmetic in the same order as one step at a time.
 constexpr int PF = 8;
-RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane y) {
+template <typename R>
+RPA_HD R lu_solve(int n, LaneT<R> u0, LaneT<R> u1, LaneT<R> u2, LaneT<R> l, LaneT<R> piv,
+                  LaneT<R> y) {
   // forward: row exchanges and multipliers; cur = y[k] as updated so far
-  double cur = n > 0 ? y[0] : 0.0;
+  R cur = n > 0 ? y[0] : R(0);
   for (int k0 = 0; k0 + 1 < n; k0 += PF) {
     const int cnt = (n - 1 - k0) < PF ? (n - 1 - k0) : PF;
-    double bp[PF], bl[PF], by[PF];
+    R bp[PF], bl[PF], by[PF];
     for (int t = 0; t < cnt; ++t) {
       bp[t] = piv[k0 + t];
       bl[t] = l[k0 + t];
@@ -224,8 +234,8 @@ RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane 
     }
     for (int t = 0; t < cnt; ++t) {
       const int k = k0 + t;
-      if (bp[t] != 0.0) {
-        const double yk = cur, yk1 = by[t];
+      if (bp[t] != R(0)) {
+        const R yk = cur, yk1 = by[t];
         y[k] = yk1;
         cur = yk - bl[t] * yk1;
       } else {
@@ -235,13 +245,13 @@ RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane 
     }
   }
   if (n > 0) y[n - 1] = cur;
-  double scale = 1.0;
-  const double big = 1e150;
+  R scale = R(1);
+  const R big = sizeof(R) == 4 ? R(1e30) : R(1e150);
   // backward: s_k = (y_k - u1_k s_{k+1} - u2_k s_{k+2}) / u0_k
-  double s1 = 0.0, s2 = 0.0;  // s_{k+1}, s_{k+2}
+  R s1 = R(0), s2 = R(0);  // s_{k+1}, s_{k+2}
   for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
     const int cnt = (k0 + 1) < PF ? (k0 + 1) : PF;
-    double by[PF], b0[PF], b1[PF], b2[PF];
+    R by[PF], b0[PF], b1[PF], b2[PF];
     for (int t = 0; t < cnt; ++t) {
       const int k = k0 - t;
       by[t] = y[k];
@@ -251,18 +261,18 @@ RPA_HD double lu_solve(int n, Lane u0, Lane u1, Lane u2, Lane l, Lane piv, Lane 
     }
     for (int t = 0; t < cnt; ++t) {
       const int k = k0 - t;
-      double s = by[t];
+      R s = by[t];
       if (k + 1 < n) s -= b1[t] * s1;
       if (k + 2 < n) s -= b2[t] * s2;
       s /= b0[t];
-      if (fabs(s) > big) {
+      if (rabs(s) > big) {
         // rescale the solved tail (and the rest of the right-hand side) by 1/big
-        for (int i = 0; i < n; ++i) y[i] *= 1.0 / big;
-        for (int t2 = t + 1; t2 < cnt; ++t2) by[t2] *= 1.0 / big;
-        s1 *= 1.0 / big;
-        s2 *= 1.0 / big;
-        s *= 1.0 / big;
-        scale *= 1.0 / big;
+        for (int i = 0; i < n; ++i) y[i] *= R(1) / big;
+        for (int t2 = t + 1; t2 < cnt; ++t2) by[t2] *= R(1) / big;
+        s1 *= R(1) / big;
+        s2 *= R(1) / big;
+        s *= R(1) / big;
+        scale *= R(1) / big;
       }
       y[k] = s;
       s2 = s1;
@@ -285,40 +295,43 @@ RPA_HD double start_component(int j, long i) {
 
 // Eigenvectors of the cluster w[j0..j1-1] by inverse iteration.  Column j of Z is
 // z[i * ldz + j] (row-major, i the row).  The scratch lanes hold n elements each.
-RPA_HD void cluster_vectors(const double* d, const double* e, int n, const double* w, int j0,
-                            int j1, double tiny, double* z, long ldz, Lane u0, Lane u1,
-                            Lane u2, Lane l, Lane piv, Lane y) {
+// R: the arithmetic and scratch type (double, or float for a T that is itself an FP32
+// object); w and z are FP64 either way.
+template <typename R>
+RPA_HD void cluster_vectors(const R* d, const R* e, int n, const double* w, int j0, int j1,
+                            R tiny, double* z, long ldz, LaneT<R> u0, LaneT<R> u1, LaneT<R> u2,
+                            LaneT<R> l, LaneT<R> piv, LaneT<R> y) {
   for (int j = j0; j < j1; ++j) {
-    lu_factor(d, e, n, w[j], tiny, u0, u1, u2, l, piv);
-    double nrm2 = 0.0;
+    lu_factor(d, e, n, (R)w[j], tiny, u0, u1, u2, l, piv);
+    R nrm2 = R(0);
     for (long i = 0; i < n; ++i) {
-      y[i] = start_component(j, i);
+      y[i] = (R)start_component(j, i);
       nrm2 += y[i] * y[i];
     }
     for (int it = 0; it < 3; ++it) {
-      const double s = 1.0 / sqrt(nrm2);
+      const R s = R(1) / sqrt(nrm2);
       for (long i = 0; i < n; ++i) y[i] *= s;
       lu_solve(n, u0, u1, u2, l, piv, y);
       // modified Gram-Schmidt against the cluster's earlier (unit) vectors
       for (int jj = j0; jj < j; ++jj) {
-        double dot = 0.0;
-        for (long i = 0; i < n; ++i) dot += z[i * ldz + jj] * y[i];
-        for (long i = 0; i < n; ++i) y[i] -= dot * z[i * ldz + jj];
+        R dot = R(0);
+        for (long i = 0; i < n; ++i) dot += (R)z[i * ldz + jj] * y[i];
+        for (long i = 0; i < n; ++i) y[i] -= dot * (R)z[i * ldz + jj];
       }
-      nrm2 = 0.0;
+      nrm2 = R(0);
       for (long i = 0; i < n; ++i) nrm2 += y[i] * y[i];
-      if (!(nrm2 > 0.0)) {
+      if (!(nrm2 > R(0))) {
         // the solve returned nothing outside the earlier vectors: restart from a
         // different pseudo-random vector
-        nrm2 = 0.0;
+        nrm2 = R(0);
         for (long i = 0; i < n; ++i) {
-          y[i] = start_component(j + 7919 * (it + 1), i);
+          y[i] = (R)start_component(j + 7919 * (it + 1), i);
           nrm2 += y[i] * y[i];
         }
       }
     }
-    const double s = 1.0 / sqrt(nrm2);
-    for (long i = 0; i < n; ++i) z[i * ldz + j] = y[i] * s;
+    const R s = R(1) / sqrt(nrm2);
+    for (long i = 0; i < n; ++i) z[i * ldz + j] = (double)(y[i] * s);
   }
 }
 

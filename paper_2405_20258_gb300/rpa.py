@@ -24,7 +24,7 @@ RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
             "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings",
-            "rpa_trace_term_static")
+            "rpa_trace_term_static", "rpa_tridiagonalize", "rpa_hermitian_eig_jacobi")
 STATIC_TRACE_MAX_VC = 524288
 TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other", "slice")
 
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
         "rpa_version": ([], ctypes.c_char_p),
         "rpa_plan_timings": ([vp, vp, vp], i),
         "rpa_trace_term_static": ([vp, i, i, i, vp, vp, vp, i, d, vp, vp], i),
+        "rpa_tridiagonalize": ([i, i, vp, vp, vp, vp], i),
+        "rpa_hermitian_eig_jacobi": ([i, vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -286,6 +288,24 @@ def rpa_trace_term_static(mtilde, n_eig, n_v, n_c, e_v, e_c, omega, n_freq, omeg
     _check(load().rpa_trace_term_static(_ptr(mtilde), int(n_eig), int(n_v), int(n_c), _ptr(e_v),
                                         _ptr(e_c), _ptr(omega), int(n_freq), float(omega_cell),
                                         _ptr(trace_out), _stream(stream)))
+
+
+def rpa_tridiagonalize(a, d, e, stream=None):
+    """Householder tridiagonalisation T = Q^H A Q of the square Hermitian device tensor
+    a (complex64: FP32, complex128: FP64; read column-major, overwritten with the
+    reflectors) into the real device tensors d (n) and e (n - 1)."""
+    import torch
+    bits = 64 if a.dtype == torch.complex128 else 32
+    _check(load().rpa_tridiagonalize(int(a.shape[0]), bits, _ptr(a), _ptr(d), _ptr(e),
+                                     _stream(stream)))
+
+
+def rpa_hermitian_eig_jacobi(g, theta, y, stream=None):
+    """All eigenpairs of the Hermitian complex128 device tensor g (m x m, read
+    column-major, destroyed) by the library's Jacobi solver: theta (m, ascending) and
+    the column-major eigenvectors y (m x m complex128)."""
+    _check(load().rpa_hermitian_eig_jacobi(int(g.shape[0]), _ptr(g), _ptr(theta), _ptr(y),
+                                           _stream(stream)))
 
 
 def rpa_version():
