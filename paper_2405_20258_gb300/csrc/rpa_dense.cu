@@ -163,7 +163,9 @@ size_t bar_words(int grid) { return BAR_FLAGS + (size_t)BAR_STRIDE * (size_t)gri
 //      is recomputed by each CTA from y_{k+1} (the same arithmetic, so the same
 //      value).
 // After 32 columns (or the last): barrier, A(k+1:, k+1:) -= V W^H + W V^H over the
-// CTA's columns, barrier.
+// CTA's columns (register-tiled: a lane updates up to four rows of four columns per
+// pass over the panel), barrier.  Each step issues its global loads in one round:
+// what a step needs from other CTAs was written before the barrier that opens it.
 // ---------------------------------------------------------------------------
 constexpr int PNB = 32;             // panel width
 constexpr int HT = 512;             // threads per CTA
@@ -171,7 +173,13 @@ constexpr int HW = HT / 32;         // warps per CTA
 constexpr int PL = 2 * PNB + 1;     // partial sums per CTA
 constexpr int MAXG = 160;           // largest persistent grid (the sums' staging)
 constexpr int MAXOWN = 128;         // rows a CTA may own (n <= MAXOWN * grid)
-constexpr int RJ = 32;              // rows per chunk of the trailing update
+
+// Rows per chunk of the trailing update staged in shared memory: 128 (FP32) or 32
+// (FP64); a lane updates up to RJ/32 rows of four columns per pass.
+template <typename T>
+__host__ __device__ constexpr int rj_rows() {
+  return sizeof(T) == 4 ? 128 : 32;
+}
 
 template <typename T>
 struct HetrdArgs {
@@ -187,36 +195,42 @@ struct HetrdArgs {
 };
 
 // The reflector v of the current column is staged in shared memory when it has at
-// most VCAP elements (96 KB); longer ones are read from L2.
+// most VCAP elements (96 KB); longer ones are read from L2.  During a trailing
+// update the same space holds conj W(i, :) and conj V(i, :) of the CTA's columns.
 template <typename T>
 __host__ __device__ constexpr int vcap() {
   return (int)(96 * 1024 / sizeof(typename CxT<T>::C));
 }
 
+// Shared memory of hetrd_kernel in complex elements: y and v of the CTA's columns
+// (2 MAXOWN), partial sums (PL MAXG/4), their totals (PL), W^H v and V^H v (2 PNB),
+// the staged panel rows of a trailing-update chunk (2 RJ (PNB + 1)), scalars (8),
+// the staged reflector (vcap).
 template <typename T>
 size_t hetrd_smem() {
   using C = typename CxT<T>::C;
-  return sizeof(C) *
-         (MAXOWN + PL * (MAXG / 4) + PL + 4 * PNB + 2 * RJ * (PNB + 1) + 2 * HW * PNB + 4 + vcap<T>());
+  return sizeof(C) * (2 * MAXOWN + PL * (MAXG / 4) + PL + 2 * PNB +
+                      2 * rj_rows<T>() * (PNB + 1) + 8 + vcap<T>());
 }
 
 template <typename T>
 __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
   using C = typename CxT<T>::C;
+  constexpr int RJT = rj_rows<T>();
+  constexpr int RL = RJT / 32;                // rows per lane of a whole chunk
+  constexpr int NCB = vcap<T>() / (2 * PNB);  // columns staged per trailing-update batch
+  static_assert(NCB % 4 == 0, "column batches of whole quads");
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* xs = (C*)smraw;            // [MAXOWN] this CTA's x
-  C* red = xs + MAXOWN;         // [PL * MAXG/4] (>= HW * PL)
+  C* ys = (C*)smraw;               // [MAXOWN] y_i of this CTA's columns (step B to C)
+  C* vsv = ys + MAXOWN;            // [MAXOWN] v_i of this CTA's columns
+  C* red = vsv + MAXOWN;           // [PL * MAXG/4] (>= HW * PL)
   C* tot = red + PL * (MAXG / 4);  // [PL]
-  C* vk = tot + PL;             // [PNB] V(k, :)
-  C* wk = vk + PNB;             // [PNB] W(k, :)
-  C* s1 = wk + PNB;             // [PNB] W^H v
-  C* s2 = s1 + PNB;             // [PNB] V^H v
-  C* Vs = s2 + PNB;             // [RJ][PNB + 1]
-  C* Ws = Vs + RJ * (PNB + 1);  // [RJ][PNB + 1]
-  C* wb = Ws + RJ * (PNB + 1);  // [HW][PNB] conj W(i, :)
-  C* vb = wb + HW * PNB;        // [HW][PNB] conj V(i, :)
-  C* scal = vb + HW * PNB;      // tau, sc, alpha2, W(k+1, c)
-  C* vsm = scal + 4;            // [vcap] v(k+1 : n) when it fits
+  C* s1 = tot + PL;                // [PNB] W^H v
+  C* s2 = s1 + PNB;                // [PNB] V^H v
+  C* Vs = s2 + PNB;                // [RJT][PNB + 1]
+  C* Ws = Vs + RJT * (PNB + 1);    // [RJT][PNB + 1]
+  C* scal = Ws + RJT * (PNB + 1);  // tau, sc, alpha2, W(k+1, c), alpha
+  C* vsm = scal + 8;               // [vcap] v(k+1 : n) when it fits
   const int n = p.n, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5,
             lane = tid & 31;
   const int rend = n > b ? (n - b + G - 1) / G : 0;  // local r < rend: i = b + G r < n
@@ -224,75 +238,82 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
   int c = 0;
   if (tid == 0) scal[3] = C{0, 0};
   for (int k = 0; k < n; ++k) {
-    // ---- A: this CTA's rows of the updated column k
+    // W(i, c-1) of this CTA's rows, written by other threads of the CTA in step C of
+    // the previous column, is read below
+    __syncthreads();
+    // ---- A: this CTA's rows of the updated column k and their partial sums, one
+    // round of loads per row.  Row k of the panel is held by lane q < c of every
+    // warp: V(k, c-1) = 1, W(k, c-1) as recomputed in step C of the previous column.
     const int rbeg = k > b ? (k - b + G - 1) / G : 0;
     const int nown = max(0, rend - rbeg);
-    if (tid < c) {
-      vk[tid] = tid == c - 1 ? C{1, 0} : __ldcg(&p.vp[(size_t)k * PNB + tid]);
-      wk[tid] = tid == c - 1 ? scal[3] : __ldcg(&p.wp[(size_t)k * PNB + tid]);
+    C vkl = {0, 0}, wkl = {0, 0};
+    if (lane < c) {
+      vkl = lane == c - 1 ? C{1, 0} : __ldcg(&p.vp[(size_t)k * PNB + lane]);
+      wkl = lane == c - 1 ? scal[3] : __ldcg(&p.wp[(size_t)k * PNB + lane]);
     }
-    __syncthreads();
-    // a warp per owned row, lanes over the panel's columns
+    C a1 = {0, 0}, a2 = {0, 0};
+    T nrm = T(0);
+    // a warp per owned row, lanes over the panel's columns; partial sums over the
+    // rows >= k+2 (per warp in row order, then warps in order): ||x||^2, W^H x, V^H x
     for (int q = warp; q < nown; q += HW) {
       const int i = b + G * (rbeg + q);
-      C term = {0, 0};
-      if (lane < c)
-        term = cadd(cmul_cb(__ldcg(&p.vp[(size_t)i * PNB + lane]), wk[lane]),
-                    cmul_cb(__ldcg(&p.wp[(size_t)i * PNB + lane]), vk[lane]));
-      term = warp_csum(term);
+      C vil = {0, 0}, wil = {0, 0};
+      if (lane < c) {
+        vil = __ldcg(&p.vp[(size_t)i * PNB + lane]);
+        wil = __ldcg(&p.wp[(size_t)i * PNB + lane]);
+      }
+      const C aik = __ldcg(&p.a[(size_t)k * n + i]);
+      const C x = csub(aik, warp_csum(cadd(cmul_cb(vil, wkl), cmul_cb(wil, vkl))));
       if (lane == 0) {
-        const C x = csub(__ldcg(&p.a[(size_t)k * n + i]), term);
-        xs[q] = x;
         if (i == k)
           p.d[k] = x.x;
         else
           p.xcol[i] = x;
       }
+      if (i >= k + 2) {
+        nrm += x.x * x.x + x.y * x.y;
+        a1 = cadd(a1, cmul_ca(wil, x));
+        a2 = cadd(a2, cmul_ca(vil, x));
+      }
     }
     if (k == n - 1) break;
+    if (lane == 0) red[warp * PL] = C{nrm, T(0)};
+    if (lane < c) {
+      red[warp * PL + 1 + lane] = a1;
+      red[warp * PL + 1 + c + lane] = a2;
+    }
     __syncthreads();
-    {
-      // partial sums over this CTA's rows >= k+2 (per warp in row order, then warps
-      // in order): ||x||^2, W^H x, V^H x
-      C a1 = {0, 0}, a2 = {0, 0};
-      T nrm = T(0);
-      for (int q = warp; q < nown; q += HW) {
-        const int i = b + G * (rbeg + q);
-        if (i < k + 2) continue;
-        const C x = xs[q];
-        nrm += x.x * x.x + x.y * x.y;
-        if (lane < c) {
-          a1 = cadd(a1, cmul_ca(__ldcg(&p.wp[(size_t)i * PNB + lane]), x));
-          a2 = cadd(a2, cmul_ca(__ldcg(&p.vp[(size_t)i * PNB + lane]), x));
-        }
-      }
-      if (lane == 0) red[warp * PL] = C{nrm, T(0)};
-      if (lane < c) {
-        red[warp * PL + 1 + lane] = a1;
-        red[warp * PL + 1 + c + lane] = a2;
-      }
-      __syncthreads();
-      if (tid <= 2 * c) {
-        C acc = {0, 0};
-        for (int w = 0; w < HW; ++w) acc = cadd(acc, red[w * PL + tid]);
-        p.part[(size_t)b * PL + tid] = acc;
-      }
+    if (tid <= 2 * c) {
+      C acc = {0, 0};
+      for (int w = 0; w < HW; ++w) acc = cadd(acc, red[w * PL + tid]);
+      p.part[(size_t)b * PL + tid] = acc;
     }
     if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
 
-    // ---- B: reflector and A_eff v over this CTA's columns
+    // ---- B: reflector and A_eff v over this CTA's columns.  One round of
+    // independent loads: every CTA's partial sums, alpha = x(k+1), row k+1 of the
+    // panel, and x(k+2:) staged unscaled.
     const int L = 2 * c + 1;
-    // every entry's G partials in nsg segments of at most four (one round of loads)
-    const int nsg = (G + 3) / 4;
+    const int nsg = (G + 3) / 4;  // every entry's G partials in segments of at most four
+    const int j0 = k + 1, len = n - j0;
+    const bool staged = len <= vcap<T>();
     for (int w = tid; w < L * nsg; w += HT) {
       const int q = w / nsg, sg = w % nsg;
       const int g0 = sg * 4;
       C a0 = __ldcg(&p.part[(size_t)g0 * PL + q]);
-      const C a1 = g0 + 1 < G ? __ldcg(&p.part[(size_t)(g0 + 1) * PL + q]) : C{0, 0};
-      const C a2 = g0 + 2 < G ? __ldcg(&p.part[(size_t)(g0 + 2) * PL + q]) : C{0, 0};
-      const C a3 = g0 + 3 < G ? __ldcg(&p.part[(size_t)(g0 + 3) * PL + q]) : C{0, 0};
-      red[w] = cadd(cadd(a0, a1), cadd(a2, a3));
+      const C b1 = g0 + 1 < G ? __ldcg(&p.part[(size_t)(g0 + 1) * PL + q]) : C{0, 0};
+      const C b2 = g0 + 2 < G ? __ldcg(&p.part[(size_t)(g0 + 2) * PL + q]) : C{0, 0};
+      const C b3 = g0 + 3 < G ? __ldcg(&p.part[(size_t)(g0 + 3) * PL + q]) : C{0, 0};
+      red[w] = cadd(cadd(a0, b1), cadd(b2, b3));
     }
+    C wr1 = {0, 0}, vr1 = {0, 0};
+    if (tid < c) {
+      wr1 = __ldcg(&p.wp[(size_t)(k + 1) * PNB + tid]);
+      vr1 = __ldcg(&p.vp[(size_t)(k + 1) * PNB + tid]);
+    }
+    if (tid == HT - 1) scal[4] = __ldcg(&p.xcol[k + 1]);
+    if (staged)
+      for (int t = tid; t < len; t += HT) vsm[t] = t == 0 ? C{1, 0} : __ldcg(&p.xcol[j0 + t]);
     __syncthreads();
     if (tid < L) {
       C t = {0, 0};
@@ -301,7 +322,7 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     }
     __syncthreads();
     if (tid == 0) {
-      const C alpha = __ldcg(&p.xcol[k + 1]);
+      const C alpha = scal[4];
       const T xn2 = tot[0].x;
       C tau, sc;
       T beta;
@@ -310,8 +331,8 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
         sc = C{0, 0};
         beta = alpha.x;
       } else {
-        const T nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-        beta = alpha.x >= T(0) ? -nrm : nrm;
+        const T nrm2 = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+        beta = alpha.x >= T(0) ? -nrm2 : nrm2;
         tau = C{(beta - alpha.x) / beta, -alpha.y / beta};
         const T dx = alpha.x - beta, dy = alpha.y, dd = dx * dx + dy * dy;
         sc = C{dx / dd, -dy / dd};
@@ -326,19 +347,14 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     __syncthreads();
     const C tau = scal[0], sc = scal[1];
     if (tid < c) {
-      s1[tid] = cadd(cconj(__ldcg(&p.wp[(size_t)(k + 1) * PNB + tid])), cmul(sc, tot[1 + tid]));
-      s2[tid] = cadd(cconj(__ldcg(&p.vp[(size_t)(k + 1) * PNB + tid])), cmul(sc, tot[1 + c + tid]));
+      s1[tid] = cadd(cconj(wr1), cmul(sc, tot[1 + tid]));
+      s2[tid] = cadd(cconj(vr1), cmul(sc, tot[1 + c + tid]));
     }
+    if (staged)
+      for (int t = 1 + tid; t < len; t += HT) vsm[t] = cmul(vsm[t], sc);
     __syncthreads();
     const int cbeg = k + 1 > b ? (k + 1 - b + G - 1) / G : 0;
     const int ncol = max(0, rend - cbeg);
-    const int j0 = k + 1, len = n - j0;
-    const bool staged = len <= vcap<T>();
-    if (staged) {
-      for (int t = tid; t < len; t += HT)
-        vsm[t] = t == 0 ? C{1, 0} : cmul(__ldcg(&p.xcol[j0 + t]), sc);
-      __syncthreads();
-    }
     C yvp = {0, 0};
     // Work items (column q, segment sg): when a CTA has fewer columns than warps,
     // each column's dot product is cut into nseg segments so that every warp streams
@@ -358,6 +374,8 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
         p.ycol[i] = y;
         p.vp[(size_t)i * PNB + c] = vi;
         p.a[(size_t)k * n + i] = vi;
+        ys[q] = y;
+        vsv[q] = vi;
         yvp = cadd(yvp, cmul_ca(y, vi));
       }
     };
@@ -410,8 +428,9 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     }
     if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
 
-    // ---- C: the panel's W column
+    // ---- C: the panel's W column (y and v of the CTA's columns from shared memory)
     if (warp == 0) {
+      const C y1 = lane == 0 ? __ldcg(&p.ycol[k + 1]) : C{0, 0};
       C t = {0, 0};
       for (int g = lane; g < G; g += 32) t = cadd(t, __ldcg(&p.part2[g]));
       t = warp_csum(t);
@@ -419,48 +438,100 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
         const T t2 = tau.x * tau.x + tau.y * tau.y;
         const C alpha2 = C{T(-0.5) * t2 * t.x, T(-0.5) * t2 * t.y};
         scal[2] = alpha2;
-        scal[3] = cadd(cmul(tau, __ldcg(&p.ycol[k + 1])), alpha2);
+        scal[3] = cadd(cmul(tau, y1), alpha2);
       }
     }
     __syncthreads();
     const C alpha2 = scal[2];
     for (int q = tid; q < ncol; q += HT) {
       const int i = b + G * (cbeg + q);
-      const C y = __ldcg(&p.ycol[i]);
-      const C vi = __ldcg(&p.vp[(size_t)i * PNB + c]);
-      p.wp[(size_t)i * PNB + c] = cadd(cmul(tau, y), cmul(alpha2, vi));
+      p.wp[(size_t)i * PNB + c] = cadd(cmul(tau, ys[q]), cmul(alpha2, vsv[q]));
     }
     ++c;
     if (c == PNB || k == n - 2) {
       if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
-      // trailing update of this CTA's columns i >= k+1, rows j >= k+1
+      // trailing update of this CTA's columns i >= k+1, rows j >= k+1:
+      // A(j, i) -= sum_q V(j, q) conj(W(i, q)) + W(j, q) conj(V(i, q)).  The columns'
+      // conj W(i, :), conj V(i, :) are staged in batches of NCB (in the reflector's
+      // space), the rows in chunks of RJT; a warp takes a quad of columns and a
+      // slice of the chunk's rows, a lane up to RL rows of the quad.
       const int kn = k + 1;
-      for (int j0 = kn; j0 < n; j0 += RJ) {
+      const int cb2 = kn > b ? (kn - b + G - 1) / G : 0;
+      const int nc2 = max(0, rend - cb2);
+      C* wcs = vsm;              // [NCB][PNB]
+      C* vcs = vsm + NCB * PNB;  // [NCB][PNB]
+      for (int cb0 = 0; cb0 < nc2; cb0 += NCB) {
+        const int ncb = min(NCB, nc2 - cb0);
         __syncthreads();
-        for (int e = tid; e < RJ * PNB; e += HT) {
-          const int r = e / PNB, qq = e % PNB, j = j0 + r;
-          const bool in = j < n && qq < c;
-          Vs[r * (PNB + 1) + qq] = in ? __ldcg(&p.vp[(size_t)j * PNB + qq]) : C{0, 0};
-          Ws[r * (PNB + 1) + qq] = in ? __ldcg(&p.wp[(size_t)j * PNB + qq]) : C{0, 0};
+        for (int e = tid; e < ncb * PNB; e += HT) {
+          const int q = e / PNB, qq = e % PNB, i = b + G * (cb2 + cb0 + q);
+          const bool in = qq < c;
+          wcs[e] = in ? cconj(__ldcg(&p.wp[(size_t)i * PNB + qq])) : C{0, 0};
+          vcs[e] = in ? cconj(__ldcg(&p.vp[(size_t)i * PNB + qq])) : C{0, 0};
         }
-        __syncthreads();
-        for (int q = warp; q < ncol; q += HW) {
-          const int i = b + G * (cbeg + q);
-          if (lane < c) {
-            wb[warp * PNB + lane] = cconj(__ldcg(&p.wp[(size_t)i * PNB + lane]));
-            vb[warp * PNB + lane] = cconj(__ldcg(&p.vp[(size_t)i * PNB + lane]));
+        // row slices per chunk: the fewest passes x rows per lane, ties to fewer slices
+        const int nquad = (ncb + 3) / 4;
+        int rs = 1, best = 1 << 30;
+        for (int r = 1; r <= RL; r *= 2) {
+          const int cost = ((nquad * r + HW - 1) / HW) * (RL / r);
+          if (cost < best) {
+            best = cost;
+            rs = r;
           }
-          __syncwarp();
-          const int j = j0 + lane;
-          if (lane < RJ && j < n) {
-            C acc = {0, 0};
-            for (int qq = 0; qq < c; ++qq)
-              acc = cadd(acc, cadd(cmul(Vs[lane * (PNB + 1) + qq], wb[warp * PNB + qq]),
-                                   cmul(Ws[lane * (PNB + 1) + qq], vb[warp * PNB + qq])));
-            C* aji = &p.a[(size_t)i * n + j];
-            *aji = csub(__ldcg(aji), acc);
+        }
+        const int nr = RL / rs;
+        for (int r0 = kn; r0 < n; r0 += RJT) {
+          __syncthreads();
+          for (int e = tid; e < RJT * PNB; e += HT) {
+            const int r = e / PNB, qq = e % PNB, j = r0 + r;
+            const bool in = j < n && qq < c;
+            Vs[r * (PNB + 1) + qq] = in ? __ldcg(&p.vp[(size_t)j * PNB + qq]) : C{0, 0};
+            Ws[r * (PNB + 1) + qq] = in ? __ldcg(&p.wp[(size_t)j * PNB + qq]) : C{0, 0};
           }
-          __syncwarp();
+          __syncthreads();
+          for (int it = warp; it < nquad * rs; it += HW) {
+            const int quad = it / rs, sl = it % rs;
+            const int rb = sl * (RJT / rs) + lane;  // this lane's rows: rb + 32 u, u < nr
+            const C* wq = wcs + quad * 4 * PNB;
+            const C* vq = vcs + quad * 4 * PNB;
+            C acc[RL][4];
+#pragma unroll
+            for (int u = 0; u < RL; ++u)
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) acc[u][cc] = C{0, 0};
+            for (int qq = 0; qq < c; ++qq) {
+              C vr[RL], wr[RL];
+#pragma unroll
+              for (int u = 0; u < RL; ++u)
+                if (u < nr) {
+                  vr[u] = Vs[(rb + 32 * u) * (PNB + 1) + qq];
+                  wr[u] = Ws[(rb + 32 * u) * (PNB + 1) + qq];
+                }
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) {
+                const C wcv = wq[cc * PNB + qq], vcv = vq[cc * PNB + qq];
+#pragma unroll
+                for (int u = 0; u < RL; ++u)
+                  if (u < nr)
+                    acc[u][cc] = cadd(acc[u][cc], cadd(cmul(vr[u], wcv), cmul(wr[u], vcv)));
+              }
+            }
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const int q = quad * 4 + cc;
+              if (q < ncb) {
+                const int i = b + G * (cb2 + cb0 + q);
+#pragma unroll
+                for (int u = 0; u < RL; ++u) {
+                  const int j = r0 + rb + 32 * u;
+                  if (u < nr && j < n) {
+                    C* aji = &p.a[(size_t)i * n + j];
+                    *aji = csub(__ldcg(aji), acc[u][cc]);
+                  }
+                }
+              }
+            }
+          }
         }
       }
       if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;

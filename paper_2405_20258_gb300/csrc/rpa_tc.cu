@@ -891,46 +891,77 @@ __global__ void proj_b_slice_kernel(const double2* B, int n_g, int n_eig, int n_
 // each maximum bounds the FP64 one from above (a row exponent may come out one
 // larger, never smaller); a product above the FP32 range is taken in FP64.
 constexpr int MAX_GROUP = 8;   // frequencies per chis_b kernel launch (upper bound)
+constexpr int RMR = 4;         // rows of M~ per block of the chi_s operand kernels
 constexpr int CHIS_PLANE_GB = 64;  // default budget of the two chi_s B plane buffers
 constexpr int PROJ_PLANE_GB = 48;  // default budget of the projection's A planes
 __global__ void chis_b_rowmax_kernel(const double2* mt, int n_eig, int n_vc, const float* f_up,
                                      const double* f, int nb, unsigned long long* rowmax,
                                      int stride) {
-  __shared__ double red[MAX_GROUP][32];
-  const int j = blockIdx.x;
+  // RMR rows of M~ per block, so that each f value read serves RMR rows
+  __shared__ double red[RMR][MAX_GROUP][8];
+  __shared__ int ovf_s;
+  const int j0 = blockIdx.x * RMR;
   const long v0 = (long)blockIdx.y * CHUNK, v1 = min((long)n_vc, v0 + CHUNK);
-  float m[MAX_GROUP];
-  double mbig[MAX_GROUP];
+  if (threadIdx.x == 0) ovf_s = 0;
+  __syncthreads();
+  float m[RMR][MAX_GROUP];
 #pragma unroll
-  for (int b = 0; b < MAX_GROUP; ++b) {
-    m[b] = 0.f;
-    mbig[b] = 0.0;
-  }
+  for (int r = 0; r < RMR; ++r)
+#pragma unroll
+    for (int b = 0; b < MAX_GROUP; ++b) m[r][b] = 0.f;
+  bool ovf = false;
   for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
-    const double2 x = mt[(long)j * n_vc + vc];
-    const double ad = fmax(fabs(x.x), fabs(x.y));
-    const float a = __double2float_ru(ad);
+    float a[RMR];
+#pragma unroll
+    for (int r = 0; r < RMR; ++r) {
+      const double2 x = j0 + r < n_eig ? mt[(long)(j0 + r) * n_vc + vc] : make_double2(0.0, 0.0);
+      a[r] = __double2float_ru(fmax(fabs(x.x), fabs(x.y)));
+    }
 #pragma unroll
     for (int b = 0; b < MAX_GROUP; ++b)
       if (b < nb) {
-        const float pr = __fmul_ru(f_up[(long)b * n_vc + vc], a);
-        if (pr <= 3.0e38f)
-          m[b] = fmaxf(m[b], pr);
-        else
-          mbig[b] = fmax(mbig[b], f[(long)b * n_vc + vc] * ad);
+        const float fu = f_up[(long)b * n_vc + vc];
+#pragma unroll
+        for (int r = 0; r < RMR; ++r) {
+          const float pr = __fmul_ru(fu, a[r]);
+          if (pr <= 3.0e38f)
+            m[r][b] = fmaxf(m[r][b], pr);
+          else
+            ovf = true;
+        }
       }
   }
+  if (ovf) ovf_s = 1;
 #pragma unroll
-  for (int b = 0; b < MAX_GROUP; ++b) {
-    double v = fmax((double)m[b], mbig[b]);
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) red[b][threadIdx.x >> 5] = v;
-  }
+  for (int r = 0; r < RMR; ++r)
+#pragma unroll
+    for (int b = 0; b < MAX_GROUP; ++b) {
+      float v = m[r][b];
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((threadIdx.x & 31) == 0) red[r][b][threadIdx.x >> 5] = (double)v;
+    }
   __syncthreads();
-  if (threadIdx.x < nb) {
+  if (ovf_s) {
+    // a product beyond the FP32 range (rare): this block's maxima in FP64 instead
+    for (int q = 0; q < RMR * nb; ++q) {
+      const int r = q / nb, b = q % nb;
+      double v = 0.0;
+      if (j0 + r < n_eig)
+        for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
+          const double2 x = mt[(long)(j0 + r) * n_vc + vc];
+          v = fmax(v, f[(long)b * n_vc + vc] * fmax(fabs(x.x), fabs(x.y)));
+        }
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) red[r][b][threadIdx.x >> 5] = v;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < RMR * nb) {
+    const int r = threadIdx.x / nb, b = threadIdx.x % nb, j = j0 + r;
     double mm = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[threadIdx.x][w]);
-    if (mm > 0.0) atomic_max_pos(rowmax + (long)threadIdx.x * stride + j, mm);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[r][b][w]);
+    if (j < n_eig && mm > 0.0) atomic_max_pos(rowmax + (long)b * stride + j, mm);
   }
 }
 
@@ -941,53 +972,61 @@ __global__ void float_up_kernel(const double* f, long n, float* out) {
 }
 
 // chi_s B operand of the group's frequencies: for row j, f_b(vc) M~[j][vc] as
-// rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); grid (n_eig_pad, chunks).
+// rows 2j = (f m_r, f m_i) and 2j+1 = (-f m_i, f m_r); RMR rows j per block (each f
+// value read serves all of them), grid (ceil(n_eig_pad / RMR), chunks).
 template <typename P>
 __global__ void chis_b_slice_kernel(const double2* mt, int n_eig, int n_eig_pad, int n_vc,
                                     long K, const double* f, int nb, int S,
                                     const unsigned long long* rowmax, P* planes, int* exps,
                                     int eb_stride, int split) {
-  const int j = blockIdx.x;
-  __shared__ int e[MAX_GROUP];
-  if (threadIdx.x < MAX_GROUP) {
-    const int b = threadIdx.x;
-    e[b] = (b < nb && j < n_eig)
-               ? row_exponent(__longlong_as_double((long long)rowmax[(long)b * eb_stride + j]))
-               : 0;
-    if (blockIdx.y == 0 && b < nb) exps[b * eb_stride + j] = e[b];
+  const int j0 = blockIdx.x * RMR;
+  __shared__ int e[RMR][MAX_GROUP];
+  if (threadIdx.x < RMR * MAX_GROUP) {
+    const int r = threadIdx.x / MAX_GROUP, b = threadIdx.x % MAX_GROUP, j = j0 + r;
+    e[r][b] = (b < nb && j < n_eig)
+                  ? row_exponent(__longlong_as_double((long long)rowmax[(long)b * eb_stride + j]))
+                  : 0;
+    if (blockIdx.y == 0 && b < nb && j < n_eig_pad) exps[b * eb_stride + j] = e[r][b];
   }
   __syncthreads();
   const long plane = (long)2 * n_eig_pad * (K / 2);
   const long v0 = (long)blockIdx.y * CHUNK, v1 = min(K / 2, v0 + CHUNK);
   for (long vc = v0 + threadIdx.x; vc < v1; vc += blockDim.x) {
-    double2 x = make_double2(0.0, 0.0);
-    const bool in = j < n_eig && vc < n_vc;
-    if (in) x = mt[(long)j * n_vc + vc];
+    double2 x[RMR];
+#pragma unroll
+    for (int r = 0; r < RMR; ++r)
+      x[r] = (j0 + r < n_eig && vc < n_vc) ? mt[(long)(j0 + r) * n_vc + vc]
+                                           : make_double2(0.0, 0.0);
 #pragma unroll 1
     for (int b = 0; b < nb; ++b) {
-      const double fv = in ? f[(long)b * n_vc + vc] : 0.0;
-      P* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
-      if (split) {
-        emit_split<P>(fv * x.x, fv * x.y, e[b], S, [&](int s, float fr, float fi) {
+      const double fv = vc < n_vc ? f[(long)b * n_vc + vc] : 0.0;
+#pragma unroll
+      for (int r = 0; r < RMR; ++r) {
+        const int j = j0 + r;
+        if (j >= n_eig_pad) break;
+        P* p = planes + (long)(b * S) * plane + (long)(2 * j) * (K / 2) + vc;
+        if (split) {
+          emit_split<P>(fv * x[r].x, fv * x[r].y, e[r][b], S, [&](int s, float fr, float fi) {
+            P* p0 = p + s * plane;
+            PlaneT<P>::put(p0, fr, fi);
+            PlaneT<P>::put(p0 + K / 2, -fi, fr);
+          });
+          continue;
+        }
+        long long yr, yi;
+        if (S <= PROD_DIGITS_MAX_S) {
+          yr = digits_y_prod(x[r].x, fv, e[r][b], S);
+          yi = digits_y_prod(x[r].y, fv, e[r][b], S);
+        } else {
+          yr = digits_y(fv * x[r].x, e[r][b], S);
+          yi = digits_y(fv * x[r].y, e[r][b], S);
+        }
+        emit_digits(yr, yi, S, [&](int s, float fr, float fi) {
           P* p0 = p + s * plane;
           PlaneT<P>::put(p0, fr, fi);
           PlaneT<P>::put(p0 + K / 2, -fi, fr);
         });
-        continue;
       }
-      long long yr, yi;
-      if (S <= PROD_DIGITS_MAX_S) {
-        yr = digits_y_prod(x.x, fv, e[b], S);
-        yi = digits_y_prod(x.y, fv, e[b], S);
-      } else {
-        yr = digits_y(fv * x.x, e[b], S);
-        yi = digits_y(fv * x.y, e[b], S);
-      }
-      emit_digits(yr, yi, S, [&](int s, float fr, float fi) {
-        P* p0 = p + s * plane;
-        PlaneT<P>::put(p0, fr, fi);
-        PlaneT<P>::put(p0 + K / 2, -fi, fr);
-      });
     }
   }
 }
@@ -1630,11 +1669,11 @@ rpa_status chis_t(Workspace& w, const cplx* mt, int n_eig, int n_vc, const doubl
     if (g >= 2) CK(cudaStreamWaitEvent(cut, w.ev_gemm[buf], 0));
     if (cut == st) w.hook(RPA_T_SLICE, 1);
     CK(cudaMemsetAsync(rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), cut));
-    chis_b_rowmax_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, cut>>>(
+    chis_b_rowmax_kernel<<<dim3((unsigned)cdiv(n_eig, RMR), cdiv(n_vc, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, n_vc, w.fweights + (size_t)k0 * n_vc, f + (size_t)k0 * n_vc,
         nb, rowmax, (int)e_pad);
     CK(cudaGetLastError());
-    chis_b_slice_kernel<P><<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
+    chis_b_slice_kernel<P><<<dim3((unsigned)cdiv(e_pad, RMR), cdiv(K / 2, CHUNK)), 256, 0, cut>>>(
         (const double2*)mt, n_eig, (int)e_pad, n_vc, K, f + (size_t)k0 * n_vc, nb, S, rowmax, pb,
         eb, (int)e_pad, w.split);
     CK(cudaGetLastError());
