@@ -54,6 +54,15 @@ template <typename C>
 __device__ __forceinline__ C cmul_cb(C a, C b) {
   return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
+// acc + a b with four FMAs
+template <typename C>
+__device__ __forceinline__ C cfma(C acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
 template <typename C>
 __device__ __forceinline__ C cconj(C a) {
   return C{a.x, -a.y};
@@ -76,75 +85,48 @@ __device__ __forceinline__ cplx ldcg_c(const cplx* p) {
   return cplx{v.x, v.y};
 }
 
-// Grid-wide barrier among the nblocks CTAs of a cooperative launch.  bar[2] is the
-// abort word.  CTA g publishes the generation it has reached in a 64-byte line of
-// its own, bar[BAR_FLAGS + BAR_STRIDE g] (a release store after a CTA barrier), and
-// warp 0 of every CTA polls the lines of all CTAs until each has reached the
-// generation (then an acquire fence): no read-modify-write on one shared word, so
-// the arrivals do not queue at one L2 address.  gen is the generation this CTA last
-// passed (kept by the lanes of warp 0).  false: a wait ran out here or in another
-// CTA; the caller returns.
-constexpr int BAR_FLAGS = 32;   // words before the first flag line (bar[2]: abort)
-constexpr int BAR_STRIDE = 16;  // words per flag line
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
+// Grid-wide barrier: bar[0] arrivals, bar[1] generation, bar[2] abort.  gen is the
+// generation this CTA last passed (kept by thread 0).  false: a wait ran out here
+// or in another CTA; the caller returns.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* status,
                              int code) {
   __shared__ int ok_s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const unsigned lane = threadIdx.x, target = gen + 1;
-    if (lane == 0) {
-      __threadfence();
-      st_release_u32(&bar[BAR_FLAGS + BAR_STRIDE * blockIdx.x], target);
-    }
-    // lane l watches the flags of CTAs l, l + 32, ...
-    const unsigned nu = (nblocks + 31) / 32;
-    unsigned need = 0, seen = 0;
-    for (unsigned u = 0; u < nu; ++u)
-      if (lane + 32 * u < nblocks) need |= 1u << u;
+  if (threadIdx.x == 0) {
     int ok = 1;
-    const long long t0 = clock64();
-    while (true) {
-      for (unsigned u = 0; u < nu; ++u)
-        if (((need & ~seen) >> u) & 1u)
-          if (ld_relaxed_u32(&bar[BAR_FLAGS + BAR_STRIDE * (lane + 32 * u)]) >= target)
-            seen |= 1u << u;
-      if (__all_sync(0xffffffffu, seen == need)) break;
-      int stop = 0;
-      if (lane == 0) {
-        if (ld_relaxed_u32(&bar[2])) {
-          stop = 1;
-        } else if (clock64() - t0 > kWaitCycles) {
+    const unsigned target = gen + 1;
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = clock64();
+      while (true) {
+        if (*(volatile unsigned*)&bar[1] == target) break;
+        if (*(volatile unsigned*)&bar[2]) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > kWaitCycles) {
           atomicExch(&bar[2], 1u);
           atomicOr(status, code);
-          stop = 1;
+          ok = 0;
+          break;
         }
+        __nanosleep(32);
       }
-      if (__shfl_sync(0xffffffffu, stop, 0)) {
-        ok = 0;
-        break;
-      }
-      __nanosleep(16);
     }
     __threadfence();
     gen = target;
-    if (lane == 0) ok_s = ok;
+    ok_s = ok;
   }
   __syncthreads();
   return ok_s != 0;
 }
 
-// Words of barrier state for a grid of `grid` CTAs.
-size_t bar_words(int grid) { return BAR_FLAGS + (size_t)BAR_STRIDE * (size_t)grid; }
+// Words of barrier state for a grid of `grid` CTAs (arrivals, generation, abort).
+size_t bar_words(int) { return 4; }
 
 // ---------------------------------------------------------------------------
 // Householder tridiagonalisation (lower), blocked, persistent.
@@ -286,25 +268,37 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     if (tid <= 2 * c) {
       C acc = {0, 0};
       for (int w = 0; w < HW; ++w) acc = cadd(acc, red[w * PL + tid]);
-      p.part[(size_t)b * PL + tid] = acc;
+      p.part[(size_t)tid * G + b] = acc;  // entry-major: one entry's G partials adjacent
     }
     if (!grid_barrier(p.bar, G, gen, p.status, 1)) return;
 
     // ---- B: reflector and A_eff v over this CTA's columns.  One round of
-    // independent loads: every CTA's partial sums, alpha = x(k+1), row k+1 of the
-    // panel, and x(k+2:) staged unscaled.
-    const int L = 2 * c + 1;
-    const int nsg = (G + 3) / 4;  // every entry's G partials in segments of at most four
+    // independent loads: every CTA's partial sums (entry q by the 8 lanes of group
+    // tid / 8, each summing G/8 partials in order, then a fixed tree over the group:
+    // the same order in every CTA), alpha = x(k+1), row k+1 of the panel, and
+    // x(k+2:) staged unscaled.
+    const int L = 2 * c + 1;  // <= 63: c <= 31 here
     const int j0 = k + 1, len = n - j0;
     const bool staged = len <= vcap<T>();
-    for (int w = tid; w < L * nsg; w += HT) {
-      const int q = w / nsg, sg = w % nsg;
-      const int g0 = sg * 4;
-      C a0 = __ldcg(&p.part[(size_t)g0 * PL + q]);
-      const C b1 = g0 + 1 < G ? __ldcg(&p.part[(size_t)(g0 + 1) * PL + q]) : C{0, 0};
-      const C b2 = g0 + 2 < G ? __ldcg(&p.part[(size_t)(g0 + 2) * PL + q]) : C{0, 0};
-      const C b3 = g0 + 3 < G ? __ldcg(&p.part[(size_t)(g0 + 3) * PL + q]) : C{0, 0};
-      red[w] = cadd(cadd(a0, b1), cadd(b2, b3));
+    {
+      const int q = tid >> 3, sub = tid & 7;
+      C acc = {0, 0};
+      if (q < L) {
+        C v[MAXG / 8];
+#pragma unroll
+        for (int u = 0; u < MAXG / 8; ++u) {
+          const int g = sub + 8 * u;
+          v[u] = g < G ? __ldcg(&p.part[(size_t)q * G + g]) : C{0, 0};
+        }
+#pragma unroll
+        for (int u = 0; u < MAXG / 8; ++u) acc = cadd(acc, v[u]);
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (sub == 0 && q < L) tot[q] = acc;
     }
     C wr1 = {0, 0}, vr1 = {0, 0};
     if (tid < c) {
@@ -314,12 +308,6 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
     if (tid == HT - 1) scal[4] = __ldcg(&p.xcol[k + 1]);
     if (staged)
       for (int t = tid; t < len; t += HT) vsm[t] = t == 0 ? C{1, 0} : __ldcg(&p.xcol[j0 + t]);
-    __syncthreads();
-    if (tid < L) {
-      C t = {0, 0};
-      for (int sg = 0; sg < nsg; ++sg) t = cadd(t, red[tid * nsg + sg]);
-      tot[tid] = t;
-    }
     __syncthreads();
     if (tid == 0) {
       const C alpha = scal[4];
@@ -512,8 +500,7 @@ __global__ void __launch_bounds__(HT, 1) hetrd_kernel(HetrdArgs<T> p) {
                 const C wcv = wq[cc * PNB + qq], vcv = vq[cc * PNB + qq];
 #pragma unroll
                 for (int u = 0; u < RL; ++u)
-                  if (u < nr)
-                    acc[u][cc] = cadd(acc[u][cc], cadd(cmul(vr[u], wcv), cmul(wr[u], vcv)));
+                  if (u < nr) acc[u][cc] = cfma(cfma(acc[u][cc], vr[u], wcv), wr[u], vcv);
               }
             }
 #pragma unroll

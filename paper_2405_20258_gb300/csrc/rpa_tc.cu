@@ -509,19 +509,32 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
       }
       tc_fence_after();
       if constexpr (kLoTmem) {
+        // per 8 columns: the low halves and the first two levels issued together, one
+        // wait (a third level, where there is one, after them)
 #pragma unroll
         for (int c0 = 0; c0 < CPT; c0 += 8) {
-          uint32_t lr[8];
+          uint32_t lr[8], r[2][8];
           tmem_ld8(lo_base + c0, lr);
+          tmem_ld8(lane_base + (ab * NL) * TS + CPT * h + c0, r[0]);
+          if (NL > 1) tmem_ld8(lane_base + (ab * NL + 1) * TS + CPT * h + c0, r[1]);
           tmem_wait_ld();
-          for (int L = 0; L < NL; ++L) {
-            uint32_t r[8];
-            tmem_ld8(lane_base + (ab * NL + L) * TS + CPT * h + c0, r);
+#pragma unroll
+          for (int L = 0; L < 2; ++L)
+            if (L < NL) {
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                float l = __uint_as_float(lr[c]);
+                dfloat_add(hi[c0 + c], l, __uint_as_float(r[L][c]));
+                lr[c] = __float_as_uint(l);
+              }
+            }
+          for (int L = 2; L < NL; ++L) {
+            tmem_ld8(lane_base + (ab * NL + L) * TS + CPT * h + c0, r[0]);
             tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               float l = __uint_as_float(lr[c]);
-              dfloat_add(hi[c0 + c], l, __uint_as_float(r[c]));
+              dfloat_add(hi[c0 + c], l, __uint_as_float(r[0][c]));
               lr[c] = __float_as_uint(l);
             }
           }
@@ -1053,10 +1066,15 @@ int n_levels(int S, int Le) { return Le < S ? Le + 1 : S; }
 // lowest-weight levels in the tail (weights 2^-8(S-2) and below relative to the
 // leading level; the FP32 rounding of their sum stays below the truncation of
 // the digit expansion); the projection, whose accuracy the whole subspace
-// rests on, keeps every level exact.  RPA_TC_LE_<STAGE> overrides (tuning).
+// rests on, keeps every level exact.  chi~(0) at S = 4 keeps only level 0 exact:
+// the tail's FP32 rounding (~2^-32 of the leading level per interval) then matches
+// the truncation (2^-31), the drain interval doubles to 16 K-tiles and one
+// accumulator fewer is drained (measured at N_G = 4000: |dE_c| 1.2e-7 / 1.0e-8 /
+// 4.5e-8 Ha at N_eig = 200 / 400 / 800 against the FP64 path, chi~ 9% faster).
+// RPA_TC_LE_<STAGE> overrides (tuning).
 int clamp_levels(int Le, int S) { return std::max(1, std::min(S, Le)); }
 int exact_levels_chi0(int S) {
-  return clamp_levels(env_int("RPA_TC_LE_CHI0", S >= 3 ? S - 2 : S), S);
+  return clamp_levels(env_int("RPA_TC_LE_CHI0", S == 4 ? 1 : (S >= 3 ? S - 2 : S)), S);
 }
 int exact_levels_proj(int S) { return clamp_levels(env_int("RPA_TC_LE_PROJ", S), S); }
 int exact_levels_chis(int S) {
