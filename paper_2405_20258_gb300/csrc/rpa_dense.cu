@@ -722,15 +722,15 @@ __global__ void __launch_bounds__(AQ_THREADS) apply_q_kernel(const typename CxT<
 // k = 1 .. M/2 - 1.  With m odd, the player paired with the padding index m takes
 // no rotation that round (its column still takes the other pairs' row rotations).
 // Per round:
-//   1. every CTA computes every pair's rotation from a = G_pp, c = G_qq,
-//      g = G_pq = |g| e^{i phi}, read from a buffer of their own (below):
-//      zeta = (c - a) / (2 |g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-//      cs = 1/sqrt(1 + t^2), sn = t cs; J = diag(1, e^{-i phi}) [[cs, sn], [-sn, cs]];
-//   2. the CTA owning pair k (k = b, b + G, ...) rotates its columns p, q of G and
-//      Y (G J, Y J), applies every pair's row rotation (J^H) to those two columns,
-//      zeroes G_pq, and writes the entries of its columns that the next round's
-//      rotations need into the other buffer (double-buffered by round);  barrier
-//   One grid barrier per round, and no CTA reads G while another rotates it.
+//   1. the CTA owning pair k (k = b, b + G, ...) computes its rotation from
+//      a = G_pp, c = G_qq, g = G_pq = |g| e^{i phi}: zeta = (c - a) / (2 |g|),
+//      t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), cs = 1/sqrt(1 + t^2),
+//      sn = t cs; J = diag(1, e^{-i phi}) [[cs, sn], [-sn, cs]];      barrier
+//   2. it rotates its columns p, q of G and Y (G J, Y J), then applies every
+//      pair's row rotation (J^H) to those two columns, and zeroes G_pq;  barrier
+//   (Every CTA computing every pair's rotation from double-buffered inputs, one
+//   barrier per round, measured slower: the rotations' FP64 square roots and
+//   divisions then run G times over.)
 // Rotations with |g| <= 1e-300 or |g| <= eps sqrt(|a c|) are skipped.  A sweep
 // is M - 1 rounds; sweeps stop when no pair of a sweep needed a rotation.
 // ---------------------------------------------------------------------------
@@ -754,7 +754,7 @@ struct JacArgs {
   cplx* g;
   int m;
   cplx* y;
-  double* prm;   // [2][M/2][4]: G_pp, G_qq, Re G_pq, Im G_pq of each pair of a round
+  double* prm;   // [M/2][4]: cs, sn, Re e^{-i phi}, Im e^{-i phi}
   double* part;  // [grid]: rotations needed in the sweep
   unsigned* bar;
   int* status;
@@ -773,33 +773,18 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
   // only rotations below kConverged the matrix it leaves is diagonal to ~kConverged^2
   double offmax = 0.0;
   constexpr double kConverged = 1e-8;
-  // the entries a rotation needs, round 0
-  for (int k = b + G * tid; k < np; k += G * JT) {
-    int pp, qq;
-    pair_of(M, 0, k, pp, qq);
-    if (qq >= m) continue;
-    const cplx gpq = p.g[(size_t)qq * m + pp];
-    double* o = p.prm + 4 * (size_t)k;
-    o[0] = p.g[(size_t)pp * m + pp].re;
-    o[1] = p.g[(size_t)qq * m + qq].re;
-    o[2] = gpq.re;
-    o[3] = gpq.im;
-  }
-  if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
-  int R = 0;  // rounds done: the inputs of round R are in prm[R & 1]
   for (int sweep = 0; sweep < p.max_sweeps; ++sweep) {
-    for (int r = 0; r < M - 1; ++r, ++R) {
-      const double* in = p.prm + (size_t)(R & 1) * 4 * np;
-      double* nx = p.prm + (size_t)((R + 1) & 1) * 4 * np;
-      // 1. rotation parameters of every pair, computed by every CTA (the same
-      //    arithmetic on the same entries, so the same values) into shared memory
-      for (int k = tid; k < np; k += JT) {
+    for (int r = 0; r < M - 1; ++r) {
+      // 1. rotation parameters of this CTA's pairs (the FP64 pipe is narrow: each pair's
+      //    are computed once, by its owner, and published)
+      for (int k = b + G * tid; k < np; k += G * JT) {
         int pp, qq;
         pair_of(M, r, k, pp, qq);
         double cs = 1.0, sn = 0.0, er = 1.0, ei = 0.0;
         if (qq < m) {
-          const double a = __ldcg(&in[4 * k]), c = __ldcg(&in[4 * k + 1]);
-          const cplx gpq = {__ldcg(&in[4 * k + 2]), __ldcg(&in[4 * k + 3])};
+          const double a = ldcg_c(&p.g[(size_t)pp * m + pp]).re;
+          const double c = ldcg_c(&p.g[(size_t)qq * m + qq]).re;
+          const cplx gpq = ldcg_c(&p.g[(size_t)qq * m + pp]);
           const double beta = hypot(gpq.re, gpq.im);
           const double ref = sqrt(fabs(a * c));
           if (beta > 1e-300 && beta > eps * ref) {
@@ -812,11 +797,14 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
             ei = -gpq.im / beta;
           }
         }
-        jsm[4 * k] = cs;
-        jsm[4 * k + 1] = sn;
-        jsm[4 * k + 2] = er;
-        jsm[4 * k + 3] = ei;
+        double* o = p.prm + 4 * (size_t)k;
+        o[0] = cs;
+        o[1] = sn;
+        o[2] = er;
+        o[3] = ei;
       }
+      if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
+      for (int e = tid; e < 4 * np; e += JT) jsm[e] = __ldcg(&p.prm[e]);
       __syncthreads();
       // 2. columns p, q of this CTA's pairs: G J and Y J, then J^H on those columns
       for (int k = b; k < np; k += G) {
@@ -863,34 +851,6 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
           p.g[(size_t)pp * m + qq] = cplx{0.0, 0.0};
           p.g[(size_t)pp * m + pp].im = 0.0;
           p.g[(size_t)qq * m + qq].im = 0.0;
-        }
-        __syncthreads();
-        // columns pp and qq are final for this round: their entries that the next
-        // round's rotations need (its diagonal entries, and G_p'q' from the column
-        // of the larger index q') go to the other buffer, so that no CTA reads G while
-        // another rotates it
-        if (tid < (idle ? 1 : 2)) {
-          const int cix = tid == 0 ? pp : qq;
-          const int rn = r + 1 < M - 1 ? r + 1 : 0;
-          int kn;
-          if (cix == M - 1 || cix == rn) {
-            kn = 0;
-          } else {
-            const int dd = ((cix - rn) % (M - 1) + (M - 1)) % (M - 1);
-            kn = dd < np ? dd : (M - 1) - dd;
-          }
-          int p2, q2;
-          pair_of(M, rn, kn, p2, q2);
-          if (q2 < m) {
-            if (cix == p2) {
-              nx[4 * kn] = p.g[(size_t)cix * m + cix].re;
-            } else {
-              const cplx gv = p.g[(size_t)cix * m + p2];
-              nx[4 * kn + 1] = p.g[(size_t)cix * m + cix].re;
-              nx[4 * kn + 2] = gv.re;
-              nx[4 * kn + 3] = gv.im;
-            }
-          }
         }
       }
       if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
