@@ -20,7 +20,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -579,26 +578,21 @@ def main():
 
         def stage(i, after=None):
             # H2D of step i's inputs into slot i % 2 (its previous user, step i-2, is done:
-            # plan.run returns only after the step's result reached the host).  Runs in a
-            # thread that keeps at most two 256 MB pieces queued on the copy engine, so that
-            # the small transfers of the running step (its eigensolver's) are not queued
-            # behind the whole 16 GB.
+            # plan.run returns only after the step's result reached the host), all pieces
+            # queued on the copy stream at once: the copy engine then runs at the link's
+            # rate (~210 GB/s) beside the running step, whose own small transfers wait at
+            # most one copy's length.  (Feeding the pieces from a host thread, two at a
+            # time, measured 30 GB/s: the thread could not keep the engine busy.)
             d = slots[i % 2]
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
-            rows = max(1, (256 << 20) // (host_A.shape[1] * host_A.element_size()))
+            rows = max(1, (1 << 30) // (host_A.shape[1] * host_A.element_size()))
             with torch.cuda.device(dev), torch.cuda.stream(copy_stream):
                 if after is not None:
                     copy_stream.wait_event(after)
                 c0.record(copy_stream)
-                inflight = []
                 for r0 in range(0, host_A.shape[0], rows):
                     d.m[r0:r0 + rows].copy_(host_A[r0:r0 + rows], non_blocking=True)
-                    ev = torch.cuda.Event()
-                    ev.record(copy_stream)
-                    inflight.append(ev)
-                    if len(inflight) > 2:
-                        inflight.pop(0).synchronize()
                 for d_, h_ in zip((d.qg2, d.e_v, d.e_c), host_small):
                     d_.copy_(h_, non_blocking=True)
                 c1.record(copy_stream)
@@ -610,13 +604,9 @@ def main():
             ecs_e = []
             for i in range(n):
                 stream.wait_event(ready[i % 2])
-                t = None
                 if i + 1 < n:
-                    t = threading.Thread(target=stage, args=(i + 1,))
-                    t.start()
+                    stage(i + 1)  # step i+1's inputs copy while step i computes
                 ecs_e.append(plan_e.run(i % 2))  # returns E_c to the host (8 bytes)
-                if t is not None:
-                    t.join()
             return ecs_e
 
         run_e2e(2)
