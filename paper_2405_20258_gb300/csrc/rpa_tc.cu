@@ -542,23 +542,16 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         }
         tmem_wait_st();
       } else {
-        // per 8 columns: two levels issued together before one wait, in level order
-        // (a column's accumulation order is that of one level at a time)
+        for (int L = 0; L < NL; ++L) {
+          const uint32_t ta = lane_base + (ab * NL + L) * TS + CPT * h;
 #pragma unroll
-        for (int c0 = 0; c0 < CPT; c0 += 8) {
-          for (int L0 = 0; L0 < NL; L0 += 2) {
-            uint32_t r[2][8];
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-              if (L0 + u < NL) tmem_ld8(lane_base + (ab * NL + L0 + u) * TS + CPT * h + c0, r[u]);
+          for (int c0 = 0; c0 < CPT; c0 += 8) {
+            uint32_t r[8];
+            tmem_ld8(ta + c0, r);
             tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-              if (L0 + u < NL) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                  dfloat_add(hi[c0 + c], lo[(c0 + c) % NLO], __uint_as_float(r[u][c]));
-              }
+            for (int c = 0; c < 8; ++c)
+              dfloat_add(hi[c0 + c], lo[(c0 + c) % NLO], __uint_as_float(r[c]));
           }
         }
       }
