@@ -759,10 +759,7 @@ struct JacArgs {
   unsigned* bar;
   int* status;
   int max_sweeps;
-  int pb;        // pairs whose two columns of G are staged in shared memory at a time
 };
-
-constexpr size_t JAC_SMEM = 200 * 1024;  // dynamic shared memory of the Jacobi kernel (at most)
 
 __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
   extern __shared__ double jsm[];  // [M/2][4]
@@ -809,94 +806,52 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(JacArgs p) {
       if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
       for (int e = tid; e < 4 * np; e += JT) jsm[e] = __ldcg(&p.prm[e]);
       __syncthreads();
-      // 2. this CTA's pairs, p.pb at a time (their columns of G staged in shared memory,
-      //    the pairs processed together): G J and Y J on the columns p, q, then every
-      //    pair's row rotation J^H on the staged columns, then G_pq zeroed and the
-      //    columns written back.  With m odd, the player paired with the padding index m
-      //    idles this round: its column takes no column rotation but still every pair's
-      //    row rotation.
-      cplx* stg = (cplx*)(jsm + 4 * np);  // [pb][2][m]
-      for (int k0 = b; k0 < np; k0 += G * p.pb) {
-        int nb = 0;  // pairs in this batch
-        while (nb < p.pb && k0 + G * nb < np) ++nb;
-        // stage the batch's columns
-        for (int e = tid; e < nb * 2 * m; e += JT) {
-          const int j = e / (2 * m), col = (e / m) & 1, i = e % m;
-          int pp, qq;
-          pair_of(M, r, k0 + G * j, pp, qq);
-          const int c = col == 0 ? pp : qq;
-          if (c < m) stg[e] = ldcg_c(&p.g[(size_t)c * m + i]);
-        }
-        __syncthreads();
-        // column rotations: G in shared memory, Y in place
-        for (int e = tid; e < nb * m; e += JT) {
-          const int j = e / m, i = e % m, k = k0 + G * j;
-          int pp, qq;
-          pair_of(M, r, k, pp, qq);
-          const double cs = jsm[4 * k], sn = jsm[4 * k + 1], er = jsm[4 * k + 2],
-                       ei = jsm[4 * k + 3];
-          if (qq >= m || (sn == 0.0 && er == 1.0 && ei == 0.0)) continue;
-          cplx* gp = stg + (size_t)(2 * j) * m;
-          cplx* gq = gp + m;
-          {
-            const cplx xp = gp[i], xq = gq[i];
-            // e^{-i phi} xq
-            const cplx eq = {er * xq.re - ei * xq.im, er * xq.im + ei * xq.re};
-            gp[i] = cplx{cs * xp.re - sn * eq.re, cs * xp.im - sn * eq.im};
-            gq[i] = cplx{sn * xp.re + cs * eq.re, sn * xp.im + cs * eq.im};
-          }
-          {
-            cplx* Y = p.y;
-            const cplx xp = ldcg_c(&Y[(size_t)pp * m + i]), xq = ldcg_c(&Y[(size_t)qq * m + i]);
-            const cplx eq = {er * xq.re - ei * xq.im, er * xq.im + ei * xq.re};
-            Y[(size_t)pp * m + i] = cplx{cs * xp.re - sn * eq.re, cs * xp.im - sn * eq.im};
-            Y[(size_t)qq * m + i] = cplx{sn * xp.re + cs * eq.re, sn * xp.im + cs * eq.im};
+      // 2. columns p, q of this CTA's pairs: G J and Y J, then J^H on those columns
+      for (int k = b; k < np; k += G) {
+        int pp, qq;
+        pair_of(M, r, k, pp, qq);
+        // with m odd, the player paired with the padding index m idles this round: its
+        // column takes no column rotation but still every pair's row rotation
+        const bool idle = qq >= m;
+        const double cs = jsm[4 * k], sn = jsm[4 * k + 1], er = jsm[4 * k + 2], ei = jsm[4 * k + 3];
+        if (idle || (sn == 0.0 && er == 1.0 && ei == 0.0)) {
+          // no rotation of these columns; their rows still rotate below
+        } else {
+          for (int mat = 0; mat < 2; ++mat) {
+            cplx* X = mat == 0 ? p.g : p.y;
+            for (int i = tid; i < m; i += JT) {
+              const cplx xp = ldcg_c(&X[(size_t)pp * m + i]), xq = ldcg_c(&X[(size_t)qq * m + i]);
+              // e^{-i phi} xq
+              const cplx eq = {er * xq.re - ei * xq.im, er * xq.im + ei * xq.re};
+              X[(size_t)pp * m + i] = cplx{cs * xp.re - sn * eq.re, cs * xp.im - sn * eq.im};
+              X[(size_t)qq * m + i] = cplx{sn * xp.re + cs * eq.re, sn * xp.im + cs * eq.im};
+            }
           }
         }
         __syncthreads();
-        // row rotations on the staged columns:
-        // (J^H X)[p'] = cs X[p'] - sn e^{i phi'} X[q'], (J^H X)[q'] = sn X[p'] + cs e^{i phi'} X[q']
-        for (int e = tid; e < nb * 2 * np; e += JT) {
-          const int sc = e / np, k2 = e % np, j = sc >> 1;
-          int pp, qq;
-          pair_of(M, r, k0 + G * j, pp, qq);
-          if ((sc & 1) && qq >= m) continue;  // the padding column
-          int p2, q2;
-          pair_of(M, r, k2, p2, q2);
-          if (q2 >= m) continue;
-          const double c2 = jsm[4 * k2], s2 = jsm[4 * k2 + 1], er2 = jsm[4 * k2 + 2],
-                       ei2 = -jsm[4 * k2 + 3];  // e^{+i phi'}
-          if (s2 == 0.0 && er2 == 1.0 && ei2 == 0.0) continue;
-          cplx* X = stg + (size_t)sc * m;
-          const cplx xp = X[p2], xq = X[q2];
-          const cplx eq = {er2 * xq.re - ei2 * xq.im, er2 * xq.im + ei2 * xq.re};
-          X[p2] = cplx{c2 * xp.re - s2 * eq.re, c2 * xp.im - s2 * eq.im};
-          X[q2] = cplx{s2 * xp.re + c2 * eq.re, s2 * xp.im + c2 * eq.im};
-        }
-        __syncthreads();
-        if (tid < nb) {
-          const int k = k0 + G * tid;
-          int pp, qq;
-          pair_of(M, r, k, pp, qq);
-          const double sn = jsm[4 * k + 1], er = jsm[4 * k + 2], ei = jsm[4 * k + 3];
-          if (qq < m && !(sn == 0.0 && er == 1.0 && ei == 0.0)) {
-            cplx* gp = stg + (size_t)(2 * tid) * m;
-            cplx* gq = gp + m;
-            gq[pp] = cplx{0.0, 0.0};
-            gp[qq] = cplx{0.0, 0.0};
-            gp[pp].im = 0.0;
-            gq[qq].im = 0.0;
+        // rows: (J^H X)[p'] = cs X[p'] - sn e^{i phi'} X[q'], (J^H X)[q'] = sn X[p'] + cs e^{i phi'} X[q']
+        for (int col = 0; col < (idle ? 1 : 2); ++col) {
+          cplx* X = p.g + (size_t)(col == 0 ? pp : qq) * m;
+          for (int k2 = tid; k2 < np; k2 += JT) {
+            int p2, q2;
+            pair_of(M, r, k2, p2, q2);
+            if (q2 >= m) continue;
+            const double c2 = jsm[4 * k2], s2 = jsm[4 * k2 + 1], er2 = jsm[4 * k2 + 2],
+                         ei2 = -jsm[4 * k2 + 3];  // e^{+i phi'}
+            if (s2 == 0.0 && er2 == 1.0 && ei2 == 0.0) continue;
+            const cplx xp = ldcg_c(&X[p2]), xq = ldcg_c(&X[q2]);
+            const cplx eq = {er2 * xq.re - ei2 * xq.im, er2 * xq.im + ei2 * xq.re};
+            X[p2] = cplx{c2 * xp.re - s2 * eq.re, c2 * xp.im - s2 * eq.im};
+            X[q2] = cplx{s2 * xp.re + c2 * eq.re, s2 * xp.im + c2 * eq.im};
           }
         }
         __syncthreads();
-        for (int e = tid; e < nb * 2 * m; e += JT) {
-          const int j = e / (2 * m), col = (e / m) & 1, i = e % m;
-          int pp, qq;
-          pair_of(M, r, k0 + G * j, pp, qq);
-          const int c = col == 0 ? pp : qq;
-          if (c < m) p.g[(size_t)c * m + i] = stg[e];
+        if (tid == 0 && !idle && !(sn == 0.0 && er == 1.0 && ei == 0.0)) {
+          p.g[(size_t)qq * m + pp] = cplx{0.0, 0.0};
+          p.g[(size_t)pp * m + qq] = cplx{0.0, 0.0};
+          p.g[(size_t)pp * m + pp].im = 0.0;
+          p.g[(size_t)qq * m + qq].im = 0.0;
         }
-        __syncthreads();
       }
       if (!grid_barrier(p.bar, G, gen, p.status, 2)) return;
     }
@@ -1097,7 +1052,7 @@ rpa_status coop_setup(int& sms, std::string& err) {
         cudaFuncSetAttribute(hetrd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hetrd_smem<double>()) != cudaSuccess ||
         cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)JAC_SMEM) != cudaSuccess) {
+                             (int)(sizeof(double) * 4 * (MAX_JM / 2))) != cudaSuccess) {
       (void)cudaGetLastError();
       err = "cudaFuncSetAttribute for the dense eigensolver kernels failed";
       L.sms = 0;
@@ -1277,14 +1232,10 @@ rpa_status jacobi(JacobiWork& w, cplx* g, int m, double* theta, cplx* y, cplx* y
     err = "Jacobi eigensolver: barrier reset failed";
     return RPA_ECUDA;
   }
-  // pairs per CTA per round, and how many of them fit in shared memory at a time
-  const int own = (np + G - 1) / G;
-  const size_t jsm_bytes = sizeof(double) * 4 * np, col_bytes = 2 * sizeof(cplx) * (size_t)m;
-  const int pb = (int)std::max<size_t>(1, std::min<size_t>(own, (JAC_SMEM - jsm_bytes) / col_bytes));
-  JacArgs args{g, m, ywork, w.prm, w.part, w.bar, w.status, 12, pb};
+  JacArgs args{g, m, ywork, w.prm, w.part, w.bar, w.status, 12};
   void* kargs[] = {&args};
   cudaError_t ce = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(G), dim3(JT),
-                                               kargs, jsm_bytes + (size_t)pb * col_bytes, st);
+                                               kargs, sizeof(double) * 4 * np, st);
   if (ce != cudaSuccess) {
     (void)cudaGetLastError();
     err = std::string("Jacobi launch: ") + cudaGetErrorString(ce);
