@@ -410,6 +410,9 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
         // first MMAs of an interval into a column range overwrite it: plane
         // s = 0 covers every exact level, and its first tail MMA the tail.
         const uint64_t bd0 = smem_desc(sB0 + bb * S * B_TILE);
+        // with a single tail level (S = Le + 1) the tail accumulator sits where level Le
+        // would, so every plane's pairs form one contiguous run
+        const int Lr = S - Le == 1 ? S : min(S, Le);
         bool tail_first = first;
         for (int s = 0; s < S; ++s, ++i) {
           if (pos == 0) {
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             tc_fence_after();
           }
           const uint64_t ad = smem_desc(sA0 + (h * G + pos) * A_TILE);
-          const int rows = s < Le ? BN * (min(S, Le) - s) : 0;
+          const int rows = s < Lr ? BN * (Lr - s) : 0;
           for (int c0 = 0; c0 < rows; c0 += MMA_N_MAX) {
             const int n = min(MMA_N_MAX, rows - c0);
             const uint32_t id = idesc_n(n, TF);
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
 #pragma unroll
             for (int kk = 1; kk < KSTEPS; ++kk) mma_issue<TF>(d, ad + 2 * kk, bd + 2 * kk, id, 1u);
           }
-          for (int t = max(0, Le - s); t <= S - 1 - s; ++t) {
+          for (int t = max(0, Lr - s); t <= S - 1 - s; ++t) {
             const uint32_t id = idesc_n(BN, TF);
             const uint64_t bd = bd0 + (uint64_t)((t * BN * ROWB) >> 4);
             const uint32_t d = acc_base + Le * TS;
@@ -1065,8 +1068,11 @@ int n_levels(int S, int Le) { return Le < S ? Le + 1 : S; }
 // Exact levels per stage: chi~(0) and chi_s with S >= 3 slices keep their two
 // lowest-weight levels in the tail (weights 2^-8(S-2) and below relative to the
 // leading level; the FP32 rounding of their sum stays below the truncation of
-// the digit expansion); the projection, whose accuracy the whole subspace
-// rests on, keeps every level exact.  chi~(0) at S = 4 keeps only level 0 exact:
+// the digit expansion); the projection, whose accuracy the whole subspace rests on
+// and whose sums cancel strongly, keeps all but its last level exact: the tail then
+// holds level S-1 alone (weight 2^-8(S-1)), whose FP32 rounding lies ~2^-9 below the
+// truncation, it occupies level S-1's own columns (the MMAs are those of all-exact
+// levels), and the drain interval grows from 2 to 3 K-tiles at S = 6.  chi~(0) at S = 4 keeps only level 0 exact:
 // the tail's FP32 rounding (~2^-32 of the leading level per interval) then matches
 // the truncation (2^-31), the drain interval doubles to 16 K-tiles and one
 // accumulator fewer is drained (measured at N_G = 4000: |dE_c| 1.2e-7 / 1.0e-8 /
@@ -1076,7 +1082,9 @@ int clamp_levels(int Le, int S) { return std::max(1, std::min(S, Le)); }
 int exact_levels_chi0(int S) {
   return clamp_levels(env_int("RPA_TC_LE_CHI0", S == 4 ? 1 : (S >= 3 ? S - 2 : S)), S);
 }
-int exact_levels_proj(int S) { return clamp_levels(env_int("RPA_TC_LE_PROJ", S), S); }
+int exact_levels_proj(int S) {
+  return clamp_levels(env_int("RPA_TC_LE_PROJ", S >= 2 ? S - 1 : S), S);
+}
 int exact_levels_chis(int S) {
   return clamp_levels(env_int("RPA_TC_LE_CHIS", S >= 3 ? S - 2 : S), S);
 }
