@@ -212,7 +212,7 @@ def reference_arm(args, w, rank, dist):
 # of 8,000 transitions and S = 4, from the ncu capture summarised in
 # profiles/slice_gemm_chi0_ng4000.md (a K = 32,000 launch scaled to K = 16,000). Valid for
 # the GEMM kernel as captured; set to None when the kernel changes until it is re-captured.
-CHI0_GEMM_TRAFFIC = {"workload": "qpoint-4000", "slices": 4, "bytes_per_launch": 3.58e9}
+CHI0_GEMM_TRAFFIC = {"workload": "qpoint-4000", "slices": 4, "bytes_per_launch": 3.52e9}
 
 
 def products(S):
