@@ -1378,7 +1378,8 @@ rpa_status alloc_workspace(Workspace& w, size_t max_g, size_t max_eig, size_t ma
   w.plane2_bytes = p2 * 2;
   w.exp_count = std::max({(size_t)g_pad, (size_t)vc_pad, (size_t)e_pad}) +
                 std::max((size_t)g_pad, (size_t)2 * grp * e_pad);
-  w.rowmax_count = std::max({(size_t)2 * g_pad, (size_t)vc_pad, (size_t)2 * grp * e_pad});
+  // chi_s: the A operand's row maxima (e_pad) beside the B operand's two groups
+  w.rowmax_count = std::max({(size_t)2 * g_pad, (size_t)vc_pad, (size_t)(2 * grp + 1) * e_pad});
   w.work_count = 1 << 20;
   w.fweight_count = max_freq * max_vc;
   auto al = [&](void** p, size_t bytes) {
@@ -1666,15 +1667,18 @@ rpa_status chis_t(Workspace& w, const cplx* mt, int n_eig, int n_vc, const doubl
   w.proj_a.valid = false;
   w.hook(RPA_T_SLICE, 1);
   if (join_side(w, st, err) != RPA_OK) return RPA_ECUDA;
+  float_up_kernel<<<std::min(cdiv((long)n_freq * n_vc, 256), 4096), 256, 0, st>>>(
+      f, (long)n_freq * n_vc, w.fweights);
+  CK(cudaGetLastError());
+  // the first frequency group's B planes are cut on the side stream while the A planes
+  // of M~ are cut here
+  if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
   CK(cudaMemsetAsync(w.rowmax, 0, e_pad * sizeof(unsigned long long), st));
   row_max_kernel<<<dim3((unsigned)n_eig, cdiv(n_vc, CHUNK)), 256, 0, st>>>(mt, RPA_C128, n_vc,
                                                                             n_eig, n_vc, w.rowmax);
   CK(cudaGetLastError());
   slice_rows_kernel<P><<<dim3((unsigned)e_pad, cdiv(K / 2, CHUNK)), 256, 0, st>>>(
       mt, RPA_C128, n_vc, n_eig, n_vc, (int)e_pad, K, S, w.rowmax, pa, ea, w.split);
-  CK(cudaGetLastError());
-  float_up_kernel<<<std::min(cdiv((long)n_freq * n_vc, 256), 4096), 256, 0, st>>>(
-      f, (long)n_freq * n_vc, w.fweights);
   CK(cudaGetLastError());
   if (launches) *launches += 3;
   w.hook(RPA_T_SLICE, 0);
@@ -1684,14 +1688,13 @@ rpa_status chis_t(Workspace& w, const cplx* mt, int n_eig, int n_vc, const doubl
   // B planes of frequency groups in two alternating buffers: group g + 1 is cut
   // on the side stream while group g is multiplied on `st`.
   const size_t buf_pairs = (size_t)grp * S * 2 * e_pad * (K / 2);  // BF16 pairs per buffer
-  if (side_fork(w, st, err) != RPA_OK) return RPA_ECUDA;
   cudaStream_t cut = w.chis_overlap ? w.side : st;
   int g = 0;
   for (int k0 = 0; k0 < n_freq; k0 += grp, ++g) {
     const int nb = std::min(grp, n_freq - k0), buf = g & 1;
     P* pb = (P*)w.planes + buf * buf_pairs;
     int* eb = w.exps + e_pad + (size_t)buf * grp * e_pad;
-    unsigned long long* rowmax = w.rowmax + (size_t)buf * grp * e_pad;
+    unsigned long long* rowmax = w.rowmax + e_pad + (size_t)buf * grp * e_pad;
     if (g >= 2) CK(cudaStreamWaitEvent(cut, w.ev_gemm[buf], 0));
     if (cut == st) w.hook(RPA_T_SLICE, 1);
     CK(cudaMemsetAsync(rowmax, 0, (size_t)nb * e_pad * sizeof(unsigned long long), cut));
