@@ -260,6 +260,24 @@ rpa_status rpa_trace_term_static(const void* mtilde, int n_eig, int n_v, int n_c
 rpa_status rpa_tridiagonalize(int n, int bits, void* a, void* d, void* e, void* stream);
 rpa_status rpa_hermitian_eig_jacobi(int m, void* g, double* theta, void* y, void* stream);
 
+/* Transition order of the mixed path's chi~(0) (allocates its scratch per call,
+ * synchronises `stream`).  The paper has no counterpart: this is the library's own
+ * arrangement of the transitions into the K-blocks of the digit-sliced chi~(0)
+ * contraction, each block with its own digit scale, so that a block holds
+ * transitions of similar weight f_vc(0) (Eq. chi0_partial_occs: f proportional to
+ * |w / Delta|).  order[pos] = the transitions vc < n by decreasing key
+ * |ow[vc] / delta[vc]| (0 where either is 0), equal keys by increasing vc: the
+ * permutation of a stable sort.  seg_bands > 0 (a q-point drawn in chunks of
+ * seg_bands valence bands): sorted within each segment of seg_bands bands of one
+ * k-point (the last of a k-point may be shorter), as indices local to the segment's
+ * first transition; n is then a multiple of n_v * n_c, transitions numbered
+ * (k, v, c) with c fastest.  delta, ow: device, n doubles; order: device, n ints.
+ * Errors: RPA_EINVAL (n < 1, n_v or n_c < 1, seg_bands outside 0..n_v, n not a
+ * multiple of n_v * n_c when seg_bands > 0, NULL pointer), RPA_ENOMEM, RPA_ECUDA;
+ * message in rpa_last_error(NULL). */
+rpa_status rpa_transition_order(int n, int n_v, int n_c, int seg_bands, const double* delta,
+                                const double* ow, int* order, void* stream);
+
 /* Library version string. */
 const char* rpa_version(void);
 

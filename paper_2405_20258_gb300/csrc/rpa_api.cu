@@ -53,7 +53,7 @@ struct rpa_plan_s {
   double *sv = nullptr, *delta = nullptr, *sf0 = nullptr, *w = nullptr, *ow = nullptr;
   double* fall = nullptr;  // [max_freq][max_vc] transition weights (mixed path's FP64 diagonal)
   int* order = nullptr;    // [max_vc] transitions sorted by sqrt f(0) (mixed path's chi~ blocks)
-  int order_iq = -1;       // q-point whose order `order` holds
+  void* order_scratch = nullptr;  // the device sort's items (order_items(max_vc) x 16 bytes)
   double *omega = nullptr, *weight = nullptr;  // [n_q][max_freq]
   double *lam_all = nullptr, *lam = nullptr, *trace = nullptr, *ec = nullptr, *logdet = nullptr;
   int* flags = nullptr;  // [0] bad-input bits, [1] numeric bits, [2] solver info
@@ -138,7 +138,7 @@ void free_plan(rpa_plan_t p) {
                   p->lam_all,
                   p->lam,  p->trace, p->ec,        p->logdet, p->flags, p->chi,   p->chi_work,
                   p->C,    p->B,     p->mt,        p->chis,  p->chis_work, p->gen_a, p->sol_dev,
-                  p->infos, p->fall, p->order, p->chol_inv};
+                  p->infos, p->fall, p->order, p->order_scratch, p->chol_inv};
   for (void* b : bufs)
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
@@ -308,53 +308,19 @@ rpa_status tc_status(rpa_plan_t p) {
   return fail(p, RPA_ETIMEOUT, "a tensor-core kernel gave up waiting (code %d)", code);
 }
 
-// Transitions of q-point iq ordered by decreasing f_vc(0) = 4 w/Delta (stable,
-// from the small band arrays copied to the host once per q-point): the K-blocks
-// of the tensor-core chi~(0) then group transitions of similar weight.
+// Transitions of q-point iq ordered by decreasing f_vc(0) = 4 w/Delta (the
+// permutation of a stable sort, sorted on the device from the scalars prepare()
+// left for iq): the K-blocks of the tensor-core chi~(0) then group transitions of
+// similar weight.  Recomputed on every call, since the caller may have copied a
+// new q-point's inputs into the same entry; nothing crosses the host link.
 rpa_status transition_order(rpa_plan_t p, int iq) {
-  if (p->order_iq == iq) return RPA_OK;
   const rpa_qpoint& q = p->q[iq];
-  const int n_k = q.n_k > 1 ? q.n_k : 1;
-  const long nv = (long)n_k * q.n_v, nc = (long)n_k * q.n_c, n = rpa::n_transitions(q);
-  std::vector<double> ev(nv), ec(nc), fv, fc, kw;
-  CU(p, cudaMemcpy(ev.data(), q.e_v, nv * sizeof(double), cudaMemcpyDeviceToHost));
-  CU(p, cudaMemcpy(ec.data(), q.e_c, nc * sizeof(double), cudaMemcpyDeviceToHost));
-  if (q.occ_v) {
-    fv.resize(nv);
-    CU(p, cudaMemcpy(fv.data(), q.occ_v, nv * sizeof(double), cudaMemcpyDeviceToHost));
-  }
-  if (q.occ_c) {
-    fc.resize(nc);
-    CU(p, cudaMemcpy(fc.data(), q.occ_c, nc * sizeof(double), cudaMemcpyDeviceToHost));
-  }
-  if (q.k_weight) {
-    kw.resize(n_k);
-    CU(p, cudaMemcpy(kw.data(), q.k_weight, n_k * sizeof(double), cudaMemcpyDeviceToHost));
-  }
-  std::vector<double> key(n);
-  for (long vc = 0; vc < n; ++vc) {
-    const long k = vc / ((long)q.n_v * q.n_c), r = vc % ((long)q.n_v * q.n_c);
-    const long v = k * q.n_v + r / q.n_c, c = k * q.n_c + r % q.n_c;
-    const double d = ec[c] - ev[v];
-    const double w = (kw.empty() ? 1.0 : kw[k]) * ((fv.empty() ? 1.0 : fv[v]) - (fc.empty() ? 0.0 : fc[c]));
-    key[vc] = (w != 0.0 && d != 0.0) ? std::fabs(w / d) : 0.0;
-  }
-  std::vector<int> idx(n);
-  for (long i = 0; i < n; ++i) idx[i] = (int)i;
-  if (!q.m && p->opt.vc_chunk > 0) {
-    // a q-point drawn in chunks: each chunk's rows sorted among themselves, as
-    // indices local to the chunk
-    for (const Chunk& c : chunks_of(q, p->opt.vc_chunk)) {
-      int* b = idx.data() + c.r0;
-      for (int i = 0; i < c.rows; ++i) b[i] = i;
-      const double* kb = key.data() + c.r0;
-      std::stable_sort(b, b + c.rows, [&](int x, int y) { return kb[x] > kb[y]; });
-    }
-  } else {
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key[a] > key[b]; });
-  }
-  CU(p, cudaMemcpy(p->order, idx.data(), n * sizeof(int), cudaMemcpyHostToDevice));
-  p->order_iq = iq;
+  if (p->scalars_iq != iq) return fail(p, RPA_ESTATE, "q-point %d: scalars not prepared", iq);
+  const int nvb = streamed(p, iq) ? chunk_bands(q, p->opt.vc_chunk) : 0;
+  int nl = 0;
+  CU(p, rpa::launch_transition_order(p->delta, p->ow, rpa::n_transitions(q), q.n_v, q.n_c, nvb,
+                                     p->order_scratch, p->order, p->st, &nl));
+  p->launches += nl;
   return RPA_OK;
 }
 
@@ -582,7 +548,8 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     p->tcw.split = split ? 1 : 0;
     p->tcw.tf32 = tf32 ? 1 : 0;
     if (tf32) p->tcw.slices.chi0 = p->tcw.slices.proj = p->tcw.slices.chis = 2;
-    if (dalloc(nullptr, &p->fall, F * V) != RPA_OK || dalloc(nullptr, &p->order, V) != RPA_OK) {
+    if (dalloc(nullptr, &p->fall, F * V) != RPA_OK || dalloc(nullptr, &p->order, V) != RPA_OK ||
+        dalloc(nullptr, (char**)&p->order_scratch, 16 * (size_t)rpa::order_items(V)) != RPA_OK) {
       free_plan(p);
       return RPA_ENOMEM;
     }

@@ -1,7 +1,8 @@
-// Building blocks of the subspace step (a3, Method: the N_eig eigenvectors of chi~(0))
-// exposed through the C ABI, so that each can be checked on its own: the Householder
-// tridiagonalisation that starts the eigensolver, and the Jacobi eigensolver of its
-// Rayleigh-Ritz step.  Both allocate their scratch per call and synchronise.
+// Building blocks exposed through the C ABI, so that each can be checked on its own:
+// the Householder tridiagonalisation that starts the subspace eigensolver (a3, Method:
+// the N_eig eigenvectors of chi~(0)), the Jacobi eigensolver of its Rayleigh-Ritz
+// step, and the transition order of the mixed path's chi~(0) K-blocks.  Each
+// allocates its scratch per call and synchronises.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -82,4 +83,25 @@ extern "C" rpa_status rpa_hermitian_eig_jacobi(int m, void* g, double* theta, vo
   cudaFree(ywork);
   jacobi_free(w);
   return s == RPA_OK ? RPA_OK : fail(s, err);
+}
+
+extern "C" rpa_status rpa_transition_order(int n, int n_v, int n_c, int seg_bands,
+                                           const double* delta, const double* ow, int* order,
+                                           void* stream) {
+  if (n < 1 || n_v < 1 || n_c < 1 || seg_bands < 0 || seg_bands > n_v || !delta || !ow ||
+      !order || (seg_bands > 0 && n % ((long)n_v * n_c) != 0))
+    return fail(RPA_EINVAL, "rpa_transition_order: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* items = nullptr;
+  if (cudaMalloc(&items, 16 * (size_t)rpa::order_items(n)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(RPA_ENOMEM, "rpa_transition_order: cudaMalloc failed");
+  }
+  cudaError_t e =
+      rpa::launch_transition_order(delta, ow, n, n_v, n_c, seg_bands, items, order, st, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(items);
+  if (e != cudaSuccess)
+    return fail(RPA_ECUDA, std::string("rpa_transition_order: ") + cudaGetErrorString(e));
+  return RPA_OK;
 }

@@ -81,6 +81,18 @@ __global__ void to_c128_kernel(const float2* v32, long n, int cols, cplx* x) {
 
 // T in FP64 (an exact promotion of the FP32 reduction) and its squared
 // off-diagonal in FP64 and in FP32
+// A few host integers written to the device as kernel arguments (4 KB at most per
+// launch), not by a host-to-device copy: such a copy queues on the copy engine
+// behind whatever large input copy another stream has in flight.
+struct IntBatch {
+  int off, cnt;
+  int v[1000];
+};
+
+__global__ void put_ints_kernel(IntBatch b, int* dst) {
+  for (int i = threadIdx.x; i < b.cnt; i += blockDim.x) dst[b.off + i] = b.v[i];
+}
+
 __global__ void promote_tri_kernel(const float* d32, const float* e32, int n, double* d,
                                    double* e, double* e2, float* e2f) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -527,7 +539,14 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
     err = "eigensolver: a cluster of " + std::to_string(widest) + " eigenvalues";
     return RPA_ENUMERIC;
   }
-  CU_E(cudaMemcpyAsync(first, fh.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int o = 0; o <= nc; o += 1000) {
+    IntBatch b;
+    b.off = o;
+    b.cnt = std::min(1000, nc + 1 - o);
+    std::copy(fh.begin() + o, fh.begin() + o + b.cnt, b.v);
+    put_ints_kernel<<<1, 256, 0, st>>>(b, first);
+    nl += 1;
+  }
   const char* ib_env = getenv("RPA_EIG_INVIT_BLOCK");
   const int ib = std::max(1, std::min(256, ib_env ? atoi(ib_env) : 32));
   if (mode == 2)

@@ -53,6 +53,15 @@ cudaError_t launch_mirror_hermitian(cplx* m, int n, int batch, cudaStream_t st);
 // bad |= 1 (|q+G|^2), 2 (transition energy), 4 (pair weight sign), 8 (slab kernel).
 cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delta, double* ow,
                                    double* sf0, int* bad, cudaStream_t st);
+// Transition order of the tensor-core chi~(0) K-blocks: order[pos] = the transitions
+// by decreasing |ow| / |delta| (0 where either is 0), equal keys by index, on the
+// device (bitonic sort).  nvb > 0: sorted within segments of nvb valence bands of one
+// k-point (the chunks of a streamed q-point), as indices local to the segment.
+// items: order_items(n) 16-byte items of scratch.  *launches += the kernels launched.
+long order_items(long n);
+cudaError_t launch_transition_order(const double* delta, const double* ow, long n, int n_v,
+                                    int n_c, int nvb, void* items, int* order, cudaStream_t st,
+                                    int* launches);
 cudaError_t launch_freq_grid(int n_freq, double s, double* omega, double* weight,
                              cudaStream_t st);
 // C = conj(U) in canonical gauge; B = sv * C.  U column-major [n_g x n_eig] (ld = ldu).

@@ -317,12 +317,145 @@ inline int grid_for(long n, int bs) {
   return (int)(b < 152L * 32 ? (b > 0 ? b : 1) : 152L * 32);
 }
 
+
+// ---- transition order of the tensor-core chi~(0) K-blocks --------------------
+// Transitions by decreasing weight |f_vc| / Delta_vc, equal weights by index (the
+// permutation of a stable sort), within segments of consecutive transitions when a
+// q-point is drawn in chunks of valence bands.  Items (segment, key bits, index) are
+// sorted ascending by a bitonic network: a non-negative double's bit pattern orders
+// like its value, so its complement orders by decreasing weight.  Padding items
+// carry the largest segment and sort last.
+struct OrderItem {
+  unsigned long long kb;
+  unsigned seg, idx;
+};
+
+__device__ __forceinline__ bool item_less(const OrderItem& a, const OrderItem& b) {
+  if (a.seg != b.seg) return a.seg < b.seg;
+  if (a.kb != b.kb) return a.kb < b.kb;
+  return a.idx < b.idx;
+}
+
+// Compare-exchange of items i < l of stage k: ascending where bit k of i is clear.
+__device__ __forceinline__ void order_cx(OrderItem& a, OrderItem& b, bool asc) {
+  if (asc ? item_less(b, a) : item_less(a, b)) {
+    const OrderItem t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// nvb > 0: segments of nvb valence bands (the chunks of a streamed q-point).
+__global__ void order_keys_kernel(const double* delta, const double* ow, long n, int n_v,
+                                  int n_c, int nvb, long npad, OrderItem* it) {
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < npad; i += stride) {
+    OrderItem x;
+    x.idx = (unsigned)i;
+    if (i < n) {
+      const double d = delta[i], w = ow[i];
+      const double key = (w != 0.0 && d != 0.0) ? fabs(w / d) : 0.0;
+      x.kb = ~(unsigned long long)__double_as_longlong(key);
+      x.seg = 0;
+      if (nvb > 0) {
+        const long per_k = (long)n_v * n_c, k = i / per_k;
+        const int vb = (int)((i % per_k) / n_c);
+        x.seg = (unsigned)(k * ((n_v + nvb - 1) / nvb) + vb / nvb);
+      }
+    } else {
+      x.kb = ~0ull;
+      x.seg = 0xffffffffu;
+    }
+    it[i] = x;
+  }
+}
+
+// One tile of kOrderTile items per block in shared memory.  kk == 0: the stages
+// k = 2 .. kOrderTile (each tile sorted, in the direction stage kOrderTile gives it);
+// kk > kOrderTile: the strides kOrderTile/2 .. 1 of stage kk.
+constexpr int kOrderTile = 2048;
+
+__global__ void __launch_bounds__(kOrderTile / 2) order_tile_kernel(OrderItem* it, long kk) {
+  __shared__ OrderItem s[kOrderTile];
+  const long base = (long)blockIdx.x * kOrderTile;
+  const int t = threadIdx.x, h = kOrderTile / 2;
+  s[t] = it[base + t];
+  s[t + h] = it[base + t + h];
+  __syncthreads();
+  const long k0 = kk ? kk : 2, k1 = kk ? kk : kOrderTile;
+  for (long k = k0; k <= k1; k <<= 1)
+    for (int j = (int)(k / 2 < h ? k / 2 : h); j > 0; j >>= 1) {
+      const int i = 2 * j * (t / j) + t % j;
+      order_cx(s[i], s[i + j], ((base + i) & k) == 0);
+      __syncthreads();
+    }
+  it[base + t] = s[t];
+  it[base + t + h] = s[t + h];
+}
+
+// Stride j >= kOrderTile of stage k, one compare-exchange per thread.
+__global__ void order_merge_kernel(OrderItem* it, long pairs, long k, long j) {
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < pairs; t += stride) {
+    const long i = 2 * j * (t / j) + t % j;
+    OrderItem a = it[i], b = it[i + j];
+    const unsigned a0 = a.idx;
+    order_cx(a, b, (i & k) == 0);
+    if (a.idx != a0) {
+      it[i] = a;
+      it[i + j] = b;
+    }
+  }
+}
+
+// order[pos] = transition index, local to its segment's first transition.
+__global__ void order_out_kernel(const OrderItem* it, long n, int n_v, int n_c, int nvb,
+                                 int* order) {
+  const long stride = (long)gridDim.x * blockDim.x;
+  const unsigned nchk = nvb > 0 ? (unsigned)((n_v + nvb - 1) / nvb) : 1u;
+  for (long pos = blockIdx.x * (long)blockDim.x + threadIdx.x; pos < n; pos += stride) {
+    const OrderItem x = it[pos];
+    long r0 = 0;
+    if (nvb > 0) r0 = ((long)(x.seg / nchk) * n_v + (long)(x.seg % nchk) * nvb) * n_c;
+    order[pos] = (int)((long)x.idx - r0);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delta, double* ow,
                                    double* sf0, int* bad, cudaStream_t st) {
   long n = q.n_g + n_transitions(q);
   prepare_kernel<<<grid_for(n, 256), 256, 0, st>>>(q, sv, delta, ow, sf0, bad);
+  return cudaGetLastError();
+}
+
+long order_items(long n) {
+  long npad = kOrderTile;
+  while (npad < n) npad <<= 1;
+  return npad;
+}
+
+cudaError_t launch_transition_order(const double* delta, const double* ow, long n, int n_v,
+                                    int n_c, int nvb, void* items, int* order, cudaStream_t st,
+                                    int* launches) {
+  if (n <= 0) return cudaSuccess;
+  const long npad = order_items(n);
+  OrderItem* it = (OrderItem*)items;
+  order_keys_kernel<<<grid_for(npad, 256), 256, 0, st>>>(delta, ow, n, n_v, n_c, nvb, npad, it);
+  const unsigned tiles = (unsigned)(npad / kOrderTile);
+  order_tile_kernel<<<tiles, kOrderTile / 2, 0, st>>>(it, 0);
+  int nl = 2;
+  for (long k = 2L * kOrderTile; k <= npad; k <<= 1) {
+    for (long j = k / 2; j >= kOrderTile; j >>= 1) {
+      order_merge_kernel<<<grid_for(npad / 2, 256), 256, 0, st>>>(it, npad / 2, k, j);
+      ++nl;
+    }
+    order_tile_kernel<<<tiles, kOrderTile / 2, 0, st>>>(it, k);
+    ++nl;
+  }
+  order_out_kernel<<<grid_for(n, 256), 256, 0, st>>>(it, n, n_v, n_c, nvb, order);
+  if (launches) *launches += nl + 1;
   return cudaGetLastError();
 }
 

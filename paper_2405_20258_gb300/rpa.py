@@ -24,7 +24,8 @@ RPA_COULOMB_BARE, RPA_COULOMB_SLAB = 0, 1
 EXPORTED = ("rpa_plan_create", "rpa_plan_destroy", "rpa_last_error", "rpa_status_string",
             "rpa_chi0_static", "rpa_subspace_basis", "rpa_chi_freq", "rpa_ecorr",
             "rpa_plan_frequencies", "rpa_generate_m", "rpa_version", "rpa_plan_timings",
-            "rpa_trace_term_static", "rpa_tridiagonalize", "rpa_hermitian_eig_jacobi")
+            "rpa_trace_term_static", "rpa_tridiagonalize", "rpa_hermitian_eig_jacobi",
+            "rpa_transition_order")
 STATIC_TRACE_MAX_VC = 524288
 TIMERS = ("chi0", "eig0", "proj", "chis", "trace", "eigs", "energy", "other", "slice")
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
         "rpa_trace_term_static": ([vp, i, i, i, vp, vp, vp, i, d, vp, vp], i),
         "rpa_tridiagonalize": ([i, i, vp, vp, vp, vp], i),
         "rpa_hermitian_eig_jacobi": ([i, vp, vp, vp, vp], i),
+        "rpa_transition_order": ([i, i, i, i, vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -306,6 +308,15 @@ def rpa_hermitian_eig_jacobi(g, theta, y, stream=None):
     the column-major eigenvectors y (m x m complex128)."""
     _check(load().rpa_hermitian_eig_jacobi(int(g.shape[0]), _ptr(g), _ptr(theta), _ptr(y),
                                            _stream(stream)))
+
+
+def rpa_transition_order(delta, ow, order, n_v, n_c, seg_bands=0, stream=None):
+    """Transition order of the mixed path's chi~(0) K-blocks into the int32 device
+    tensor order: the transitions by decreasing |ow / delta| (0 where either is 0),
+    equal keys by index; seg_bands > 0 sorts within segments of that many valence
+    bands of one k-point, as segment-local indices.  delta, ow: float64 device."""
+    _check(load().rpa_transition_order(int(delta.numel()), int(n_v), int(n_c), int(seg_bands),
+                                       _ptr(delta), _ptr(ow), _ptr(order), _stream(stream)))
 
 
 def rpa_version():

@@ -72,3 +72,36 @@ def test_jacobi_eigenpairs(m, kind):
     assert err_lam < 1e-13
     assert orth < max(1e-13, 5e-16 * m)
     assert resid < 1e-13
+
+
+def stable_order(delta, ow, n_v, n_c, seg_bands):
+    """The permutation the K-blocks of the mixed chi~(0) take: numpy's stable argsort
+    of the negated keys, per segment of seg_bands valence bands when seg_bands > 0."""
+    key = np.where((ow != 0) & (delta != 0), np.abs(ow / np.where(delta != 0, delta, 1.0)), 0.0)
+    if seg_bands == 0:
+        return np.argsort(-key, kind="stable")
+    out = np.empty(key.size, dtype=np.int64)
+    for k in range(key.size // (n_v * n_c)):
+        for v0 in range(0, n_v, seg_bands):
+            r0 = (k * n_v + v0) * n_c
+            rows = min(seg_bands, n_v - v0) * n_c
+            out[r0:r0 + rows] = np.argsort(-key[r0:r0 + rows], kind="stable")
+    return out
+
+
+@pytest.mark.parametrize("n_k,n_v,n_c,seg", [(1, 1, 1, 0), (1, 1, 2047, 0), (1, 2, 1024, 0),
+                                             (1, 3, 683, 0), (1, 40, 2500, 0), (1, 128, 2000, 0),
+                                             (2, 5, 333, 2), (3, 9, 250, 4), (1, 64, 4096, 5)])
+def test_transition_order_is_a_stable_sort(n_k, n_v, n_c, seg):
+    import torch
+    rng = np.random.default_rng(7 + n_v * n_c + seg)
+    n = n_k * n_v * n_c
+    delta = rng.uniform(0.05, 3.0, n)
+    delta[rng.random(n) < 0.1] = 1.0
+    ow = rng.choice([0.0, 0.5, 1.0, 2.0], size=n) * np.where(rng.random(n) < 0.5, 1.0,
+                                                             rng.uniform(0.9, 1.1, n))
+    order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    rpa.rpa_transition_order(torch.tensor(delta, device="cuda"), torch.tensor(ow, device="cuda"),
+                             order, n_v, n_c, seg)
+    got = order.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, stable_order(delta, ow, n_v, n_c, seg))
