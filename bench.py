@@ -14,6 +14,7 @@ Multi-GPU (torchrun): every rank runs its own q-point; no data-path collective.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import math
 import os
@@ -580,13 +581,13 @@ def main():
             # H2D of step i's inputs into slot i % 2 (its previous user, step i-2, is done:
             # plan.run returns only after the step's result reached the host), all pieces
             # queued on the copy stream at once: the copy engine then runs at the link's
-            # rate (~210 GB/s) beside the running step, whose own small transfers wait at
-            # most one copy's length.  (Feeding the pieces from a host thread, two at a
-            # time, measured 30 GB/s: the thread could not keep the engine busy.)
+            # rate beside the running step, whose own small device-to-host reads wait at
+            # most one piece's length (64 MB: 0.3 ms at 210 GB/s, 2 ms at 35 GB/s, the two
+            # rates seen on different boxes)
             d = slots[i % 2]
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
-            rows = max(1, (1 << 30) // (host_A.shape[1] * host_A.element_size()))
+            rows = max(1, (64 << 20) // (host_A.shape[1] * host_A.element_size()))
             with torch.cuda.device(dev), torch.cuda.stream(copy_stream):
                 if after is not None:
                     copy_stream.wait_event(after)
@@ -599,6 +600,14 @@ def main():
                 ready[i % 2].record(copy_stream)
             h2d_ev.append((c0, c1))
 
+        host_ms = collections.defaultdict(float)
+
+        def timed(name, fn, *a):
+            t0 = time.perf_counter()
+            r = fn(*a)
+            host_ms[name] += (time.perf_counter() - t0) * 1e3
+            return r
+
         def run_e2e(n, after=None):
             stage(0, after)
             ecs_e = []
@@ -609,18 +618,19 @@ def main():
                 # step: no stage after that puts a host-to-device copy on the copy engine
                 # (the transition sort runs on the device, the eigensolver's cluster starts
                 # reach it as kernel arguments), so none waits behind the 16 GB copy
-                plan_e.chi0_static(i % 2)
+                timed("chi0_static", plan_e.chi0_static, i % 2)
                 if i + 1 < n:
-                    stage(i + 1)
-                plan_e.subspace_basis(i % 2)
-                plan_e.chi_freq(i % 2)
-                ecs_e.append(plan_e.ecorr(i % 2))  # E_c to the host (8 bytes)
+                    timed("stage", stage, i + 1)
+                timed("subspace_basis", plan_e.subspace_basis, i % 2)
+                timed("chi_freq", plan_e.chi_freq, i % 2)
+                ecs_e.append(timed("ecorr", plan_e.ecorr, i % 2))  # E_c to the host (8 bytes)
             return ecs_e
 
         run_e2e(2)
         torch.cuda.synchronize()
         plan_e.timings()
         h2d_ev.clear()
+        host_ms.clear()
         barrier(dist)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -630,6 +640,7 @@ def main():
         torch.cuda.synchronize()
         barrier(dist)
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        e2e_stage_ms, _ = plan_e.timings()
         h2d_ms = [a.elapsed_time(b) for a, b in h2d_ev]
         e2e = {"value": world * args.steps / t_e2e, "unit": "q-points/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
@@ -637,7 +648,9 @@ def main():
                "h2d_overlap": "step i+1's inputs are copied during step i (two input slots)",
                "host_buffers": "pinned, allocated by a thread on the GPU's NUMA node" if near
                else "pinned",
-               "ec_spread": max(ecs_e2e) - min(ecs_e2e)}
+               "ec_spread": max(ecs_e2e) - min(ecs_e2e),
+               "stage_ms_per_step": {k: v / args.steps for k, v in e2e_stage_ms.items()},
+               "host_ms_per_call": {k: v / args.steps for k, v in host_ms.items()}}
         plan_e.close()
         del host_A, dq2, slots
 

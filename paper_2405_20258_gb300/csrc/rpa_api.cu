@@ -69,6 +69,7 @@ struct rpa_plan_s {
   bool batched_eig = false;   // cusolverDnXsyevBatched usable for the chi_s eigenvalues
   int* infos = nullptr;       // [max_freq] solver info of the batched solve
   rpa::tc::Workspace tcw;     // tensor-core path workspace
+  rpa::HostReader reader;     // small host reads outside the copy engines
   rpa::eig::Refine refine;    // the library's own eigensolver of chi~ (rpa_eig.cu)
   bool refine_ready = false;
   // stage timers (CUDA events on the plan stream) and the library's launch count
@@ -143,6 +144,7 @@ void free_plan(rpa_plan_t p) {
     if (b) cudaFree(b);
   rpa::tc::free_workspace(p->tcw);
   p->refine.release();
+  rpa::reader_free(p->reader);
   if (p->sol_host) free(p->sol_host);
   if (p->params) cusolverDnDestroyParams(p->params);
   if (p->sol) cusolverDnDestroy(p->sol);
@@ -301,8 +303,8 @@ rpa_status draw_chunk(rpa_plan_t p, int iq, const Chunk& c, const void** a, int*
 rpa_status tc_status(rpa_plan_t p) {
   if (!p->tcw.status) return RPA_OK;
   int code = 0;
-  CU(p, cudaMemcpyAsync(&code, p->tcw.status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
-  CU(p, cudaStreamSynchronize(p->st));
+  const rpa::ReadPiece rp = {p->tcw.status, &code, sizeof(int)};
+  CU(p, rpa::read_to_host(p->reader, &rp, 1, p->st));
   if (code == 0) return RPA_OK;
   CU(p, cudaMemsetAsync(p->tcw.status, 0, sizeof(int), p->st));
   return fail(p, RPA_ETIMEOUT, "a tensor-core kernel gave up waiting (code %d)", code);
@@ -334,8 +336,8 @@ rpa_status prepare(rpa_plan_t p, int iq) {
     p->launches += 1;
   }
   int h = 0;
-  CU(p, cudaMemcpyAsync(&h, p->flags, sizeof(int), cudaMemcpyDeviceToHost, p->st));
-  CU(p, cudaStreamSynchronize(p->st));
+  const rpa::ReadPiece rp = {p->flags, &h, sizeof(int)};
+  CU(p, rpa::read_to_host(p->reader, &rp, 1, p->st));
   if (h & 1) return fail(p, RPA_EINVAL, "q-point %d: |q+G|^2 must be finite and > 0", iq);
   if (h & 2) return fail(p, RPA_EINVAL, "q-point %d: e_c[c] - e_v[v] must be finite", iq);
   if (h & 4)
@@ -555,6 +557,11 @@ rpa_status rpa_plan_create(rpa_plan_t* out, const rpa_qpoint* q, int n_q, const 
     }
     p->tcw.hook.ctx = p;
     p->tcw.hook.mark = mark_event;
+  }
+  if (rpa::reader_alloc(p->reader, 4096) != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_plan(p);
+    return fail(nullptr, RPA_ENOMEM, "mapped host buffer of 4 KB");
   }
   if (cusolverDnCreate(&p->sol) != CUSOLVER_STATUS_SUCCESS ||
       cusolverDnCreateParams(&p->params) != CUSOLVER_STATUS_SUCCESS) {
@@ -926,9 +933,10 @@ static rpa_status energy_one(rpa_plan_t p, int iq, double* ec_host, double* lam_
                             cudaMemcpyDeviceToDevice, p->st));
   }
   int fl[4];
-  CU(p, cudaMemcpyAsync(fl, p->flags, sizeof fl, cudaMemcpyDeviceToHost, p->st));
-  CU(p, cudaMemcpyAsync(ec_host, p->ec, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-  CU(p, cudaStreamSynchronize(p->st));
+  {
+    const rpa::ReadPiece rp[2] = {{p->flags, fl, sizeof fl}, {p->ec, ec_host, sizeof(double)}};
+    CU(p, rpa::read_to_host(p->reader, rp, 2, p->st));
+  }
   rpa_status ts = tc_status(p);
   if (ts != RPA_OK) return ts;
   if (p->opt.energy_route == RPA_ROUTE_EIG) {

@@ -84,6 +84,8 @@ __global__ void to_c128_kernel(const float2* v32, long n, int cols, cplx* x) {
 // A few host integers written to the device as kernel arguments (4 KB at most per
 // launch), not by a host-to-device copy: such a copy queues on the copy engine
 // behind whatever large input copy another stream has in flight.
+constexpr long kInvitSmemMax = 227L * 1024;  // dynamic shared memory a block may opt into
+
 struct IntBatch {
   int off, cnt;
   int v[1000];
@@ -207,6 +209,25 @@ __global__ void invit32_kernel(const float* d, const float* e, int n, const doub
   tri::cluster_vectors<float>(d, e, n, w, first[c], first[c + 1], tiny, z, ldz, LF{b, nc},
                               LF{b + plane, nc}, LF{b + 2 * plane, nc}, LF{b + 3 * plane, nc},
                               LF{b + 4 * plane, nc}, LF{b + 5 * plane, nc});
+}
+
+// The same with each thread's six lanes in shared memory (`per` clusters a block, one
+// warp, lanes interleaved with stride `per`): the factor and the solves walk a chain
+// of dependent steps over n rows, so a step's latency sets the time, and a load from
+// shared memory returns in a few tens of cycles where one that follows the thread's
+// own global store to the same lanes goes to L2.  Same arithmetic, same results.
+__global__ void invit32_smem_kernel(const float* d, const float* e, int n, const double* w,
+                                    const int* first, int nc, float tiny, double* z, int ldz,
+                                    int per) {
+  extern __shared__ float lane_sm[];
+  const int c = blockIdx.x * per + threadIdx.x;
+  if (threadIdx.x >= per || c >= nc) return;
+  const long plane = (long)n * per;
+  float* b = lane_sm + threadIdx.x;
+  using LF = tri::LaneT<float>;
+  tri::cluster_vectors<float>(d, e, n, w, first[c], first[c + 1], tiny, z, ldz, LF{b, per},
+                              LF{b + plane, per}, LF{b + 2 * plane, per}, LF{b + 3 * plane, per},
+                              LF{b + 4 * plane, per}, LF{b + 5 * plane, per});
 }
 
 // c[i + n j] = z[i k + j] as complex64 (column-major n x k from row-major FP64)
@@ -411,6 +432,12 @@ rpa_status Refine::alloc(int n_max, int mp_max, bool with32, std::string& err) {
   }
   if (s == RPA_OK) s = dense::hetrd_alloc(hw64, n_max, sizeof(cplx), err);
   if (s == RPA_OK) s = dense::jacobi_alloc(jw, mp_max, err);
+  // host reads of the eigenvalues of T (m' + 1), the Ritz values and a few flags
+  if (s == RPA_OK && reader_alloc(reader, (mp + 2) * sizeof(double) + 64) != cudaSuccess) {
+    (void)cudaGetLastError();
+    err = "eigensolver: mapped host buffer";
+    s = RPA_ENOMEM;
+  }
   if (s != RPA_OK) {
     release();
     return s;
@@ -428,6 +455,7 @@ void Refine::release() {
   dense::hetrd_free(hw64);
   dense::jacobi_free(jw);
   if (has_tw) tc::free_workspace(tw);
+  reader_free(reader);
   *this = Refine{};
 }
 
@@ -496,11 +524,12 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   std::vector<double> w(nval);
   unsigned long long mx_bits = 0;
   int hst = 0;
-  CU_E(cudaMemcpyAsync(w.data(), wt, nval * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CU_E(cudaMemcpyAsync(&mx_bits, absmax, sizeof mx_bits, cudaMemcpyDeviceToHost, st));
-  CU_E(cudaMemcpyAsync(&hst, s32 ? hw32.status : hw64.status, sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
-  CU_E(cudaStreamSynchronize(st));
+  {
+    const ReadPiece rp[3] = {{wt, w.data(), nval * sizeof(double)},
+                             {absmax, &mx_bits, sizeof mx_bits},
+                             {s32 ? hw32.status : hw64.status, &hst, sizeof(int)}};
+    CU_E(read_to_host(reader, rp, 3, st));
+  }
   if (launches) *launches += nl;
   nl = 0;
   if (hst != 0) {
@@ -549,7 +578,19 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
   }
   const char* ib_env = getenv("RPA_EIG_INVIT_BLOCK");
   const int ib = std::max(1, std::min(256, ib_env ? atoi(ib_env) : 32));
-  if (mode == 2)
+  // shared-memory lanes: two clusters a block where 6 n floats each fit twice in 227 KB,
+  // one where they fit once (RPA_EIG_INVIT_SMEM=0: lanes in global memory)
+  const char* sm_env = getenv("RPA_EIG_INVIT_SMEM");
+  const long lane_bytes = 6L * n * (long)sizeof(float);
+  const int per = (sm_env && sm_env[0] == '0') ? 0
+                  : 2 * lane_bytes <= kInvitSmemMax ? 2 : lane_bytes <= kInvitSmemMax ? 1 : 0;
+  if (mode == 2 && per > 0) {
+    const size_t smem = (size_t)per * lane_bytes;
+    CU_E(cudaFuncSetAttribute(invit32_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+    invit32_smem_kernel<<<(nc + per - 1) / per, 32, smem, st>>>(
+        d32, e32, n, wt, first, nc, (float)(FLT_EPSILON * tnorm), zt, mp, per);
+  } else if (mode == 2)
     invit32_kernel<<<(nc + ib - 1) / ib, ib, 0, st>>>(d32, e32, n, wt, first, nc,
                                                       (float)(FLT_EPSILON * tnorm), zt, mp,
                                                       (float*)lanes);
@@ -643,8 +684,8 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
       CU_E(cudaMemsetAsync(flags, 0, sizeof(int), st));
       CU_E(launch_cholesky_tiled(g, mp, 1, nullptr, flags, chol_inv, st, &nl));
       int bad = 0;
-      CU_E(cudaMemcpyAsync(&bad, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CU_E(cudaStreamSynchronize(st));
+      const ReadPiece rp = {flags, &bad, sizeof(int)};
+      CU_E(read_to_host(reader, &rp, 1, st));
       if (bad == 0) break;
       if (attempt == 1) {
         err = "eigensolver: Cholesky-QR of the block failed with a shift";
@@ -731,8 +772,8 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
     if (step + 1 < steps) {
       RS_E(qy(xk, yv, mp, xn));
       std::vector<double> th(mp);
-      CU_E(cudaMemcpyAsync(th.data(), theta, sizeof(double) * mp, cudaMemcpyDeviceToHost, st));
-      CU_E(cudaStreamSynchronize(st));
+      const ReadPiece rp = {theta, th.data(), sizeof(double) * mp};
+      CU_E(read_to_host(reader, &rp, 1, st));
       a = th[mp - 1];
       lo = th[0];
       xs = xn;
@@ -743,8 +784,10 @@ rpa_status Refine::subspace(const cplx* hc, int n, int n_eig, double* lam_out, c
     CU_E(cudaMemcpyAsync(lam_out, theta, sizeof(double) * n_eig, cudaMemcpyDeviceToDevice, st));
   }
   int jst = 0;
-  CU_E(cudaMemcpyAsync(&jst, jw.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CU_E(cudaStreamSynchronize(st));
+  {
+    const ReadPiece rp = {jw.status, &jst, sizeof(int)};
+    CU_E(read_to_host(reader, &rp, 1, st));
+  }
   if (launches) *launches += nl;
   if (jst != 0) {
     CU_E(cudaMemset(jw.status, 0, sizeof(int)));

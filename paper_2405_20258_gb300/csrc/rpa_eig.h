@@ -50,6 +50,7 @@ struct Refine {
   cplx* chol_inv = nullptr;
   int* flags = nullptr;
   unsigned long long* absmax = nullptr;
+  HostReader reader;                     // small host reads outside the copy engines
   dense::HetrdWork hw32, hw64;
   dense::JacobiWork jw;
   // tensor-core workspace of the FP32 start's block products (planes of its own, so

@@ -112,4 +112,24 @@ cudaError_t launch_cholesky_logdet(cplx* work, const cplx* chis, int n, int batc
 cudaError_t launch_generate_m(const rpa_qpoint* q, int v0, int nv, int c0, int nc, void* out,
                               int dtype, cudaStream_t st);
 
+// Small device-to-host reads that bypass the copy engines: one kernel stores the pieces
+// into mapped pinned host memory, then the stream is synchronised.  A copy-engine read
+// (cudaMemcpyAsync to the host) can wait behind a large host-to-device copy that another
+// stream has in flight, such as the next q-point's inputs.
+struct HostReader {
+  char* host = nullptr;  // pinned, mapped
+  char* dev = nullptr;   // its device address
+  size_t bytes = 0;
+};
+struct ReadPiece {
+  const void* src;  // device
+  void* dst;        // host
+  size_t bytes;     // a multiple of 4
+};
+cudaError_t reader_alloc(HostReader& r, size_t bytes);
+void reader_free(HostReader& r);
+// Reads up to four pieces and synchronises st; pieces that do not fit the reader (or a
+// reader never allocated) go through cudaMemcpyAsync instead.
+cudaError_t read_to_host(HostReader& r, const ReadPiece* p, int n, cudaStream_t st);
+
 }  // namespace rpa

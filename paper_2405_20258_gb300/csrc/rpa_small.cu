@@ -3,6 +3,8 @@
 // and the counter-based input generator.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -421,6 +423,20 @@ __global__ void order_out_kernel(const OrderItem* it, long n, int n_v, int n_c, 
   }
 }
 
+
+// Words of up to four device arrays into one host-mapped buffer (read_to_host).
+struct ReadArgs {
+  const unsigned* src[4];
+  unsigned off[4], words[4];
+  int n;
+};
+
+__global__ void read_pieces_kernel(ReadArgs a, unsigned* out) {
+  for (int k = 0; k < a.n; ++k)
+    for (unsigned i = threadIdx.x; i < a.words[k]; i += blockDim.x) out[a.off[k] + i] = a.src[k][i];
+  __threadfence_system();
+}
+
 }  // namespace
 
 cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delta, double* ow,
@@ -428,6 +444,59 @@ cudaError_t launch_prepare_scalars(const rpa_qpoint& q, double* sv, double* delt
   long n = q.n_g + n_transitions(q);
   prepare_kernel<<<grid_for(n, 256), 256, 0, st>>>(q, sv, delta, ow, sf0, bad);
   return cudaGetLastError();
+}
+
+cudaError_t reader_alloc(HostReader& r, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* h = nullptr;
+  cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+  if (e != cudaSuccess) return e;
+  void* d = nullptr;
+  e = cudaHostGetDevicePointer(&d, h, 0);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h);
+    return e;
+  }
+  r.host = (char*)h;
+  r.dev = (char*)d;
+  r.bytes = bytes;
+  return cudaSuccess;
+}
+
+void reader_free(HostReader& r) {
+  if (r.host) cudaFreeHost(r.host);
+  r = HostReader{};
+}
+
+cudaError_t read_to_host(HostReader& r, const ReadPiece* p, int n, cudaStream_t st) {
+  size_t total = 0;
+  bool fits = r.host && n <= 4;
+  for (int k = 0; k < n; ++k) {
+    fits = fits && p[k].bytes % 4 == 0 && ((uintptr_t)p[k].src & 3) == 0;
+    total += p[k].bytes;
+  }
+  if (!fits || total > r.bytes) {
+    for (int k = 0; k < n; ++k) {
+      cudaError_t e = cudaMemcpyAsync(p[k].dst, p[k].src, p[k].bytes, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(st);
+  }
+  ReadArgs a{};
+  a.n = n;
+  unsigned off = 0;
+  for (int k = 0; k < n; ++k) {
+    a.src[k] = (const unsigned*)p[k].src;
+    a.off[k] = off;
+    a.words[k] = (unsigned)(p[k].bytes / 4);
+    off += a.words[k];
+  }
+  read_pieces_kernel<<<1, 256, 0, st>>>(a, (unsigned*)r.dev);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < n; ++k) memcpy(p[k].dst, r.host + 4 * (size_t)a.off[k], p[k].bytes);
+  return cudaSuccess;
 }
 
 long order_items(long n) {
