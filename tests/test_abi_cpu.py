@@ -76,3 +76,24 @@ def test_null_plan_calls(lib):
     assert lib.rpa_ecorr(None, 0, None, None) == rpa.RPA_EINVAL
     assert lib.rpa_plan_destroy(None) == rpa.RPA_EINVAL
     assert lib.rpa_generate_m(None, 0, 1, 0, 1, None, 0, None) == rpa.RPA_EINVAL
+
+
+def test_building_blocks_reject_bad_arguments(lib):
+    # every case fails its argument check before any CUDA call, so no device is needed;
+    # the non-NULL pointers below are never dereferenced
+    p = ctypes.c_void_p(256)
+    assert lib.rpa_tridiagonalize(0, 64, p, p, p, None) == rpa.RPA_EINVAL
+    assert lib.rpa_tridiagonalize(8, 16, p, p, p, None) == rpa.RPA_EINVAL
+    assert lib.rpa_tridiagonalize(8, 32, None, p, p, None) == rpa.RPA_EINVAL
+    assert lib.rpa_tridiagonalize(8, 32, p, p, None, None) == rpa.RPA_EINVAL
+    assert lib.rpa_hermitian_eig_jacobi(0, p, p, p, None) == rpa.RPA_EINVAL
+    assert lib.rpa_hermitian_eig_jacobi(4, p, None, p, None) == rpa.RPA_EINVAL
+    order = lib.rpa_transition_order
+    assert order(0, 1, 1, 0, p, p, p, None) == rpa.RPA_EINVAL          # no transitions
+    assert order(6, 0, 6, 0, p, p, p, None) == rpa.RPA_EINVAL          # n_v < 1
+    assert order(6, 2, 3, 3, p, p, p, None) == rpa.RPA_EINVAL          # seg_bands > n_v
+    assert order(6, 2, 3, -1, p, p, p, None) == rpa.RPA_EINVAL         # seg_bands < 0
+    assert order(10, 2, 3, 1, p, p, p, None) == rpa.RPA_EINVAL         # not k x n_v x n_c
+    assert order(6, 2, 3, 0, None, p, p, None) == rpa.RPA_EINVAL       # NULL delta
+    assert order(6, 2, 3, 0, p, p, None, None) == rpa.RPA_EINVAL       # NULL order
+    assert b"rpa_transition_order" in lib.rpa_last_error(None)
