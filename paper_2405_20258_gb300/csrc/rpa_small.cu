@@ -319,9 +319,9 @@ inline int grid_for(long n, int bs) {
   return (int)(b < 152L * 32 ? (b > 0 ? b : 1) : 152L * 32);
 }
 
-
 // ---- transition order of the tensor-core chi~(0) K-blocks --------------------
-// Transitions by decreasing weight |f_vc| / Delta_vc, equal weights by index (the
+// Transitions by decreasing |w_vc / Delta_vc| (w_vc = g_k (f_v - f_c) the pair weight,
+// so the key orders like f_vc(0)), equal keys by index (the
 // permutation of a stable sort), within segments of consecutive transitions when a
 // q-point is drawn in chunks of valence bands.  Items (segment, key bits, index) are
 // sorted ascending by a bitonic network: a non-negative double's bit pattern orders
@@ -422,7 +422,6 @@ __global__ void order_out_kernel(const OrderItem* it, long n, int n_v, int n_c, 
     order[pos] = (int)((long)x.idx - r0);
   }
 }
-
 
 // Words of up to four device arrays into one host-mapped buffer (read_to_host).
 struct ReadArgs {
