@@ -213,6 +213,9 @@ def reference_arm(args, w, rank, dist):
 # of 8,000 transitions and S = 4, from the ncu capture summarised in
 # profiles/slice_gemm_chi0_ng4000.md (a K = 32,000 launch scaled to K = 16,000). Valid for
 # the GEMM kernel as captured; set to None when the kernel changes until it is re-captured.
+# The one change to slice_gemm since the capture moves a lone FP32 tail level into its own
+# level's columns (S - Le == 1, the projection); the chi~(0) launch (S = 4, Le = 1) issues
+# the same loads, MMAs and epilogue as captured.
 CHI0_GEMM_TRAFFIC = {"workload": "qpoint-4000", "slices": 4, "bytes_per_launch": 3.52e9}
 
 
