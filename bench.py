@@ -585,8 +585,8 @@ def main():
             # plan.run returns only after the step's result reached the host), all pieces
             # queued on the copy stream at once: the copy engine then runs at the link's
             # rate beside the running step, whose own small device-to-host reads wait at
-            # most one piece's length (64 MB: 0.3 ms at 210 GB/s, 2 ms at 35 GB/s, the two
-            # rates seen on different boxes)
+            # most one piece's length (64 MB: 0.3 ms at 210 GB/s, 2 ms at 35 GB/s; host links
+            # have been measured at both rates)
             d = slots[i % 2]
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
